@@ -1,0 +1,105 @@
+"""Oracle: the generic GN / LM loop of Sec. 2 ("Solving NLS") on a stacked Jacobian.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+
+One iteration: H = J^T J, g = J^T r; LM adds lambda * D with D = diag(max(diag H, 1e-9));
+delta = -(H + lambda D)^-1 g (Cholesky, dense via torch.linalg, or sparse LU via SciPy);
+theta_c = theta (+) delta; accept iff S(theta_c) < S(theta) (GN always accepts); on accept
+lambda <- max(lambda/10, 1e-12) and the problem is re-linearised at theta_c, on reject
+lambda <- min(10 lambda, 1e12).  A problem stops ("freezes") once |S_old - S_c| <= tau S_old.
+The paper names LM with adaptive damping without its rule; these constants are this project's
+reading and are used identically by the CUDA path.
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import Callable
+
+import numpy as np
+import torch
+
+STATUS_OK, STATUS_NOT_CONVERGED, STATUS_NOT_SPD, STATUS_NAN = 0, 1, 2, 3
+LAM_MIN, LAM_MAX, DIAG_FLOOR = 1e-12, 1e12, 1e-9
+
+
+@dataclasses.dataclass
+class SolveInfo:
+    S_init: float
+    S_final: float
+    iterations: int
+    accepted: int
+    lam: float
+    status: int
+    S_history: list
+
+
+def damped_step(J, r, lam, damped):
+    """delta = -(J^T J + lam D)^-1 J^T r; returns (delta, ok).  J dense torch or scipy sparse."""
+    if isinstance(J, torch.Tensor):
+        H = J.T @ J
+        g = J.T @ r
+        A = H + lam * torch.diag(torch.clamp(torch.diagonal(H), min=DIAG_FLOOR)) if damped else H
+        L, info = torch.linalg.cholesky_ex(A)
+        if int(info) != 0:
+            return None, False
+        return -torch.cholesky_solve(g[:, None], L)[:, 0], True
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spl
+    H = (J.T @ J).tocsc()
+    g = J.T @ np.asarray(r.detach() if isinstance(r, torch.Tensor) else r)
+    if damped:
+        H = H + lam * sp.diags(np.maximum(H.diagonal(), DIAG_FLOOR))
+    delta = -spl.spsolve(H.tocsc(), g, permc_spec="MMD_AT_PLUS_A")
+    ok = bool(np.all(np.isfinite(delta)))
+    return torch.as_tensor(delta), ok
+
+
+def lm_loop(linearize: Callable, objective: Callable, retract: Callable, theta0,
+            algo="lm", iters=20, lam0=1e-3, tau=1e-14, record=False):
+    """Run ``iters`` GN/LM iterations.  ``linearize(theta) -> (r, J)``, ``objective(theta) -> S``,
+    ``retract(theta, delta) -> theta'``.  Branch decisions are taken on values; the arithmetic
+    stays on the autograd tape, so the loop can be differentiated (unrolled backward)."""
+    theta = theta0
+    r, J = linearize(theta)
+    S = 0.5 * (r * r).sum()
+    S0 = float(S.detach()) if isinstance(S, torch.Tensor) else float(S)
+    lam = float(lam0)
+    status = STATUS_OK
+    accepted = 0
+    done = 0
+    hist = [float(S)]
+    for it in range(iters):
+        done = it + 1
+        delta, ok = damped_step(J, r, lam, damped=(algo == "lm"))
+        if not ok:
+            if algo == "gn":
+                status = STATUS_NOT_SPD
+                break
+            lam = min(lam * 10.0, LAM_MAX)
+            hist.append(float(S))
+            continue
+        theta_c = retract(theta, delta)
+        S_c = objective(theta_c)
+        if not bool(torch.isfinite(torch.as_tensor(S_c))):
+            if algo == "gn":
+                status = STATUS_NAN
+                break
+            lam = min(lam * 10.0, LAM_MAX)
+            hist.append(float(S))
+            continue
+        S_old = float(S)
+        accept = (algo == "gn") or (float(S_c) < S_old)
+        frozen = abs(S_old - float(S_c)) <= tau * S_old
+        if accept:
+            theta = theta_c
+            S = S_c
+            accepted += 1
+            lam = max(lam / 10.0, LAM_MIN)
+            if not frozen and it + 1 < iters:
+                r, J = linearize(theta)
+        else:
+            lam = min(lam * 10.0, LAM_MAX)
+        hist.append(float(S))
+        if frozen:
+            break
+    return theta, SolveInfo(S0, float(S), done, accepted, lam, status, hist if record else [])

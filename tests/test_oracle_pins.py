@@ -1,0 +1,395 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics (CPU only).
+
+Each check is chosen so that a plausible slip in the oracle (a dropped term, a wrong sign,
+a transposed operand, the wrong perturbation side) fails at least one of them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.optimize as so
+import torch
+from scipy.spatial.transform import Rotation
+
+from oracle import ba, lie, nls, pgo
+from paper_2207_09442_b300 import synth
+
+F64 = torch.float64
+ANGLES = [0.0, 1e-9, 1e-5, 1e-3, 0.1, 1.0, 3.0, math.pi - 1e-6]
+
+
+def _twist4(xi):
+    M = np.zeros((4, 4))
+    M[:3, :3] = lie.hat3(torch.as_tensor(xi[3:])).numpy()
+    M[:3, 3] = xi[:3]
+    return M
+
+
+# ----------------------------------------------------------------------------- Lie groups
+@pytest.mark.parametrize("ang", ANGLES)
+def test_se3_exp_log_match_matrix_exponential(ang):
+    """SE(3) Exp is the matrix exponential of the twist; Log is its principal inverse (App. C)."""
+    rng = np.random.default_rng(1)
+    ax = rng.normal(size=3)
+    ax /= np.linalg.norm(ax)
+    xi = np.concatenate([rng.normal(size=3), ax * ang])
+    T = lie.se3_exp(torch.as_tensor(xi)).numpy()
+    E = sla.expm(_twist4(xi))
+    assert np.abs(T - E[:3, :4]).max() < 1e-13
+    back = lie.se3_log(torch.as_tensor(E[:3, :4])).numpy()
+    assert np.abs(back - xi).max() < 1e-9 * max(1.0, 1.0 / max(math.pi - ang, 1e-3) * 1e-3)
+    if 1e-3 < ang < 3.0:
+        L = sla.logm(E)
+        assert np.abs(L[:3, 3] - back[:3]).max() < 1e-10
+
+
+@pytest.mark.parametrize("ang", ANGLES)
+def test_so3_exp_matches_rotvec(ang):
+    ax = np.array([0.3, -0.5, 0.81])
+    ax /= np.linalg.norm(ax)
+    R = lie.so3_exp(torch.as_tensor(ax * ang)).numpy()
+    assert np.abs(R - Rotation.from_rotvec(ax * ang).as_matrix()).max() < 1e-14
+
+
+def test_so3_axis_aligned_closed_form():
+    """Rotation about z by psi is [[c, -s, 0], [s, c, 0], [0, 0, 1]] (textbook)."""
+    for psi in [0.2, -1.3, 2.9]:
+        R = lie.so3_exp(torch.tensor([0.0, 0.0, psi])).numpy()
+        c, s = math.cos(psi), math.sin(psi)
+        assert np.abs(R - np.array([[c, -s, 0], [s, c, 0], [0, 0, 1]])).max() < 1e-15
+
+
+@pytest.mark.parametrize("ang", ANGLES)
+def test_se2_exp_log_match_matrix_exponential(ang):
+    xi = np.array([0.7, -1.1, ang])
+    P = lie.se2_exp(torch.as_tensor(xi)).numpy()
+    E = sla.expm(np.array([[0, -ang, xi[0]], [ang, 0, xi[1]], [0, 0, 0]]))
+    assert abs(P[0] - E[0, 2]) + abs(P[1] - E[1, 2]) < 1e-13
+    assert abs(P[2] - E[0, 0]) + abs(P[3] - E[1, 0]) < 1e-14
+    assert np.abs(lie.se2_log(torch.as_tensor(P)).numpy() - xi).max() < 1e-9
+
+
+def test_log_exp_roundtrip_random():
+    g = torch.Generator().manual_seed(3)
+    xi = torch.randn(200, 6, generator=g, dtype=F64)
+    nrm = xi[:, 3:].norm(dim=-1, keepdim=True)
+    xi[:, 3:] *= torch.rand(200, 1, generator=g, dtype=F64) * 3.0 / nrm   # |phi| < 3 < pi
+    assert (lie.se3_log(lie.se3_exp(xi)) - xi).abs().max() < 1e-12
+    T = lie.se3_exp(xi)
+    assert (lie.se3_exp(lie.se3_log(T)) - T).abs().max() < 1e-12
+
+
+def test_adjoint_identity_via_oracle_primitives():
+    """T Exp(xi) T^-1 = Exp(Ad_T xi), Ad_T = [[R, [t]x R], [0, R]] for xi = [rho; phi]."""
+    g = torch.Generator().manual_seed(4)
+    T = lie.se3_exp(torch.randn(6, generator=g, dtype=F64))
+    xi = 0.3 * torch.randn(6, generator=g, dtype=F64)
+    R, t = T[:3, :3], T[:3, 3]
+    Ad = torch.zeros(6, 6, dtype=F64)
+    Ad[:3, :3] = R
+    Ad[3:, 3:] = R
+    Ad[:3, 3:] = lie.hat3(t) @ R
+    lhs = lie.se3_compose(lie.se3_compose(T, lie.se3_exp(xi)), lie.se3_inv(T))
+    rhs = lie.se3_exp(Ad @ xi)
+    assert (lhs - rhs).abs().max() < 1e-14
+
+
+def test_tangent_gradient_is_right_perturbation_derivative():
+    """App. C: D_g F . xi = d/ds F(g tau(s xi)) at s = 0; the oracle's tangent_grad is checked
+    against central differences of exactly that definition."""
+    g = torch.Generator().manual_seed(5)
+    T = lie.flat_se3(lie.se3_exp(torch.randn(3, 6, generator=g, dtype=F64)))
+    Tgt = lie.flat_se3(lie.se3_exp(torch.randn(3, 6, generator=g, dtype=F64)))
+    loss = lambda X: pgo.pose_error_loss(3, X, Tgt)
+    v = pgo.tangent_grad(3, loss, T)
+    h = 1e-6
+    for k in range(3):
+        for a in range(6):
+            e = torch.zeros(3, 6, dtype=F64)
+            e[k, a] = h
+            fd = (loss(lie.pose_retract(3, T, e)) - loss(lie.pose_retract(3, T, -e))) / (2 * h)
+            assert abs(float(fd) - float(v[k, a])) < 1e-8
+
+
+# ----------------------------------------------------------------------------- GN / LM loop
+def test_gn_one_step_on_listing1_model():
+    """Listing 1's model y = v exp(x) is linear in v: one GN step lands on the least-squares fit."""
+    rng = np.random.default_rng(0)
+    x = rng.normal(size=50)
+    y = 2.5 * np.exp(x) + 0.1 * rng.normal(size=50)
+    X, Y = torch.as_tensor(x), torch.as_tensor(y)
+    lin = lambda v: (Y - v * torch.exp(X), (-torch.exp(X))[:, None])
+    obj = lambda v: 0.5 * ((Y - v * torch.exp(X)) ** 2).sum()
+    v, info = nls.lm_loop(lin, obj, lambda v, d: v + d, torch.tensor([1.0]), algo="gn", iters=1)
+    ref = np.linalg.lstsq(np.exp(x)[:, None], y, rcond=None)[0]
+    assert abs(float(v[0]) - ref[0]) < 1e-12
+
+
+def test_gn_one_step_linear_least_squares_and_lm_limit():
+    rng = np.random.default_rng(1)
+    A = rng.normal(size=(30, 5))
+    b = rng.normal(size=30)
+    At, bt = torch.as_tensor(A), torch.as_tensor(b)
+    lin = lambda th: (At @ th - bt, At)
+    obj = lambda th: 0.5 * ((At @ th - bt) ** 2).sum()
+    ret = lambda th, d: th + d
+    th0 = torch.as_tensor(rng.normal(size=5))
+    th_gn, _ = nls.lm_loop(lin, obj, ret, th0, algo="gn", iters=1)
+    ref = np.linalg.lstsq(A, b, rcond=None)[0]
+    assert np.abs(th_gn.numpy() - ref).max() < 1e-12
+    # LM with lambda -> 0 takes the GN step
+    th_lm, _ = nls.lm_loop(lin, obj, ret, th0, algo="lm", iters=1, lam0=1e-12)
+    assert np.abs(th_lm.numpy() - ref).max() < 1e-9
+    # a large damping still decreases S and the accepted S never increases
+    th_big, info = nls.lm_loop(lin, obj, ret, th0, algo="lm", iters=15, lam0=1e3, record=True)
+    hist = info.S_history
+    assert all(b_ <= a_ for a_, b_ in zip(hist, hist[1:]))
+    assert np.abs(th_big.numpy() - ref).max() < 1e-6
+
+
+def _read_tree_golden():
+    here = os.path.join(os.path.dirname(__file__), "golden", "tree_se2_chain.txt")
+    edges, poses = [], []
+    for line in open(here):
+        if line.startswith("#") or not line.strip():
+            continue
+        f = line.split()
+        if f[0] in ("prior", "edge"):
+            edges.append((int(f[1]), int(f[2]), float(f[3]), float(f[4]), float(f[5])))
+        else:
+            poses.append((float(f[2]), float(f[3]), float(f[4])))
+    return edges, poses
+
+
+def test_tree_graph_optimum_is_dead_reckoning_golden():
+    edges, poses = _read_tree_golden()
+    N = len(poses)
+    Z = torch.tensor([[x, y, math.cos(p), math.sin(p)] for (_, _, x, y, p) in edges])
+    g = pgo.Graph(2, N, torch.tensor([e[0] for e in edges]), torch.tensor([e[1] for e in edges]),
+                  Z, torch.ones(len(edges), 3), torch.zeros(len(edges)),
+                  torch.tensor([[0.3 * k, -0.2 * k, 1.0, 0.0] for k in range(N)]),
+                  torch.zeros(N, 4))
+    th, info = pgo.solve(g, algo="gn", iters=30, tau=0.0)
+    assert info.S_final < 1e-24
+    for k, (x, y, p) in enumerate(poses):
+        assert abs(float(th[k, 0]) - x) < 1e-12 and abs(float(th[k, 1]) - y) < 1e-12
+        assert abs(math.atan2(float(th[k, 3]), float(th[k, 2])) - p) < 1e-12
+
+
+def test_tree_graph_se3_dead_reckoning():
+    b = synth.pgo_se3(batch=1, n_poses=12, n_lc=0, config_id=77)
+    g = pgo.graph_from_batch(b, 0)
+    th, info = pgo.solve(g, algo="gn", iters=15, tau=0.0)
+    assert info.S_final < 1e-22
+    # dead reckoning from the prior (identity) through the noisy chain measurements
+    T = torch.eye(4, dtype=F64)[:3]
+    for k in range(1, 12):
+        T = lie.se3_compose(T, lie.as_se3(g.Z[k - 1]))
+        assert (lie.as_se3(th[k]) - T).abs().max() < 1e-10
+
+
+def _np_se2_log(E):
+    psi = math.atan2(E[1, 0], E[0, 0])
+    if abs(psi) < 1e-12:
+        return np.array([E[0, 2], E[1, 2], psi])
+    V = np.array([[math.sin(psi), -(1 - math.cos(psi))], [1 - math.cos(psi), math.sin(psi)]]) / psi
+    return np.concatenate([np.linalg.solve(V, E[:2, 2]), [psi]])
+
+
+def _np_se2(x, y, p):
+    return np.array([[math.cos(p), -math.sin(p), x], [math.sin(p), math.cos(p), y], [0, 0, 1]])
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_tiny_se2_graph_against_scipy_least_squares(seed):
+    """Brute force: scipy's trust-region least squares on (x, y, psi) coordinates with an
+    independent SE(2) log (a linear solve with V) finds the same optimum as the oracle's GN."""
+    b = synth.pgo_se2(batch=1, n_poses=5, n_lc=2, config_id=100 + seed)
+    g = pgo.graph_from_batch(b, 0)
+    th, info = pgo.solve(g, algo="gn", iters=30, tau=0.0)
+    Zm = [_np_se2(z[0], z[1], math.atan2(z[3], z[2])) for z in b.meas]
+
+    def resid(q):
+        q = q.reshape(-1, 3)
+        out = []
+        for e in range(len(b.edge_i)):
+            i, j = b.edge_i[e], b.edge_j[e]
+            Ti = _np_se2(*q[i])
+            if j < 0:
+                E = np.linalg.inv(Zm[e]) @ Ti
+            else:
+                E = np.linalg.inv(Zm[e]) @ np.linalg.inv(Ti) @ _np_se2(*q[j])
+            out.append(b.wdiag[e] * _np_se2_log(E))
+        return np.concatenate(out)
+    q0 = np.stack([[p[0], p[1], math.atan2(p[3], p[2])] for p in b.theta_init]).reshape(-1)
+    sol = so.least_squares(resid, q0, method="lm", xtol=1e-15, ftol=1e-15, gtol=1e-15)
+    q = sol.x.reshape(-1, 3)
+    assert abs(0.5 * (sol.fun ** 2).sum() - info.S_final) < 1e-12
+    for k in range(len(q)):
+        # scipy's finite-difference Jacobians bound its solution's accuracy near 1e-8 along the
+        # flattest direction; the objective values above agree to 1e-12
+        assert abs(q[k, 0] - float(th[k, 0])) < 1e-7 and abs(q[k, 1] - float(th[k, 1])) < 1e-7
+        dpsi = q[k, 2] - math.atan2(float(th[k, 3]), float(th[k, 2]))
+        assert abs(math.remainder(dpsi, 2 * math.pi)) < 1e-7
+
+
+def test_tiny_se3_graph_against_scipy_least_squares():
+    """Same brute force for SE(3): rotation-vector coordinates and a matrix-logarithm residual."""
+    b = synth.pgo_se3(batch=1, n_poses=4, n_lc=1, config_id=200)
+    g = pgo.graph_from_batch(b, 0)
+    th, info = pgo.solve(g, algo="gn", iters=30, tau=0.0)
+    mats = lambda f12: np.vstack([f12.reshape(3, 4), [0, 0, 0, 1]])
+    Zm = [mats(z) for z in b.meas]
+
+    def T_of(q):
+        T = np.eye(4)
+        T[:3, :3] = Rotation.from_rotvec(q[3:]).as_matrix()
+        T[:3, 3] = q[:3]
+        return T
+
+    def log4(E):
+        L = np.real(sla.logm(E))
+        return np.concatenate([L[:3, 3], [L[2, 1], L[0, 2], L[1, 0]]])
+
+    def resid(q):
+        q = q.reshape(-1, 6)
+        out = []
+        for e in range(len(b.edge_i)):
+            i, j = b.edge_i[e], b.edge_j[e]
+            Ti = T_of(q[i])
+            E = np.linalg.inv(Zm[e]) @ Ti if j < 0 else \
+                np.linalg.inv(Zm[e]) @ np.linalg.inv(Ti) @ T_of(q[j])
+            out.append(b.wdiag[e] * log4(E))
+        return np.concatenate(out)
+    q0 = np.concatenate([np.concatenate([p.reshape(3, 4)[:, 3],
+                                         Rotation.from_matrix(p.reshape(3, 4)[:, :3]).as_rotvec()])
+                         for p in b.theta_init])
+    sol = so.least_squares(resid, q0, method="lm", xtol=1e-15, ftol=1e-15, gtol=1e-15)
+    assert abs(0.5 * (sol.fun ** 2).sum() - info.S_final) < 1e-11
+    q = sol.x.reshape(-1, 6)
+    for k in range(len(q)):
+        Tk = T_of(q[k])[:3]
+        assert np.abs(Tk - th[k].reshape(3, 4).numpy()).max() < 1e-7
+
+
+def test_oracle_jacobian_matches_central_differences():
+    b = synth.pgo_se3(batch=1, n_poses=6, n_lc=2, config_id=300)
+    g = pgo.graph_from_batch(b, 0)
+    th = g.theta_init
+    r, J = pgo.jacobian(g, th)
+    h = 1e-6
+    for col in range(0, J.shape[1], 5):
+        xi = torch.zeros(g.n, dtype=F64)
+        xi[col] = h
+        rp = pgo.residuals(g, th, xi=xi.reshape(-1, 6)).reshape(-1)
+        rm = pgo.residuals(g, th, xi=-xi.reshape(-1, 6)).reshape(-1)
+        assert (J[:, col] - (rp - rm) / (2 * h)).abs().max() < 1e-7
+    rs = pgo.residuals(g, th)
+    assert (r - rs.reshape(-1)).abs().max() == 0
+
+
+def test_lm_monotone_and_converges_se3():
+    b = synth.pgo_se3(batch=1, n_poses=24, n_lc=6, config_id=301)
+    g = pgo.graph_from_batch(b, 0)
+    th, info = pgo.solve(g, algo="lm", iters=25, lam0=1e-3, record=True)
+    hist = info.S_history
+    assert all(b_ <= a_ for a_, b_ in zip(hist, hist[1:]))
+    r, J = pgo.jacobian(g, th)
+    assert float((J.T @ r).abs().max()) < 1e-10
+
+
+# ----------------------------------------------------------------------------- implicit gradient
+def test_implicit_zero_residual_gn_equals_exact_equals_fd():
+    """With noise-free measurements S* = 0, so the true Hessian equals J^T J at theta* and both
+    implicit modes coincide; a random linear outer loss keeps the gradient nonzero."""
+    b = synth.pgo_se3(batch=1, n_poses=8, n_lc=2, config_id=302)
+    g = pgo.graph_from_batch(b, 0)
+    # replace the measurements by the exact ground-truth relative poses
+    Zs = []
+    for e in range(len(b.edge_i)):
+        i, j = int(g.ei[e]), int(g.ej[e])
+        Ti = lie.as_se3(g.theta_gt[i])
+        Zs.append(lie.flat_se3(Ti) if j < 0 else lie.flat_se3(
+            lie.se3_compose(lie.se3_inv(Ti), lie.as_se3(g.theta_gt[j]))))
+    g.Z = torch.stack(Zs)
+    th = pgo.solve_to_convergence(g, g.theta_init)
+    assert (th - g.theta_gt).abs().max() < 1e-10
+    cvec = torch.as_tensor(np.random.default_rng(0).normal(size=(g.n_poses, 6)))
+    Tref = lie.pose_retract(3, g.theta_gt, 0.05 * torch.ones(g.n_poses, 6, dtype=F64))
+    loss = lambda X: (cvec * lie.pose_log(3, lie.pose_compose(3, lie.pose_inv(3, Tref), X))).sum()
+    v = pgo.tangent_grad(3, loss, th)
+    ge, gl, _ = pgo.implicit_grads(g, th, v, "exact")
+    gn_e, gn_l, _ = pgo.implicit_grads(g, th, v, "gn")
+    assert float((ge - gn_e).norm() / ge.norm()) < 1e-7
+    coords = [("meas", 2, 1), ("meas", 8, 4), ("meas", 5, 0)]
+    fd = pgo.fd_grads(g, loss, th, coords)
+    for (w, e, k), f in zip(coords, fd):
+        assert abs(f - float(ge[e, k])) < 1e-6 * float(ge.abs().max())
+
+
+def test_implicit_exact_matches_fd_and_unrolled_noisy():
+    """Noisy graph: the exact-Hessian implicit gradient (Eq. 3) equals both central differences
+    with re-solve and the gradient unrolled through the solver's iterations; the GN-Hessian
+    variant differs at the level of the residuals."""
+    b = synth.pgo_se3(batch=1, n_poses=16, n_lc=4, config_id=3, log_weights=True)
+    g = pgo.graph_from_batch(b, 0)
+    th, info = pgo.solve(g, algo="lm", iters=20, lam0=1e-3)
+    loss = lambda X: pgo.pose_error_loss(3, X, g.theta_gt)
+    v = pgo.tangent_grad(3, loss, th)
+    ge, gl, _ = pgo.implicit_grads(g, th, v, "exact")
+    ue, ul = pgo.unrolled_grads(g, loss, algo="lm", iters=20, lam0=1e-3)
+    assert float((ue - ge).norm() / ge.norm()) < 1e-6
+    assert float((ul - gl).norm() / gl.norm()) < 1e-6
+    rng = np.random.default_rng(7)
+    E = g.ei.shape[0]
+    coords = [("meas", int(rng.integers(E)), int(rng.integers(6))) for _ in range(4)] + \
+             [("logw", int(rng.integers(E - 1)), 0) for _ in range(4)]
+    fd = pgo.fd_grads(g, loss, th, coords)
+    scale = max(float(ge.abs().max()), float(gl.abs().max()))
+    for (w, e, k), f in zip(coords, fd):
+        ref = float(ge[e, k]) if w == "meas" else float(gl[e])
+        assert abs(f - ref) < 1e-6 * scale
+    gn_e, _, _ = pgo.implicit_grads(g, th, v, "gn")
+    assert float((gn_e - ge).norm() / ge.norm()) > 1e-5
+
+
+# ----------------------------------------------------------------------------- bundle adjustment
+def test_huber_definition():
+    d = 2.0
+    s = torch.tensor([0.0, 1.0, 4.0 - 1e-12, 4.0, 4.0 + 1e-12, 9.0, 100.0])
+    rho = ba.huber(s, d)
+    assert abs(float(rho[3]) - 4.0) < 1e-15            # continuous at delta^2
+    assert abs(float(rho[5]) - (2 * 2 * 3 - 4)) < 1e-14  # 2 delta sqrt(s) - delta^2
+    assert float(rho[1]) == 1.0
+    d1 = ba.huber_d1(s, d)
+    assert float(d1[1]) == 1.0 and abs(float(d1[6]) - 0.2) < 1e-15
+
+
+def test_ba_jacobian_and_implicit_vs_fd():
+    b = synth.ba(batch=1, n_cams=10, n_pts=40, config_id=400)
+    P = ba.ba_from_batch(b, 0)
+    th = (P.cams_init, P.pts_init)
+    c, Jc, Jp, rq, Jq = ba._local_jacobians(P, th)
+    h = 1e-6
+    for a in range(6):
+        e = torch.zeros(len(P.obs_cam), 6, dtype=F64)
+        e[:, a] = h
+        z3 = torch.zeros(len(P.obs_cam), 3, dtype=F64)
+        cp = ba.reproj_cost(P.cams_init[P.obs_cam], P.pts_init[P.obs_pt], P.obs_uv, P.focal, e, z3, 0)
+        cm = ba.reproj_cost(P.cams_init[P.obs_cam], P.pts_init[P.obs_pt], P.obs_uv, P.focal, -e, z3, 0)
+        assert ((cp - cm) / (2 * h) - Jc[:, :, a]).abs().max() < 1e-5
+    th_s, info = ba.solve(P, iters=15)
+    v = ba.tangent_grad(P, th_s[0])
+    gobs, _ = ba.implicit_grad_obs(P, th_s, v)
+    # skip observations within 1e-3 px of the Huber kink
+    cs = ba.reproj_cost(th_s[0][P.obs_cam], th_s[1][P.obs_pt], P.obs_uv, P.focal,
+                        torch.zeros(len(P.obs_cam), 6), torch.zeros(len(P.obs_cam), 3), 0)
+    nrm = cs.norm(dim=-1)
+    ok = ((nrm - P.delta).abs() > 1e-3).nonzero()[:, 0].tolist()
+    coords = [(ok[k], k % 2) for k in (0, 7, 33, 61)]
+    fd = ba.fd_grad_obs(P, th_s, coords)
+    scale = float(gobs.abs().max())
+    for (o, k), f in zip(coords, fd):
+        assert abs(f - float(gobs[o, k])) < 1e-6 * scale
