@@ -1,0 +1,195 @@
+/*
+ * dnls.h -- C ABI of libdnls: batched differentiable nonlinear least squares on B300 (sm_103a).
+ *
+ * The library solves batches of independent nonlinear least-squares problems
+ *     S(theta) = 1/2 sum_i || w_i c_i(theta^i) ||^2                      (paper Eq. 1)
+ * with Gauss-Newton or Levenberg-Marquardt (paper Sec. 2 "Solving NLS", Sec. 3 optimizers), and
+ * differentiates the solution implicitly (paper Eq. 3 and Prop. 1, App. G.3):
+ *     D_phi theta* = -[D_theta g]^-1 D_phi g,   g = grad_theta S.
+ * Problem structure follows the paper's statement of the problem (Sec. 3): variables (poses;
+ * cameras and points), cost functions with weights (priors, relative-pose "between" costs,
+ * reprojection errors), the objective that holds them, the optimizer step and the layer's
+ * forward/backward.
+ *
+ * Conventions shared by every call:
+ *   - SE(3) pose: 12 doubles, row-major 3x4 [R | t].  SE(2) pose: 4 doubles (x, y, cos, sin).
+ *   - Tangent vectors: SE(3) [rho(3); phi(3)], SE(2) [rho_x, rho_y, psi]; retraction
+ *     T (+) xi = T Exp(xi) (right perturbation, App. C).
+ *   - Cost weight: w_e = exp(logw_e) * wdiag_e (diagonal), residual r_e = w_e * c_e.
+ *   - Pointers documented "device" must be device memory of the current CUDA device; pointers
+ *     documented "host" must be host memory.  All device work is enqueued on `stream` (a
+ *     cudaStream_t passed as void*; NULL = legacy default stream) and is asynchronous: results
+ *     are valid once the stream has been synchronised.
+ *   - Ownership: the caller owns every device buffer it passes, including the workspace.  The
+ *     library owns the opaque handles and the device copy of their symbolic structure, which
+ *     it allocates at create time and frees at destroy time.
+ *   - Errors: every call returns a dnls_status; no C++ exception crosses the ABI.  Numerical
+ *     trouble in one problem of a batch does not fail the call: it is reported per problem in
+ *     dnls_info.status (DNLS_PROBLEM_*).
+ *   - A handle may be used from one host thread at a time.  Calls that share a workspace must
+ *     be ordered on one stream.
+ */
+#ifndef DNLS_H
+#define DNLS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DNLS_OK = 0,
+  DNLS_ERR_ARG = 1,          /* invalid argument (null pointer, bad index, bad size, bad enum) */
+  DNLS_ERR_CUDA = 2,         /* a CUDA runtime call failed (launch error, out of memory, ...) */
+  DNLS_ERR_WORKSPACE = 3,    /* workspace pointer null/misaligned or smaller than required */
+  DNLS_ERR_TIMEOUT = 4,      /* a bounded device-side wait gave up */
+  DNLS_ERR_UNSUPPORTED = 5   /* option combination not implemented */
+} dnls_status;
+
+/* per-problem status written to dnls_info.status */
+enum {
+  DNLS_PROBLEM_OK = 0,
+  DNLS_PROBLEM_NOT_CONVERGED = 1, /* backward: refinement did not reach refine_tol */
+  DNLS_PROBLEM_NOT_SPD = 2,       /* a Cholesky pivot was not positive (GN stops; LM raises lambda) */
+  DNLS_PROBLEM_NAN = 3            /* a non-finite objective was met */
+};
+
+enum { DNLS_SE2 = 2, DNLS_SE3 = 3 };
+enum { DNLS_GN = 0, DNLS_LM = 1 };
+enum { DNLS_FP64 = 0, DNLS_MIXED_FP32 = 1 };
+enum { DNLS_IMPLICIT_EXACT = 0, DNLS_IMPLICIT_GN = 1 };
+enum { DNLS_ORDER_MIN_DEGREE = 0, DNLS_ORDER_NATURAL = 1 };
+
+/* Solver options (paper Sec. 3: optimizer choice, max_iterations, backward_mode).  The LM
+ * damping rule is not given in the paper; this library uses: damping matrix
+ * D = diag(max(diag H, 1e-9)), lambda *= 10 on reject, /= 10 on accept, lambda clamped to
+ * [1e-12, 1e12], accept iff S_new < S_old; a problem stops once |S_old - S_new| <= tau*S_old.
+ * A rejected step counts as an iteration. */
+typedef struct {
+  int32_t algo;            /* DNLS_GN or DNLS_LM */
+  int32_t iters;           /* number of iterations K (>= 0) */
+  int32_t precision;       /* DNLS_FP64, or DNLS_MIXED_FP32 (residuals, Jacobians and H in FP32;
+                              relative poses, g, the factorization and the acceptance in FP64) */
+  int32_t backward_mode;   /* DNLS_IMPLICIT_EXACT (true Hessian of S) or DNLS_IMPLICIT_GN */
+  int32_t refine_max;      /* max refinement steps of the adjoint solve (>= 1) */
+  int32_t threads;         /* threads per CTA: 0 = library choice, else 128, 256 or 512 */
+  int32_t ctas_per_sm;     /* resident CTAs per SM of the persistent launch: 0 = library choice */
+  int32_t smem_factor;     /* 1: keep a problem's Cholesky factor in shared memory when it fits */
+  double lambda0;          /* initial LM damping */
+  double tau;              /* freeze threshold on the relative decrease of S */
+  double refine_tol;       /* adjoint solve stops once ||v - H x|| <= refine_tol * ||v|| */
+} dnls_solver_opts;
+
+/* Per-problem report (device array of `batch` entries, written by forward/backward). */
+typedef struct {
+  double S_init;        /* objective at the initial poses */
+  double S_final;       /* objective at the returned poses */
+  double lambda;        /* damping of the last factorization */
+  double refine_resid;  /* backward: final ||v - H x|| / ||v|| */
+  int32_t iterations;   /* iterations run (<= iters; fewer if the problem froze) */
+  int32_t accepted;     /* accepted steps */
+  int32_t status;       /* DNLS_PROBLEM_* (forward); backward overwrites on failure */
+  int32_t refine_steps; /* backward: refinement steps taken */
+} dnls_info;
+
+/* ------------------------------------------------------------------------------------------
+ * Pose graphs: SE(2)/SE(3) poses with prior and between costs (paper Sec. 3 "Gaussian
+ * measurements", "relative pose measurement"; App. D.1 coordinate-independent relative pose
+ * error):   between e=(i,j):  c_e = Log(Z_e^-1 T_i^-1 T_j);   prior e=(i,-1):  c_e = Log(Z_e^-1 T_i).
+ * ------------------------------------------------------------------------------------------ */
+typedef struct dnls_graph dnls_graph; /* opaque: structure + symbolic factorization of a batch */
+
+typedef struct {
+  int32_t kind;                 /* DNLS_SE2 or DNLS_SE3 */
+  int32_t batch;                /* B >= 1 independent problems */
+  const int64_t* pose_offsets;  /* host [B+1], problem b owns poses [pose_offsets[b], pose_offsets[b+1]) */
+  const int64_t* edge_offsets;  /* host [B+1], problem b owns costs [edge_offsets[b], edge_offsets[b+1]) */
+  const int32_t* edge_i;        /* host [E]: local index of the first pose of each cost */
+  const int32_t* edge_j;        /* host [E]: local index of the second pose, or -1 for a prior */
+  int32_t ordering;             /* DNLS_ORDER_MIN_DEGREE (default) or DNLS_ORDER_NATURAL */
+} dnls_graph_desc;
+
+typedef struct {
+  const double* meas;   /* device [E, 12] (SE3) or [E, 4] (SE2): measurements Z_e */
+  const double* wdiag;  /* device [E, dof]: fixed square-root-information diagonal d_e */
+  const float* logw;    /* device [E] learnable log-weights l_e, or NULL (all zero) */
+} dnls_graph_inputs;
+
+/* Build the handle: validates indices, computes a fill-reducing block ordering, the symbolic
+ * block Cholesky structure and its elimination-tree level schedule once per structure (reused
+ * by every numeric factorization, paper Sec. 4.2), and uploads it to the current device.
+ * Errors: DNLS_ERR_ARG (bad sizes/indices), DNLS_ERR_CUDA (allocation/copy). */
+dnls_status dnls_graph_create(const dnls_graph_desc* desc, dnls_graph** out);
+void dnls_graph_destroy(dnls_graph* g);
+
+/* Bytes of device workspace forward/backward need for these options (the base must be
+ * 256-byte aligned).  The workspace also carries the cached factorization from forward to
+ * backward: keep it alive and unmodified between a forward and the backward that uses it. */
+dnls_status dnls_graph_workspace_size(const dnls_graph* g, const dnls_solver_opts* opts, size_t* bytes);
+
+/* Forward (the layer's forward, Sec. 3): opts->iters GN/LM iterations on every problem, all
+ * problems in one persistent launch (one CTA per problem, scheduled longest first).
+ *   theta: device [P, 12|4] FP64, initial poses in, optimised poses out.
+ *   info:  device [B] per-problem report (may be NULL).
+ * Errors: DNLS_ERR_ARG, DNLS_ERR_WORKSPACE, DNLS_ERR_CUDA. */
+dnls_status dnls_graph_forward(const dnls_graph* g, const dnls_solver_opts* opts,
+                               const dnls_graph_inputs* in, double* theta, void* workspace,
+                               size_t workspace_bytes, void* stream, dnls_info* info);
+
+/* Implicit backward (Eq. 3 / Prop. 1, App. G.3) at theta* from the preceding forward on the
+ * same workspace.  Solves H x = v with H the true Hessian of S (DNLS_IMPLICIT_EXACT) or the
+ * Gauss-Newton matrix (DNLS_IMPLICIT_GN) by refinement preconditioned with the forward's cached
+ * factor (Sec. 4.2 "backward for custom linear solvers"), then writes
+ *   grad_meas[e] = -(D_{eps_e} g)^T x   (tangent of Z_e (+) eps = Z_e Exp(eps)), device [E, dof]
+ *   grad_logw[e] = -(D_{l_e} g)^T x,                                              device [E]
+ * v: device [P, dof] tangent gradient dL/dxi of the outer loss at theta*.
+ * Either output may be NULL.  info (device [B], may be NULL) receives refine_resid,
+ * refine_steps and DNLS_PROBLEM_NOT_CONVERGED where the tolerance was not reached. */
+dnls_status dnls_graph_backward(const dnls_graph* g, const dnls_solver_opts* opts,
+                                const dnls_graph_inputs* in, const double* theta_star,
+                                const double* v, double* grad_meas, double* grad_logw,
+                                void* workspace, size_t workspace_bytes, void* stream,
+                                dnls_info* info);
+
+/* Linearise and assemble at theta without solving (for inspection and tests): writes the
+ * undamped Gauss-Newton matrix H = J^T J (device, one dense n_b x n_b row-major block per
+ * problem, packed one after another, n_b = dof * poses of b, in the caller's pose order),
+ * g = J^T r (device [sum n_b]) and S (device [B], FP64).  Any output may be NULL. */
+dnls_status dnls_graph_linearize(const dnls_graph* g, const dnls_solver_opts* opts,
+                                 const dnls_graph_inputs* in, const double* theta,
+                                 double* H_dense, double* grad, double* S, void* workspace,
+                                 size_t workspace_bytes, void* stream);
+
+/* Projection of Euclidean gradients onto the tangent space (App. C, proj_g):
+ * v[k] = d L(T_k Exp(xi)) / d xi at 0 from G[k] = dL/dT_k (device [n, 12|4] each; v device
+ * [n, dof]).  Errors: DNLS_ERR_ARG. */
+dnls_status dnls_project_grad(int32_t kind, int64_t n, const double* theta, const double* G,
+                              double* v, void* stream);
+
+/* Minimum-norm Euclidean lift of tangent gradients at poses T (the inverse direction of
+ * dnls_project_grad on the tangent space): G[k] in T_k's tangent space with proj(G[k]) = v[k]. */
+dnls_status dnls_lift_grad(int32_t kind, int64_t n, const double* T, const double* v, double* G,
+                           void* stream);
+
+/* Sizes of the symbolic factorization (host values; for reports and tests). */
+typedef struct {
+  int64_t n_poses, n_costs, n_blocks_L, n_block_updates, n_levels_max;
+  double factor_flops;   /* FP64 flops of one numeric factorization of the whole batch */
+  double dense_flops;    /* flops an n^3/3 dense Cholesky would take on the same batch */
+} dnls_graph_stats;
+dnls_status dnls_graph_get_stats(const dnls_graph* g, dnls_graph_stats* out);
+
+/* Human-readable name of a status code (static storage). */
+const char* dnls_status_string(dnls_status s);
+
+/* Peak-rate probe used by the benchmark's roofline: times independent FP64 FMA chains on every
+ * SM and returns the achieved FP64 FLOP/s in *flops (host).  Synchronises `stream`. */
+dnls_status dnls_probe_fp64_peak(int32_t iters, void* stream, double* flops);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DNLS_H */
