@@ -1,0 +1,1091 @@
+// Pose-graph GN/LM forward and implicit backward on B300 (sm_103a).
+//
+// One CTA owns one problem for the whole solve (a persistent launch: CTAs take problems from a
+// counter in the workspace, most expensive first), so every phase of an iteration - linearize,
+// assemble, damped block Cholesky, triangular solves, retraction, objective, acceptance - runs
+// back to back on data that stays in shared memory / L1 / L2.  All reductions are done by one
+// thread per output in a fixed order: results are bitwise reproducible and need no atomics
+// beyond the work counter.
+//
+// Paper mapping: Eq. 1 objective; Sec. 2 GN step (sum J^T J) delta = -(sum J^T r) and retraction;
+// Sec. 3 LM with adaptive damping; Sec. 4.1 batching/vectorisation; Sec. 4.2 sparse Cholesky with
+// a symbolic factorization reused across numeric ones and a cached factor for the backward;
+// Eq. 3 / Prop. 1 implicit differentiation (App. G.3).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "../../include/dnls.h"
+#include "dnls_cost.cuh"
+#include "dnls_graph.h"
+
+namespace dnls {
+
+constexpr double kLamMin = 1e-12, kLamMax = 1e12, kDiagFloor = 1e-9;
+
+struct GraphDev {
+  const ProbMeta* meta;
+  const int32_t* sym;
+  const int32_t* ei;
+  const int32_t* ej;
+  const int32_t* order;
+  int B;
+};
+
+struct KArgs {
+  GraphDev g;
+  const double* meas;
+  const double* wdiag;
+  const float* logw;
+  double* theta;        // forward: in/out poses; backward/linearize: theta (read)
+  const double* v;      // backward: tangent gradient [P, dof]
+  double* grad_meas;    // backward outputs
+  double* grad_logw;
+  double* H_dense;      // linearize outputs
+  double* grad;
+  double* S_out;
+  char* ws;
+  int* counter;
+  dnls_info* info;
+  int algo, iters, mode, refine_max;
+  double lam0, tau, refine_tol;
+  int smem_L;           // bytes of dynamic shared memory available for a factor (0 = none)
+};
+
+// ----------------------------------------------------------------------------- helpers
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  const int t = threadIdx.x;
+  red[t] = v;
+  __syncthreads();
+  for (int s = blockDim.x >> 1; s > 0; s >>= 1) {
+    if (t < s) red[t] += red[t + s];
+    __syncthreads();
+  }
+  const double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+template <int KIND>
+struct Prob {
+  static constexpr int D = Group<KIND>::DOF, PW = Group<KIND>::PW, BS = D * D, JW = 2 * BS + D;
+  int N, E, npair, nnzL, nlev;
+  const int32_t *perm, *iperm, *colptr, *rows, *rowptr, *rowent, *lvlptr, *lvlcols, *tgtptr, *tgt,
+      *gptr, *gsrc, *panptr, *pan, *incptr, *inc, *pairptr, *pairs, *pairtgt, *lsrc;
+  const int32_t *ei, *ej;
+  const double *meas, *wdiag;
+  const float* logw;
+  double* theta;
+  double *H, *L, *Lg, *Linv, *g, *dx, *tmp, *thc, *bx, *bv, *br, *bhx, *ebuf;
+  void* J;
+  ProbState* st;
+  const ProbMeta* m;
+
+  __device__ void init(const KArgs& a, int b, double* smemL) {
+    m = a.g.meta + b;
+    N = m->N;
+    E = m->E;
+    npair = m->npair;
+    nnzL = m->nnzL;
+    nlev = m->nlev;
+    const int32_t* s = a.g.sym + m->sym;
+    perm = s + m->o_perm;
+    iperm = s + m->o_iperm;
+    colptr = s + m->o_colptr;
+    rows = s + m->o_rows;
+    rowptr = s + m->o_rowptr;
+    rowent = s + m->o_rowent;
+    lvlptr = s + m->o_lvlptr;
+    lvlcols = s + m->o_lvlcols;
+    tgtptr = s + m->o_tgtptr;
+    tgt = s + m->o_tgt;
+    gptr = s + m->o_gptr;
+    gsrc = s + m->o_gsrc;
+    panptr = s + m->o_panptr;
+    pan = s + m->o_pan;
+    incptr = s + m->o_incptr;
+    inc = s + m->o_inc;
+    pairptr = s + m->o_pairptr;
+    pairs = s + m->o_pairs;
+    pairtgt = s + m->o_pairtgt;
+    lsrc = s + m->o_lsrc;
+    ei = a.g.ei + m->edge_off;
+    ej = a.g.ej + m->edge_off;
+    meas = a.meas + m->edge_off * PW;
+    wdiag = a.wdiag + m->edge_off * D;
+    logw = a.logw ? a.logw + m->edge_off : nullptr;
+    theta = a.theta + m->pose_off * PW;
+    char* w = a.ws + m->ws;
+    H = (double*)(w + m->w_H);
+    Lg = (double*)(w + m->w_L);
+    L = (smemL && m->L_bytes <= a.smem_L) ? smemL : Lg;
+    Linv = (double*)(w + m->w_Linv);
+    g = (double*)(w + m->w_g);
+    dx = (double*)(w + m->w_dx);
+    tmp = (double*)(w + m->w_tmp);
+    thc = (double*)(w + m->w_thc);
+    J = (void*)(w + m->w_J);
+    bx = (double*)(w + m->w_bx);
+    bv = (double*)(w + m->w_bv);
+    br = (double*)(w + m->w_br);
+    bhx = (double*)(w + m->w_bhx);
+    ebuf = (double*)(w + m->w_ebuf);
+    st = (ProbState*)(w + m->w_state);
+  }
+
+  __device__ __forceinline__ void weight(int e, double* w) const {
+    const double s = logw ? exp((double)logw[e]) : 1.0;
+#pragma unroll
+    for (int a = 0; a < D; ++a) w[a] = s * wdiag[e * D + a];
+  }
+};
+
+// ----------------------------------------------------------------------------- linearize
+// Per cost: weighted residual and Jacobians in precision P, stored as [r | J_i | J_j].
+// The relative transforms are formed in FP64 and only then rounded to P.
+template <int KIND, class P>
+__device__ void lin_costs(Prob<KIND>& p, const double* poses) {
+  typedef Group<KIND> G;
+  constexpr int D = G::DOF, PW = G::PW, BS = D * D, JW = Prob<KIND>::JW;
+  P* Jb = (P*)p.J;
+  for (int e = threadIdx.x; e < p.E; e += blockDim.x) {
+    const int i = p.ei[e], j = p.ej[e];
+    double w[D];
+    p.weight(e, w);
+    P wp[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) wp[a] = (P)w[a];
+    const double* Z = p.meas + (int64_t)e * PW;
+    const double* Ti = poses + (int64_t)i * PW;
+    P* out = Jb + (int64_t)e * JW;
+    if (j >= 0) {
+      const double* Tj = poses + (int64_t)j * PW;
+      double A[PW], Ai[PW], Em[PW];
+      G::invmul(Ti, Tj, A);
+      G::invmul(Tj, Ti, Ai);
+      G::invmul(Z, A, Em);
+      P Ap[PW], Ep[PW];
+#pragma unroll
+      for (int k = 0; k < PW; ++k) {
+        Ap[k] = (P)Ai[k];
+        Ep[k] = (P)Em[k];
+      }
+      between_lin<KIND, P>(Ap, Ep, wp, out, out + D, out + D + BS);
+    } else {
+      double Em[PW];
+      G::invmul(Z, Ti, Em);
+      P Ep[PW];
+#pragma unroll
+      for (int k = 0; k < PW; ++k) Ep[k] = (P)Em[k];
+      prior_lin<KIND, P>(Ep, wp, out, out + D);
+    }
+  }
+}
+
+// S = 1/2 sum ||w c||^2 in FP64 (the acceptance test always runs in FP64).
+template <int KIND>
+__device__ double eval_S(Prob<KIND>& p, const double* poses, double* red) {
+  typedef Group<KIND> G;
+  constexpr int D = G::DOF, PW = G::PW;
+  double acc = 0.0;
+  for (int e = threadIdx.x; e < p.E; e += blockDim.x) {
+    const int i = p.ei[e], j = p.ej[e];
+    double w[D], Em[PW], c[D];
+    p.weight(e, w);
+    const double* Z = p.meas + (int64_t)e * PW;
+    const double* Ti = poses + (int64_t)i * PW;
+    if (j >= 0) {
+      double A[PW];
+      G::invmul(Ti, poses + (int64_t)j * PW, A);
+      G::invmul(Z, A, Em);
+    } else {
+      G::invmul(Z, Ti, Em);
+    }
+    G::log(Em, c);
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      const double r = w[a] * c[a];
+      acc += 0.5 * r * r;
+    }
+  }
+  return block_sum(acc, red);
+}
+
+// H (diagonal and pair blocks, undamped) and g = J^T r from the per-cost Jacobians.
+// H products in P (FP32 on the mixed path), g accumulated in FP64.
+template <int KIND, class P>
+__device__ void assemble(Prob<KIND>& p) {
+  constexpr int D = Group<KIND>::DOF, BS = D * D, JW = Prob<KIND>::JW;
+  const P* Jb = (const P*)p.J;
+  const int n_diag = p.N * BS, n_pair = p.npair * BS, n_g = p.N * D;
+  const int total = n_diag + n_pair + n_g;
+  for (int it = threadIdx.x; it < total; it += blockDim.x) {
+    if (it < n_diag) {
+      const int k = it / BS, el = it % BS, a = el / D, b = el % D;
+      P acc = P(0);
+      for (int q = p.incptr[k]; q < p.incptr[k + 1]; ++q) {
+        const int t = p.inc[q];
+        const P* Jt = Jb + (int64_t)(t >> 1) * JW + D + (t & 1) * BS;
+#pragma unroll
+        for (int mm = 0; mm < D; ++mm) acc += Jt[mm * D + a] * Jt[mm * D + b];
+      }
+      p.H[(int64_t)k * BS + el] = (double)acc;
+    } else if (it < n_diag + n_pair) {
+      const int q0 = it - n_diag, pr = q0 / BS, el = q0 % BS, a = el / D, b = el % D;
+      P acc = P(0);
+      for (int q = p.pairptr[pr]; q < p.pairptr[pr + 1]; ++q) {
+        const int t = p.pairs[q];
+        const P* Jc = Jb + (int64_t)(t >> 1) * JW + D;
+        const P* X = (t & 1) ? Jc + BS : Jc;  // row block's Jacobian
+        const P* Y = (t & 1) ? Jc : Jc + BS;  // column block's Jacobian
+#pragma unroll
+        for (int mm = 0; mm < D; ++mm) acc += X[mm * D + a] * Y[mm * D + b];
+      }
+      p.H[(int64_t)(p.N + pr) * BS + el] = (double)acc;
+    } else {
+      const int q0 = it - n_diag - n_pair, k = q0 / D, a = q0 % D;
+      double acc = 0.0;
+      for (int q = p.incptr[k]; q < p.incptr[k + 1]; ++q) {
+        const int t = p.inc[q];
+        const P* r = Jb + (int64_t)(t >> 1) * JW;
+        const P* Jt = r + D + (t & 1) * BS;
+#pragma unroll
+        for (int mm = 0; mm < D; ++mm) acc += (double)Jt[mm * D + a] * (double)r[mm];
+      }
+      p.g[(int64_t)k * D + a] = acc;
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------- factor
+// L <- H + lam * diag(max(diag H, floor)), then left-looking block Cholesky level by level.
+// Returns false (uniformly across the CTA) if a pivot is not positive or not finite.  A failing
+// thread writes the call's generation number `gen` into *sflag; the flag is never reset, so a
+// slow thread can never see a later call's state.
+template <int KIND>
+__device__ bool factor(Prob<KIND>& p, double lam, int* sflag, int gen) {
+  constexpr int D = Group<KIND>::DOF, BS = D * D;
+  double* L = p.L;
+  const int nb = p.N + p.nnzL;
+  for (int it = threadIdx.x; it < nb * BS; it += blockDim.x) {
+    const int t = it / BS, el = it % BS;
+    double v;
+    if (t < p.N) {
+      v = p.H[(int64_t)t * BS + el];
+      if (el / D == el % D) v += lam * fmax(v, kDiagFloor);
+    } else {
+      const int src = p.lsrc[t - p.N];
+      v = src >= 0 ? p.H[(int64_t)(p.N + src) * BS + el] : 0.0;
+    }
+    L[(int64_t)t * BS + el] = v;
+  }
+  __syncthreads();
+  for (int lv = 0; lv < p.nlev; ++lv) {
+    // (1) subtract the products of already-factored descendant columns
+    const int t0 = p.tgtptr[lv], t1 = p.tgtptr[lv + 1];
+    for (int it = threadIdx.x; it < (t1 - t0) * BS; it += blockDim.x) {
+      const int q = t0 + it / BS, el = it % BS, a = el / D, b = el % D;
+      const int s0 = p.gptr[q], s1 = p.gptr[q + 1];
+      if (s0 == s1) continue;
+      double acc = 0.0;
+      for (int s = s0; s < s1; ++s) {
+        const double* X = L + (int64_t)p.gsrc[2 * s] * BS + a * D;
+        const double* Y = L + (int64_t)p.gsrc[2 * s + 1] * BS + b * D;
+#pragma unroll
+        for (int mm = 0; mm < D; ++mm) acc = fma(X[mm], Y[mm], acc);
+      }
+      L[(int64_t)p.tgt[q] * BS + el] -= acc;
+    }
+    __syncthreads();
+    // (2) dense Cholesky of each diagonal block of the level (one thread per column) and the
+    //     inverse of its factor
+    const int c0 = p.lvlptr[lv], c1 = p.lvlptr[lv + 1];
+    for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
+      const int k = p.lvlcols[c];
+      double A[BS];
+      double* Lk = L + (int64_t)k * BS;
+#pragma unroll
+      for (int e = 0; e < BS; ++e) A[e] = Lk[e];
+      bool ok = true;
+#pragma unroll
+      for (int jj = 0; jj < D; ++jj) {
+        double d = A[jj * D + jj];
+#pragma unroll
+        for (int mm = 0; mm < jj; ++mm) d -= A[jj * D + mm] * A[jj * D + mm];
+        ok = ok && (d > 0.0) && isfinite(d);
+        const double l = sqrt(fmax(d, 1e-300));
+        const double il = 1.0 / l;
+        A[jj * D + jj] = l;
+#pragma unroll
+        for (int ii = jj + 1; ii < D; ++ii) {
+          double s = A[ii * D + jj];
+#pragma unroll
+          for (int mm = 0; mm < jj; ++mm) s -= A[ii * D + mm] * A[jj * D + mm];
+          A[ii * D + jj] = s * il;
+        }
+      }
+      // inverse of the lower-triangular factor
+      double I[BS];
+#pragma unroll
+      for (int e = 0; e < BS; ++e) I[e] = 0.0;
+#pragma unroll
+      for (int jj = 0; jj < D; ++jj) {
+        I[jj * D + jj] = 1.0 / A[jj * D + jj];
+#pragma unroll
+        for (int ii = jj + 1; ii < D; ++ii) {
+          double s = 0.0;
+#pragma unroll
+          for (int mm = jj; mm < ii; ++mm) s += A[ii * D + mm] * I[mm * D + jj];
+          I[ii * D + jj] = -s / A[ii * D + ii];
+        }
+      }
+#pragma unroll
+      for (int ii = 0; ii < D; ++ii)
+#pragma unroll
+        for (int jj = 0; jj < D; ++jj) {
+          Lk[ii * D + jj] = jj <= ii ? A[ii * D + jj] : 0.0;
+          p.Linv[(int64_t)k * BS + ii * D + jj] = I[ii * D + jj];
+        }
+      if (!ok) *sflag = gen;
+    }
+    __syncthreads();
+    if (*sflag == gen) return false;
+    // (3) off-diagonal blocks of the level's columns: L(r,k) <- A(r,k) L(k,k)^-T, one row each
+    const int q0 = p.panptr[lv], q1 = p.panptr[lv + 1];
+    for (int it = threadIdx.x; it < (q1 - q0) * D; it += blockDim.x) {
+      const int q = q0 + it / D, row = it % D;
+      double* X = L + (int64_t)p.pan[2 * q] * BS + row * D;
+      const double* Ik = p.Linv + (int64_t)p.pan[2 * q + 1] * BS;
+      double a[D], o[D];
+#pragma unroll
+      for (int mm = 0; mm < D; ++mm) a[mm] = X[mm];
+#pragma unroll
+      for (int jj = 0; jj < D; ++jj) {
+        double s = 0.0;
+#pragma unroll
+        for (int mm = 0; mm <= jj; ++mm) s = fma(a[mm], Ik[jj * D + mm], s);
+        o[jj] = s;
+      }
+#pragma unroll
+      for (int jj = 0; jj < D; ++jj) X[jj] = o[jj];
+    }
+    __syncthreads();
+  }
+  return true;
+}
+
+// In place: x <- (L L^T)^-1 x (positions order, FP64), level by level.
+template <int KIND>
+__device__ void chol_solve(Prob<KIND>& p, double* x) {
+  constexpr int D = Group<KIND>::DOF, BS = D * D;
+  const double* L = p.L;
+  for (int lv = 0; lv < p.nlev; ++lv) {
+    const int c0 = p.lvlptr[lv], c1 = p.lvlptr[lv + 1];
+    for (int it = threadIdx.x; it < (c1 - c0) * D; it += blockDim.x) {
+      const int k = p.lvlcols[c0 + it / D], i = it % D;
+      double s = x[k * D + i];
+      for (int q = p.rowptr[k]; q < p.rowptr[k + 1]; ++q) {
+        const double* B = L + (int64_t)p.rowent[2 * q] * BS + i * D;
+        const double* y = x + p.rowent[2 * q + 1] * D;
+#pragma unroll
+        for (int mm = 0; mm < D; ++mm) s = fma(-B[mm], y[mm], s);
+      }
+      p.tmp[k * D + i] = s;
+    }
+    __syncthreads();
+    for (int it = threadIdx.x; it < (c1 - c0) * D; it += blockDim.x) {
+      const int k = p.lvlcols[c0 + it / D], i = it % D;
+      const double* I = p.Linv + (int64_t)k * BS + i * D;
+      double s = 0.0;
+#pragma unroll
+      for (int mm = 0; mm < D; ++mm)
+        if (mm <= i) s = fma(I[mm], p.tmp[k * D + mm], s);
+      x[k * D + i] = s;
+    }
+    __syncthreads();
+  }
+  for (int lv = p.nlev - 1; lv >= 0; --lv) {
+    const int c0 = p.lvlptr[lv], c1 = p.lvlptr[lv + 1];
+    for (int it = threadIdx.x; it < (c1 - c0) * D; it += blockDim.x) {
+      const int k = p.lvlcols[c0 + it / D], i = it % D;
+      double s = x[k * D + i];
+      const int base = p.colptr[k];
+      const int cnt = p.colptr[k + 1] - base;
+      for (int aa = 0; aa < cnt; ++aa) {
+        const double* B = L + (int64_t)(p.N + base + aa) * BS + i;
+        const double* y = x + p.rows[base + aa] * D;
+#pragma unroll
+        for (int mm = 0; mm < D; ++mm) s = fma(-B[mm * D], y[mm], s);
+      }
+      p.tmp[k * D + i] = s;
+    }
+    __syncthreads();
+    for (int it = threadIdx.x; it < (c1 - c0) * D; it += blockDim.x) {
+      const int k = p.lvlcols[c0 + it / D], i = it % D;
+      const double* I = p.Linv + (int64_t)k * BS;
+      double s = 0.0;
+#pragma unroll
+      for (int mm = 0; mm < D; ++mm)
+        if (mm >= i) s = fma(I[mm * D + i], p.tmp[k * D + mm], s);
+      x[k * D + i] = s;
+    }
+    __syncthreads();
+  }
+}
+
+template <int KIND>
+__device__ void retract(Prob<KIND>& p, const double* src, const double* delta_pos, double* dst) {
+  typedef Group<KIND> G;
+  constexpr int D = G::DOF, PW = G::PW;
+  for (int v = threadIdx.x; v < p.N; v += blockDim.x) {
+    const double* d = delta_pos + p.iperm[v] * D;
+    double xi[D], Ex[PW], T[PW], out[PW];
+#pragma unroll
+    for (int a = 0; a < D; ++a) xi[a] = d[a];
+#pragma unroll
+    for (int a = 0; a < PW; ++a) T[a] = src[(int64_t)v * PW + a];
+    G::exp(xi, Ex);
+    G::mul(T, Ex, out);
+#pragma unroll
+    for (int a = 0; a < PW; ++a) dst[(int64_t)v * PW + a] = out[a];
+  }
+}
+
+// ----------------------------------------------------------------------------- forward
+template <int KIND, class P>
+__device__ void forward_problem(const KArgs& a, int b, double* smemL, double* red, int* sflag) {
+  constexpr int D = Group<KIND>::DOF, PW = Group<KIND>::PW;
+  Prob<KIND> p;
+  p.init(a, b, smemL);
+  const int n = p.N * D;
+  double S = eval_S<KIND>(p, p.theta, red);
+  const double S0 = S;
+  lin_costs<KIND, P>(p, p.theta);
+  __syncthreads();
+  assemble<KIND, P>(p);
+  __syncthreads();
+  const bool lm = a.algo == DNLS_LM;
+  double lam = lm ? a.lam0 : 0.0, lam_fact = lam;
+  int done = 0, accepted = 0, status = DNLS_PROBLEM_OK, factor_ok = 0;
+  for (int it = 0; it < a.iters; ++it) {
+    done = it + 1;
+    const bool ok = factor<KIND>(p, lam, sflag, it);
+    factor_ok = ok ? 1 : 0;
+    lam_fact = lam;
+    if (!ok) {
+      if (!lm) {
+        status = DNLS_PROBLEM_NOT_SPD;
+        break;
+      }
+      lam = fmin(lam * 10.0, kLamMax);
+      continue;
+    }
+    for (int k = threadIdx.x; k < n; k += blockDim.x) p.dx[k] = -p.g[k];
+    __syncthreads();
+    chol_solve<KIND>(p, p.dx);
+    retract<KIND>(p, p.theta, p.dx, p.thc);
+    __syncthreads();
+    const double Sc = eval_S<KIND>(p, p.thc, red);
+    if (!isfinite(Sc)) {
+      if (!lm) {
+        status = DNLS_PROBLEM_NAN;
+        break;
+      }
+      lam = fmin(lam * 10.0, kLamMax);
+      continue;
+    }
+    const bool accept = !lm || Sc < S;
+    const bool frozen = fabs(S - Sc) <= a.tau * S;
+    if (accept) {
+      for (int k = threadIdx.x; k < p.N * PW; k += blockDim.x) p.theta[k] = p.thc[k];
+      __syncthreads();
+      ++accepted;
+      S = Sc;
+      if (lm) lam = fmax(lam / 10.0, kLamMin);
+      if (!frozen && it + 1 < a.iters) {
+        lin_costs<KIND, P>(p, p.theta);
+        __syncthreads();
+        assemble<KIND, P>(p);
+        __syncthreads();
+      }
+    } else {
+      lam = fmin(lam * 10.0, kLamMax);
+    }
+    if (frozen) break;
+  }
+  if (p.L != p.Lg && factor_ok) {  // keep the factor for the backward
+    const int nb = (p.N + p.nnzL) * D * D;
+    for (int k = threadIdx.x; k < nb; k += blockDim.x) p.Lg[k] = p.L[k];
+  }
+  if (threadIdx.x == 0) {
+    p.st->lambda_fact = lam_fact;
+    p.st->S = S;
+    p.st->factor_ok = factor_ok;
+    if (a.info) {
+      dnls_info& in = a.info[b];
+      in.S_init = S0;
+      in.S_final = S;
+      in.lambda = lam_fact;
+      in.refine_resid = 0.0;
+      in.iterations = done;
+      in.accepted = accepted;
+      in.status = status;
+      in.refine_steps = 0;
+    }
+  }
+  __syncthreads();
+}
+
+extern __shared__ double dyn_smem[];
+
+// Takes the next problem from the workspace counter (most expensive first).
+__device__ __forceinline__ int next_problem(const KArgs& a, int* slot) {
+  if (threadIdx.x == 0) *slot = atomicAdd(a.counter, 1);
+  __syncthreads();
+  const int q = *slot;
+  __syncthreads();
+  return q < a.g.B ? a.g.order[q] : -1;
+}
+
+template <int KIND, class P>
+__global__ void __launch_bounds__(256) k_forward(KArgs a) {
+  __shared__ double red[256];
+  __shared__ int sflag, slot;
+  for (;;) {
+    const int b = next_problem(a, &slot);
+    if (b < 0) break;
+    if (threadIdx.x == 0) sflag = -1;
+    __syncthreads();
+    forward_problem<KIND, P>(a, b, a.smem_L ? dyn_smem : nullptr, red, &sflag);
+  }
+}
+
+// ----------------------------------------------------------------------------- backward
+// Exact-Hessian product at theta* for one problem: per cost, forward-mode (dual number in t)
+// evaluation of the local gradient at (T_i Exp(t x_i), T_j Exp(t x_j)), gathered per pose;
+// the chart term -1/2 ad(x_k)^T g_k turns the point-wise derivative into the derivative in the
+// chart theta* (+) xi in which the Hessian of Eq. 3 is taken.  Also leaves the local gradients
+// (value parts) in ebuf for the log-weight VJP.
+template <int KIND>
+__device__ void hvp_exact(Prob<KIND>& p, const double* x, double* hx) {
+  typedef Group<KIND> G;
+  constexpr int D = G::DOF, PW = G::PW;
+  typedef Dual<double> Dd;
+  for (int e = threadIdx.x; e < p.E; e += blockDim.x) {
+    const int i = p.ei[e], j = p.ej[e];
+    double w[D];
+    p.weight(e, w);
+    Dd wd[D], Ti[PW], Zd[PW], r[D], Ji[D * D], gi[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) wd[k] = Dd(w[k]);
+#pragma unroll
+    for (int k = 0; k < PW; ++k) Zd[k] = Dd(p.meas[(int64_t)e * PW + k]);
+    pose_dual<KIND>(p.theta + (int64_t)i * PW, x + p.iperm[i] * D, Ti);
+    double* eb = p.ebuf + (int64_t)e * 4 * D;
+    if (j >= 0) {
+      Dd Tj[PW], A[PW], Ai[PW], Em[PW], Jj[D * D], gj[D];
+      pose_dual<KIND>(p.theta + (int64_t)j * PW, x + p.iperm[j] * D, Tj);
+      G::invmul(Ti, Tj, A);
+      G::invmul(Tj, Ti, Ai);
+      G::invmul(Zd, A, Em);
+      between_lin<KIND, Dd>(Ai, Em, wd, r, Ji, Jj);
+      jt_r<D>(Ji, r, gi);
+      jt_r<D>(Jj, r, gj);
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        eb[2 * D + k] = gj[k].v;
+        eb[3 * D + k] = gj[k].d;
+      }
+    } else {
+      Dd Em[PW];
+      G::invmul(Zd, Ti, Em);
+      prior_lin<KIND, Dd>(Em, wd, r, Ji);
+      jt_r<D>(Ji, r, gi);
+    }
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      eb[k] = gi[k].v;
+      eb[D + k] = gi[k].d;
+    }
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < p.N; k += blockDim.x) {
+    double h[D], gs[D], corr[D], xk[D];
+#pragma unroll
+    for (int a2 = 0; a2 < D; ++a2) {
+      h[a2] = 0.0;
+      gs[a2] = 0.0;
+      xk[a2] = x[k * D + a2];
+    }
+    for (int q = p.incptr[k]; q < p.incptr[k + 1]; ++q) {
+      const int t = p.inc[q];
+      const double* eb = p.ebuf + (int64_t)(t >> 1) * 4 * D + (t & 1) * 2 * D;
+#pragma unroll
+      for (int a2 = 0; a2 < D; ++a2) {
+        gs[a2] += eb[a2];
+        h[a2] += eb[D + a2];
+      }
+    }
+    G::adT(xk, gs, corr);
+#pragma unroll
+    for (int a2 = 0; a2 < D; ++a2) hx[k * D + a2] = h[a2] - 0.5 * corr[a2];
+  }
+  __syncthreads();
+}
+
+// Gauss-Newton product (sum J^T J) x at theta* from FP64 Jacobians in the J buffer; also leaves
+// the local gradients J^T r in ebuf.
+template <int KIND>
+__device__ void hvp_gn(Prob<KIND>& p, const double* x, double* hx) {
+  constexpr int D = Group<KIND>::DOF, BS = D * D, JW = Prob<KIND>::JW;
+  const double* Jb = (const double*)p.J;
+  for (int e = threadIdx.x; e < p.E; e += blockDim.x) {
+    const int i = p.ei[e], j = p.ej[e];
+    const double* r = Jb + (int64_t)e * JW;
+    const double* Ji = r + D;
+    const double* Jj = Ji + BS;
+    double u[D];
+#pragma unroll
+    for (int a2 = 0; a2 < D; ++a2) {
+      double s = 0.0;
+#pragma unroll
+      for (int b2 = 0; b2 < D; ++b2) {
+        s = fma(Ji[a2 * D + b2], x[p.iperm[i] * D + b2], s);
+        if (j >= 0) s = fma(Jj[a2 * D + b2], x[p.iperm[j] * D + b2], s);
+      }
+      u[a2] = s;
+    }
+    double* eb = p.ebuf + (int64_t)e * 4 * D;
+    for (int slot = 0; slot < (j >= 0 ? 2 : 1); ++slot) {
+      const double* Js = slot ? Jj : Ji;
+#pragma unroll
+      for (int b2 = 0; b2 < D; ++b2) {
+        double s = 0.0, gv = 0.0;
+#pragma unroll
+        for (int a2 = 0; a2 < D; ++a2) {
+          s = fma(Js[a2 * D + b2], u[a2], s);
+          gv = fma(Js[a2 * D + b2], r[a2], gv);
+        }
+        eb[slot * 2 * D + b2] = gv;
+        eb[slot * 2 * D + D + b2] = s;
+      }
+    }
+  }
+  __syncthreads();
+  for (int it = threadIdx.x; it < p.N * D; it += blockDim.x) {
+    const int k = it / D, a2 = it % D;
+    double h = 0.0;
+    for (int q = p.incptr[k]; q < p.incptr[k + 1]; ++q) {
+      const int t = p.inc[q];
+      h += p.ebuf[(int64_t)(t >> 1) * 4 * D + (t & 1) * 2 * D + D + a2];
+    }
+    hx[it] = h;
+  }
+  __syncthreads();
+}
+
+template <int KIND>
+__device__ void backward_problem(const KArgs& a, int b, double* smemL, double* red, int* sflag) {
+  typedef Group<KIND> G;
+  constexpr int D = G::DOF, PW = G::PW;
+  typedef Dual<double> Dd;
+  Prob<KIND> p;
+  p.init(a, b, nullptr);  // the cached factor lives in the workspace
+  (void)smemL;
+  const int n = p.N * D;
+  int status = DNLS_PROBLEM_OK;
+  const bool need_J = a.mode == DNLS_IMPLICIT_GN;
+  if (need_J || !p.st->factor_ok) {
+    lin_costs<KIND, double>(p, p.theta);
+    __syncthreads();
+  }
+  if (!p.st->factor_ok) {  // no usable cached factor: factor H_GN(theta*) undamped
+    assemble<KIND, double>(p);
+    __syncthreads();
+    if (!factor<KIND>(p, 0.0, sflag, 0)) status = DNLS_PROBLEM_NOT_SPD;
+  }
+  double vn2 = 0.0;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const int pos = k / D, c = k % D;
+    const double vv = a.v[(p.m->pose_off + p.perm[pos]) * D + c];
+    p.bv[k] = vv;
+    p.br[k] = vv;
+    p.bx[k] = 0.0;
+    vn2 += vv * vv;
+  }
+  const double vnorm = sqrt(block_sum(vn2, red));
+  double rel = 0.0;
+  int steps = 0;
+  if (status == DNLS_PROBLEM_OK && vnorm > 0.0) {
+    for (int it = 0; it < a.refine_max; ++it) {
+      steps = it + 1;
+      for (int k = threadIdx.x; k < n; k += blockDim.x) p.dx[k] = p.br[k];
+      __syncthreads();
+      chol_solve<KIND>(p, p.dx);
+      for (int k = threadIdx.x; k < n; k += blockDim.x) p.bx[k] += p.dx[k];
+      __syncthreads();
+      if (need_J)
+        hvp_gn<KIND>(p, p.bx, p.bhx);
+      else
+        hvp_exact<KIND>(p, p.bx, p.bhx);
+      double r2 = 0.0;
+      for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const double rr = p.bv[k] - p.bhx[k];
+        p.br[k] = rr;
+        r2 += rr * rr;
+      }
+      rel = sqrt(block_sum(r2, red)) / vnorm;
+      if (!(rel > a.refine_tol)) break;
+    }
+    if (!(rel <= a.refine_tol)) status = DNLS_PROBLEM_NOT_CONVERGED;
+  } else if (status == DNLS_PROBLEM_OK) {
+    // v = 0: x = 0, but the local gradients are still needed below
+    if (need_J)
+      hvp_gn<KIND>(p, p.bx, p.bhx);
+    else
+      hvp_exact<KIND>(p, p.bx, p.bhx);
+  }
+  // per-cost VJPs with the final x
+  for (int e = threadIdx.x; e < p.E; e += blockDim.x) {
+    const int64_t ge = p.m->edge_off + e;
+    const int i = p.ei[e], j = p.ej[e];
+    if (status == DNLS_PROBLEM_NOT_SPD) {
+      if (a.grad_logw) a.grad_logw[ge] = 0.0;
+      if (a.grad_meas)
+        for (int k = 0; k < D; ++k) a.grad_meas[ge * D + k] = 0.0;
+      continue;
+    }
+    const double* xi = p.bx + p.iperm[i] * D;
+    const double* eb = p.ebuf + (int64_t)e * 4 * D;
+    if (a.grad_logw) {
+      double s = 0.0;
+#pragma unroll
+      for (int k = 0; k < D; ++k) s += xi[k] * eb[k];
+      if (j >= 0) {
+        const double* xj = p.bx + p.iperm[j] * D;
+#pragma unroll
+        for (int k = 0; k < D; ++k) s += xj[k] * eb[2 * D + k];
+      }
+      a.grad_logw[ge] = -2.0 * s;
+    }
+    if (a.grad_meas) {
+      double w[D];
+      p.weight(e, w);
+      Dd wd[D], Ti[PW], Zd[PW], Em[PW], o[D];
+#pragma unroll
+      for (int k = 0; k < D; ++k) wd[k] = Dd(w[k]);
+#pragma unroll
+      for (int k = 0; k < PW; ++k) Zd[k] = Dd(p.meas[(int64_t)e * PW + k]);
+      pose_dual<KIND>(p.theta + (int64_t)i * PW, xi, Ti);
+      if (j >= 0) {
+        Dd Tj[PW], A[PW];
+        pose_dual<KIND>(p.theta + (int64_t)j * PW, p.bx + p.iperm[j] * D, Tj);
+        G::invmul(Ti, Tj, A);
+        G::invmul(Zd, A, Em);
+      } else {
+        G::invmul(Zd, Ti, Em);
+      }
+      meas_grad_neg<KIND, Dd>(Em, wd, o);
+#pragma unroll
+      for (int k = 0; k < D; ++k) a.grad_meas[ge * D + k] = o[k].d;
+    }
+  }
+  if (threadIdx.x == 0 && a.info) {
+    a.info[b].refine_resid = rel;
+    a.info[b].refine_steps = steps;
+    if (status != DNLS_PROBLEM_OK) a.info[b].status = status;
+  }
+  __syncthreads();
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(256) k_backward(KArgs a) {
+  __shared__ double red[256];
+  __shared__ int sflag, slot;
+  for (;;) {
+    const int b = next_problem(a, &slot);
+    if (b < 0) break;
+    if (threadIdx.x == 0) sflag = -1;
+    __syncthreads();
+    backward_problem<KIND>(a, b, nullptr, red, &sflag);
+  }
+}
+
+// ----------------------------------------------------------------------------- linearize (inspection)
+template <int KIND>
+__global__ void __launch_bounds__(256) k_linearize(KArgs a) {
+  constexpr int D = Group<KIND>::DOF, BS = D * D;
+  __shared__ double red[256];
+  const int b = blockIdx.x;
+  Prob<KIND> p;
+  p.init(a, b, nullptr);
+  const double S = eval_S<KIND>(p, p.theta, red);
+  lin_costs<KIND, double>(p, p.theta);
+  __syncthreads();
+  assemble<KIND, double>(p);
+  __syncthreads();
+  const int n = p.N * D;
+  if (a.S_out && threadIdx.x == 0) a.S_out[b] = S;
+  if (a.grad)
+    for (int k = threadIdx.x; k < n; k += blockDim.x)
+      a.grad[p.m->pose_off * D + p.perm[k / D] * D + k % D] = p.g[k];
+  if (a.H_dense) {
+    double* Hd = a.H_dense + p.m->dense_off;
+    for (int k = threadIdx.x; k < n * n; k += blockDim.x) Hd[k] = 0.0;
+    __syncthreads();
+    for (int it = threadIdx.x; it < (p.N + p.npair) * BS; it += blockDim.x) {
+      const int t = it / BS, el = it % BS, aa = el / D, bb = el % D;
+      int R, C;
+      if (t < p.N) {
+        R = C = t;
+      } else {
+        const int id = p.pairtgt[t - p.N] - p.N;  // off-diagonal index in column order
+        int col = 0;
+        while (p.colptr[col + 1] <= id) ++col;
+        R = p.rows[id];
+        C = col;
+      }
+      const double v = p.H[(int64_t)t * BS + el];
+      const int r = p.perm[R] * D + aa, c = p.perm[C] * D + bb;
+      Hd[(int64_t)r * n + c] = v;
+      if (t >= p.N) Hd[(int64_t)c * n + r] = v;
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------- host side
+struct GraphHandle {
+  GraphHost h;
+  int device = -1;
+  ProbMeta* d_meta = nullptr;
+  int32_t* d_sym = nullptr;
+  int32_t* d_ei = nullptr;
+  int32_t* d_ej = nullptr;
+  int32_t* d_order = nullptr;
+  int sm_count = 0;
+  int smem_optin = 0;
+};
+
+}  // namespace dnls
+
+struct dnls_graph {
+  dnls::GraphHandle impl;
+};
+
+using namespace dnls;
+
+namespace {
+
+dnls_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return DNLS_OK;
+  cudaGetLastError();
+  return DNLS_ERR_CUDA;
+}
+
+template <class T>
+dnls_status upload(T** dst, const std::vector<T>& src) {
+  const size_t bytes = std::max<size_t>(1, src.size()) * sizeof(T);
+  if (cudaMalloc((void**)dst, bytes) != cudaSuccess) return cuda_status(cudaErrorMemoryAllocation);
+  if (!src.empty() && cudaMemcpy(*dst, src.data(), src.size() * sizeof(T),
+                                 cudaMemcpyHostToDevice) != cudaSuccess)
+    return DNLS_ERR_CUDA;
+  return DNLS_OK;
+}
+
+dnls_status check_opts(const dnls_solver_opts* o) {
+  if (!o) return DNLS_ERR_ARG;
+  if (o->algo != DNLS_GN && o->algo != DNLS_LM) return DNLS_ERR_ARG;
+  if (o->iters < 0 || o->iters > 100000) return DNLS_ERR_ARG;
+  if (o->precision != DNLS_FP64 && o->precision != DNLS_MIXED_FP32) return DNLS_ERR_ARG;
+  if (o->backward_mode != DNLS_IMPLICIT_EXACT && o->backward_mode != DNLS_IMPLICIT_GN)
+    return DNLS_ERR_ARG;
+  if (o->threads != 0 && o->threads != 128 && o->threads != 256) return DNLS_ERR_ARG;
+  if (o->ctas_per_sm < 0 || o->ctas_per_sm > 16) return DNLS_ERR_ARG;
+  if (!(o->lambda0 >= 0.0) || !(o->tau >= 0.0)) return DNLS_ERR_ARG;
+  return DNLS_OK;
+}
+
+dnls_status check_ws(const dnls_graph* g, void* ws, size_t bytes) {
+  if (!ws || ((uintptr_t)ws & 255)) return DNLS_ERR_WORKSPACE;
+  if ((int64_t)bytes < g->impl.h.ws_bytes) return DNLS_ERR_WORKSPACE;
+  return DNLS_OK;
+}
+
+KArgs base_args(const dnls_graph* g, const dnls_graph_inputs* in, void* ws) {
+  KArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.g.meta = g->impl.d_meta;
+  a.g.sym = g->impl.d_sym;
+  a.g.ei = g->impl.d_ei;
+  a.g.ej = g->impl.d_ej;
+  a.g.order = g->impl.d_order;
+  a.g.B = g->impl.h.B;
+  a.meas = in->meas;
+  a.wdiag = in->wdiag;
+  a.logw = in->logw;
+  a.ws = (char*)ws;
+  a.counter = (int*)ws;
+  return a;
+}
+
+template <class K>
+dnls_status launch_persistent(K kernel, const dnls_graph* g, const dnls_solver_opts* o, KArgs& a,
+                              cudaStream_t st, bool use_smem_L) {
+  const GraphHandle& G = g->impl;
+  const int threads = o->threads ? o->threads : (G.h.dof == 6 ? 256 : 128);
+  int ctas = o->ctas_per_sm ? o->ctas_per_sm : 2;
+  int smem = 0;
+  if (use_smem_L && o->smem_factor) {
+    const int budget = std::min(G.smem_optin, (228 * 1024) / ctas - 4096);
+    smem = std::min(G.h.max_L_bytes, budget);
+    if (smem < 0) smem = 0;
+  }
+  a.smem_L = smem;
+  if (smem > 0 &&
+      cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+    return DNLS_ERR_CUDA;
+  const int grid = std::max(1, std::min(G.h.B, G.sm_count * ctas));
+  if (cudaMemsetAsync(a.counter, 0, sizeof(int), st) != cudaSuccess) return DNLS_ERR_CUDA;
+  kernel<<<grid, threads, smem, st>>>(a);
+  return cuda_status(cudaGetLastError());
+}
+
+}  // namespace
+
+extern "C" {
+
+dnls_status dnls_graph_create(const dnls_graph_desc* desc, dnls_graph** out) {
+  if (!desc || !out) return DNLS_ERR_ARG;
+  *out = nullptr;
+  dnls_graph* g = new (std::nothrow) dnls_graph();
+  if (!g) return DNLS_ERR_ARG;
+  int rc = build_graph_host(desc->kind, desc->batch, desc->pose_offsets, desc->edge_offsets,
+                            desc->edge_i, desc->edge_j, desc->ordering, &g->impl.h);
+  if (rc != DNLS_OK) {
+    delete g;
+    return (dnls_status)rc;
+  }
+  GraphHandle& G = g->impl;
+  dnls_status s = cuda_status(cudaGetDevice(&G.device));
+  if (s == DNLS_OK) s = cuda_status(cudaDeviceGetAttribute(&G.sm_count, cudaDevAttrMultiProcessorCount, G.device));
+  if (s == DNLS_OK)
+    s = cuda_status(cudaDeviceGetAttribute(&G.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, G.device));
+  if (s == DNLS_OK) s = upload(&G.d_meta, G.h.meta);
+  if (s == DNLS_OK) s = upload(&G.d_sym, G.h.sym);
+  if (s == DNLS_OK) s = upload(&G.d_ei, G.h.ei);
+  if (s == DNLS_OK) s = upload(&G.d_ej, G.h.ej);
+  if (s == DNLS_OK) s = upload(&G.d_order, G.h.order);
+  if (s != DNLS_OK) {
+    dnls_graph_destroy(g);
+    return s;
+  }
+  *out = g;
+  return DNLS_OK;
+}
+
+void dnls_graph_destroy(dnls_graph* g) {
+  if (!g) return;
+  GraphHandle& G = g->impl;
+  cudaFree(G.d_meta);
+  cudaFree(G.d_sym);
+  cudaFree(G.d_ei);
+  cudaFree(G.d_ej);
+  cudaFree(G.d_order);
+  delete g;
+}
+
+dnls_status dnls_graph_workspace_size(const dnls_graph* g, const dnls_solver_opts* opts, size_t* bytes) {
+  if (!g || !bytes) return DNLS_ERR_ARG;
+  if (opts && check_opts(opts) != DNLS_OK) return DNLS_ERR_ARG;
+  *bytes = (size_t)g->impl.h.ws_bytes;
+  return DNLS_OK;
+}
+
+dnls_status dnls_graph_forward(const dnls_graph* g, const dnls_solver_opts* opts,
+                               const dnls_graph_inputs* in, double* theta, void* workspace,
+                               size_t workspace_bytes, void* stream, dnls_info* info) {
+  if (!g || !in || !theta || !in->meas || !in->wdiag) return DNLS_ERR_ARG;
+  dnls_status s = check_opts(opts);
+  if (s != DNLS_OK) return s;
+  if ((s = check_ws(g, workspace, workspace_bytes)) != DNLS_OK) return s;
+  KArgs a = base_args(g, in, workspace);
+  a.theta = theta;
+  a.info = info;
+  a.algo = opts->algo;
+  a.iters = opts->iters;
+  a.lam0 = opts->lambda0;
+  a.tau = opts->tau;
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool mixed = opts->precision == DNLS_MIXED_FP32;
+  if (g->impl.h.kind == DNLS_SE3)
+    return mixed ? launch_persistent(k_forward<3, float>, g, opts, a, st, true)
+                 : launch_persistent(k_forward<3, double>, g, opts, a, st, true);
+  return mixed ? launch_persistent(k_forward<2, float>, g, opts, a, st, true)
+               : launch_persistent(k_forward<2, double>, g, opts, a, st, true);
+}
+
+dnls_status dnls_graph_backward(const dnls_graph* g, const dnls_solver_opts* opts,
+                                const dnls_graph_inputs* in, const double* theta_star,
+                                const double* v, double* grad_meas, double* grad_logw,
+                                void* workspace, size_t workspace_bytes, void* stream,
+                                dnls_info* info) {
+  if (!g || !in || !theta_star || !v || !in->meas || !in->wdiag) return DNLS_ERR_ARG;
+  dnls_status s = check_opts(opts);
+  if (s != DNLS_OK) return s;
+  if (opts->refine_max < 1 || !(opts->refine_tol >= 0.0)) return DNLS_ERR_ARG;
+  if ((s = check_ws(g, workspace, workspace_bytes)) != DNLS_OK) return s;
+  KArgs a = base_args(g, in, workspace);
+  a.theta = const_cast<double*>(theta_star);
+  a.v = v;
+  a.grad_meas = grad_meas;
+  a.grad_logw = grad_logw;
+  a.info = info;
+  a.mode = opts->backward_mode;
+  a.refine_max = opts->refine_max;
+  a.refine_tol = opts->refine_tol;
+  a.counter = (int*)workspace + 1;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (g->impl.h.kind == DNLS_SE3) return launch_persistent(k_backward<3>, g, opts, a, st, false);
+  return launch_persistent(k_backward<2>, g, opts, a, st, false);
+}
+
+dnls_status dnls_graph_linearize(const dnls_graph* g, const dnls_solver_opts* opts,
+                                 const dnls_graph_inputs* in, const double* theta,
+                                 double* H_dense, double* grad, double* S, void* workspace,
+                                 size_t workspace_bytes, void* stream) {
+  if (!g || !in || !theta || !in->meas || !in->wdiag) return DNLS_ERR_ARG;
+  if (opts && check_opts(opts) != DNLS_OK) return DNLS_ERR_ARG;
+  dnls_status s = check_ws(g, workspace, workspace_bytes);
+  if (s != DNLS_OK) return s;
+  KArgs a = base_args(g, in, workspace);
+  a.theta = const_cast<double*>(theta);
+  a.H_dense = H_dense;
+  a.grad = grad;
+  a.S_out = S;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int threads = g->impl.h.dof == 6 ? 256 : 128;
+  if (g->impl.h.kind == DNLS_SE3)
+    k_linearize<3><<<g->impl.h.B, threads, 0, st>>>(a);
+  else
+    k_linearize<2><<<g->impl.h.B, threads, 0, st>>>(a);
+  return cuda_status(cudaGetLastError());
+}
+
+dnls_status dnls_graph_get_stats(const dnls_graph* g, dnls_graph_stats* out) {
+  if (!g || !out) return DNLS_ERR_ARG;
+  const GraphHost& h = g->impl.h;
+  out->n_poses = h.P_total;
+  out->n_costs = h.E_total;
+  out->n_blocks_L = h.n_blocks_L;
+  out->n_block_updates = h.n_upd;
+  out->n_levels_max = h.max_nlev;
+  out->factor_flops = h.factor_flops;
+  out->dense_flops = h.dense_flops;
+  return DNLS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,383 @@
+// Host-side symbolic analysis of a batch of pose graphs (done once per structure and reused by
+// every numeric factorization, as the paper's sparse solvers do, Sec. 4.2 and App. E):
+//   1. a fill-reducing ordering of the pose blocks (minimum degree on the pose graph, ties to
+//      the lowest index; or the natural order);
+//   2. the block structure of the Cholesky factor L by symbolic elimination;
+//   3. the elimination-tree level of every block column (a column depends only on its
+//      descendants, so all columns of one level can be factored concurrently);
+//   4. for every block of L, the list of (L(r,j), L(k,j)) products a left-looking
+//      factorization subtracts from it, so that each block is reduced by one thread group in a
+//      fixed order (no atomics, bitwise reproducible);
+//   5. the assembly maps from costs to the blocks of H and the workspace plan.
+#include <algorithm>
+#include <cstring>
+#include <map>
+
+#include "../../include/dnls.h"
+#include "dnls_graph.h"
+
+namespace dnls {
+
+namespace {
+
+struct Bits {
+  int words = 0;
+  std::vector<uint64_t> w;
+  void init(int n) { words = (n + 63) / 64; w.assign((size_t)words, 0); }
+  void set(int i) { w[i >> 6] |= (uint64_t)1 << (i & 63); }
+  void clr(int i) { w[i >> 6] &= ~((uint64_t)1 << (i & 63)); }
+  bool get(int i) const { return (w[i >> 6] >> (i & 63)) & 1; }
+};
+
+int popcount_and(const Bits& a, const Bits& b) {
+  int c = 0;
+  for (int k = 0; k < a.words; ++k) c += __builtin_popcountll(a.w[k] & b.w[k]);
+  return c;
+}
+
+// Eliminates the pose graph in the chosen order; returns the elimination order (position ->
+// pose) and, per position, the poses adjacent at elimination time (the column structure).
+void eliminate(int N, const std::vector<std::vector<int>>& adj0, bool min_degree,
+               std::vector<int>& order, std::vector<std::vector<int>>& struct_poses) {
+  std::vector<Bits> adj(N);
+  for (int v = 0; v < N; ++v) {
+    adj[v].init(N);
+    for (int u : adj0[v]) adj[v].set(u);
+  }
+  Bits alive;
+  alive.init(N);
+  for (int v = 0; v < N; ++v) alive.set(v);
+  std::vector<int> deg(N);
+  for (int v = 0; v < N; ++v) deg[v] = (int)adj0[v].size();
+  order.clear();
+  struct_poses.assign(N, {});
+  for (int step = 0; step < N; ++step) {
+    int k = -1;
+    if (min_degree) {
+      int best = 1 << 30;
+      for (int v = 0; v < N; ++v)
+        if (alive.get(v) && deg[v] < best) { best = deg[v]; k = v; }
+    } else {
+      k = step;
+    }
+    order.push_back(k);
+    alive.clr(k);
+    std::vector<int> nb;
+    for (int wd = 0; wd < adj[k].words; ++wd) {
+      uint64_t m = adj[k].w[wd] & alive.w[wd];
+      while (m) {
+        int bit = __builtin_ctzll(m);
+        nb.push_back(wd * 64 + bit);
+        m &= m - 1;
+      }
+    }
+    struct_poses[step] = nb;
+    for (int x : nb) {
+      for (int wd = 0; wd < adj[x].words; ++wd) adj[x].w[wd] |= adj[k].w[wd] & alive.w[wd];
+      adj[x].clr(x);
+      adj[x].clr(k);
+    }
+    for (int x : nb) deg[x] = popcount_and(adj[x], alive);
+  }
+}
+
+int64_t align256(int64_t x) { return (x + 255) & ~(int64_t)255; }
+
+}  // namespace
+
+int build_graph_host(int kind, int B, const int64_t* pose_offsets, const int64_t* edge_offsets,
+                     const int32_t* edge_i, const int32_t* edge_j, int ordering, GraphHost* out) {
+  if (!out || !pose_offsets || !edge_offsets || !edge_i || !edge_j) return DNLS_ERR_ARG;
+  if ((kind != DNLS_SE2 && kind != DNLS_SE3) || B < 1) return DNLS_ERR_ARG;
+  if (ordering != DNLS_ORDER_MIN_DEGREE && ordering != DNLS_ORDER_NATURAL) return DNLS_ERR_ARG;
+  if (pose_offsets[0] != 0 || edge_offsets[0] != 0) return DNLS_ERR_ARG;
+  GraphHost& G = *out;
+  G.kind = kind;
+  G.dof = kind == DNLS_SE3 ? 6 : 3;
+  G.pw = kind == DNLS_SE3 ? 12 : 4;
+  G.B = B;
+  G.P_total = pose_offsets[B];
+  G.E_total = edge_offsets[B];
+  const int D = G.dof, BS = D * D;
+  G.meta.assign(B, ProbMeta{});
+  G.sym.clear();
+  G.ei.assign(edge_i, edge_i + G.E_total);
+  G.ej.assign(edge_j, edge_j + G.E_total);
+  G.max_L_bytes = 0;
+  G.max_nlev = 0;
+  G.n_blocks_L = 0;
+  G.n_upd = 0;
+  G.factor_flops = 0;
+  G.dense_flops = 0;
+  int64_t ws = kWsHeader;
+  int64_t dense_off = 0;
+  std::vector<double> cost(B);
+
+  for (int b = 0; b < B; ++b) {
+    const int64_t p0 = pose_offsets[b], p1 = pose_offsets[b + 1];
+    const int64_t e0 = edge_offsets[b], e1 = edge_offsets[b + 1];
+    if (p1 <= p0 || e1 < e0) return DNLS_ERR_ARG;
+    if (p1 - p0 > (1 << 20) || e1 - e0 > (1 << 24)) return DNLS_ERR_ARG;
+    const int N = (int)(p1 - p0), E = (int)(e1 - e0);
+    std::vector<std::vector<int>> adj(N);
+    for (int e = 0; e < E; ++e) {
+      int i = edge_i[e0 + e], j = edge_j[e0 + e];
+      if (i < 0 || i >= N || j < -1 || j >= N || j == i) return DNLS_ERR_ARG;
+      if (j >= 0) {
+        adj[i].push_back(j);
+        adj[j].push_back(i);
+      }
+    }
+    for (auto& a : adj) {
+      std::sort(a.begin(), a.end());
+      a.erase(std::unique(a.begin(), a.end()), a.end());
+    }
+    std::vector<int> perm;
+    std::vector<std::vector<int>> spose;
+    eliminate(N, adj, ordering == DNLS_ORDER_MIN_DEGREE, perm, spose);
+    std::vector<int> iperm(N);
+    for (int k = 0; k < N; ++k) iperm[perm[k]] = k;
+
+    // column structure in positions
+    std::vector<std::vector<int>> rows(N);
+    for (int k = 0; k < N; ++k) {
+      for (int v : spose[k]) rows[k].push_back(iperm[v]);
+      std::sort(rows[k].begin(), rows[k].end());
+    }
+    std::vector<int> colptr(N + 1, 0);
+    for (int k = 0; k < N; ++k) colptr[k + 1] = colptr[k] + (int)rows[k].size();
+    const int nnzL = colptr[N];
+    auto blk = [&](int r, int c) -> int {  // block id of L(r, c), r >= c
+      if (r == c) return c;
+      auto it = std::lower_bound(rows[c].begin(), rows[c].end(), r);
+      if (it == rows[c].end() || *it != r) return -1;
+      return N + colptr[c] + (int)(it - rows[c].begin());
+    };
+    // row structure: for each k, (block L(k, j), j) for j < k
+    std::vector<std::vector<std::pair<int, int>>> rowl(N);
+    for (int j = 0; j < N; ++j)
+      for (int a = 0; a < (int)rows[j].size(); ++a)
+        rowl[rows[j][a]].push_back({N + colptr[j] + a, j});
+    // levels (height above the leaves of the elimination tree)
+    std::vector<int> lev(N, 0);
+    for (int k = 0; k < N; ++k)
+      if (!rows[k].empty()) lev[rows[k][0]] = std::max(lev[rows[k][0]], lev[k] + 1);
+    int nlev = 0;
+    for (int k = 0; k < N; ++k) nlev = std::max(nlev, lev[k] + 1);
+    std::vector<std::vector<int>> bylev(nlev);
+    for (int k = 0; k < N; ++k) bylev[lev[k]].push_back(k);
+    // gather lists: per target block of column k, the (L(r,j), L(k,j)) pairs, j in rowl[k]
+    std::vector<std::vector<std::vector<int>>> gl(N);  // gl[k][t] flat pairs, t=0 diag, 1+a off
+    int64_t n_upd = 0;
+    for (int k = 0; k < N; ++k) {
+      gl[k].assign(1 + rows[k].size(), {});
+      for (auto& pr : rowl[k]) {
+        const int bkj = pr.first, j = pr.second;
+        auto it = std::lower_bound(rows[j].begin(), rows[j].end(), k);
+        for (; it != rows[j].end(); ++it) {
+          const int r = *it;
+          const int a_src = N + colptr[j] + (int)(it - rows[j].begin());
+          int t;
+          if (r == k) {
+            t = 0;
+          } else {
+            auto jt = std::lower_bound(rows[k].begin(), rows[k].end(), r);
+            if (jt == rows[k].end() || *jt != r) return DNLS_ERR_ARG;  // cannot happen (closure)
+            t = 1 + (int)(jt - rows[k].begin());
+          }
+          gl[k][t].push_back(a_src);
+          gl[k][t].push_back(bkj);
+          ++n_upd;
+        }
+      }
+    }
+    // assembly maps
+    std::vector<std::vector<int>> inc(N);
+    std::map<int, int> pair_of_blk;
+    std::vector<std::vector<int>> pairl;
+    std::vector<int> pairtgt;
+    for (int e = 0; e < E; ++e) {
+      int i = edge_i[e0 + e], j = edge_j[e0 + e];
+      inc[iperm[i]].push_back(e << 1);
+      if (j >= 0) {
+        inc[iperm[j]].push_back((e << 1) | 1);
+        int pi = iperm[i], pj = iperm[j];
+        int R = std::max(pi, pj), C = std::min(pi, pj);
+        int id = blk(R, C);
+        if (id < 0) return DNLS_ERR_ARG;
+        auto f = pair_of_blk.find(id);
+        int p;
+        if (f == pair_of_blk.end()) {
+          p = (int)pairl.size();
+          pair_of_blk[id] = p;
+          pairl.push_back({});
+          pairtgt.push_back(id);
+        } else {
+          p = f->second;
+        }
+        pairl[p].push_back((e << 1) | (pi > pj ? 0 : 1));
+      }
+    }
+    const int npair = (int)pairl.size();
+
+    // ---- blob
+    ProbMeta& m = G.meta[b];
+    m.N = N;
+    m.E = E;
+    m.npair = npair;
+    m.nnzL = nnzL;
+    m.nlev = nlev;
+    m.n_upd = (int32_t)n_upd;
+    m.pose_off = p0;
+    m.edge_off = e0;
+    m.sym = (int64_t)G.sym.size();
+    m.dense_off = dense_off;
+    dense_off += (int64_t)N * D * N * D;
+    std::vector<int32_t> blob;
+    auto mark = [&]() { return (int32_t)blob.size(); };
+    m.o_perm = mark();
+    blob.insert(blob.end(), perm.begin(), perm.end());
+    m.o_iperm = mark();
+    blob.insert(blob.end(), iperm.begin(), iperm.end());
+    m.o_colptr = mark();
+    blob.insert(blob.end(), colptr.begin(), colptr.end());
+    m.o_rows = mark();
+    for (int k = 0; k < N; ++k) blob.insert(blob.end(), rows[k].begin(), rows[k].end());
+    m.o_rowptr = mark();
+    {
+      int acc = 0;
+      for (int k = 0; k < N; ++k) {
+        blob.push_back(acc);
+        acc += (int)rowl[k].size();
+      }
+      blob.push_back(acc);
+    }
+    m.o_rowent = mark();
+    for (int k = 0; k < N; ++k)
+      for (auto& pr : rowl[k]) {
+        blob.push_back(pr.first);
+        blob.push_back(pr.second);
+      }
+    m.o_lvlptr = mark();
+    {
+      int acc = 0;
+      for (int l = 0; l < nlev; ++l) {
+        blob.push_back(acc);
+        acc += (int)bylev[l].size();
+      }
+      blob.push_back(acc);
+    }
+    m.o_lvlcols = mark();
+    for (int l = 0; l < nlev; ++l) blob.insert(blob.end(), bylev[l].begin(), bylev[l].end());
+    // targets by level with their gather ranges
+    std::vector<int> tgt, gptr, gsrc, tgtptr, pan, panptr;
+    for (int l = 0; l < nlev; ++l) {
+      tgtptr.push_back((int)tgt.size());
+      panptr.push_back((int)pan.size() / 2);
+      for (int k : bylev[l]) {
+        for (int t = 0; t <= (int)rows[k].size(); ++t) {
+          tgt.push_back(t == 0 ? k : N + colptr[k] + t - 1);
+          gptr.push_back((int)gsrc.size() / 2);
+          gsrc.insert(gsrc.end(), gl[k][t].begin(), gl[k][t].end());
+        }
+        for (int a = 0; a < (int)rows[k].size(); ++a) {
+          pan.push_back(N + colptr[k] + a);
+          pan.push_back(k);
+        }
+      }
+    }
+    tgtptr.push_back((int)tgt.size());
+    panptr.push_back((int)pan.size() / 2);
+    gptr.push_back((int)gsrc.size() / 2);
+    m.o_tgtptr = mark();
+    blob.insert(blob.end(), tgtptr.begin(), tgtptr.end());
+    m.o_tgt = mark();
+    blob.insert(blob.end(), tgt.begin(), tgt.end());
+    m.o_gptr = mark();
+    blob.insert(blob.end(), gptr.begin(), gptr.end());
+    m.o_gsrc = mark();
+    blob.insert(blob.end(), gsrc.begin(), gsrc.end());
+    m.o_panptr = mark();
+    blob.insert(blob.end(), panptr.begin(), panptr.end());
+    m.o_pan = mark();
+    blob.insert(blob.end(), pan.begin(), pan.end());
+    m.o_incptr = mark();
+    {
+      int acc = 0;
+      for (int k = 0; k < N; ++k) {
+        blob.push_back(acc);
+        acc += (int)inc[k].size();
+      }
+      blob.push_back(acc);
+    }
+    m.o_inc = mark();
+    for (int k = 0; k < N; ++k) blob.insert(blob.end(), inc[k].begin(), inc[k].end());
+    m.o_pairptr = mark();
+    {
+      int acc = 0;
+      for (int p = 0; p < npair; ++p) {
+        blob.push_back(acc);
+        acc += (int)pairl[p].size();
+      }
+      blob.push_back(acc);
+    }
+    m.o_pairs = mark();
+    for (int p = 0; p < npair; ++p) blob.insert(blob.end(), pairl[p].begin(), pairl[p].end());
+    m.o_pairtgt = mark();
+    blob.insert(blob.end(), pairtgt.begin(), pairtgt.end());
+    m.o_lsrc = mark();
+    {
+      std::vector<int32_t> lsrc(nnzL, -1);
+      for (int p = 0; p < npair; ++p) lsrc[pairtgt[p] - N] = p;
+      blob.insert(blob.end(), lsrc.begin(), lsrc.end());
+    }
+    blob.push_back(0);  // keep every section non-empty-addressable
+    G.sym.insert(G.sym.end(), blob.begin(), blob.end());
+
+    // ---- workspace plan (layout independent of the options)
+    const int64_t n = (int64_t)N * D;
+    const int64_t JW = 2 * BS + D;  // per cost: r, J_i, J_j
+    int64_t off = 0;
+    auto take = [&](int64_t bytes) {
+      int64_t o = off;
+      off = align256(off + bytes);
+      return (int32_t)o;
+    };
+    m.w_H = take((int64_t)(N + npair) * BS * 8);
+    m.L_bytes = (int32_t)((int64_t)(N + nnzL) * BS * 8);
+    m.w_L = take(m.L_bytes);
+    m.w_Linv = take((int64_t)N * BS * 8);
+    m.w_g = take(n * 8);
+    m.w_dx = take(n * 8);
+    m.w_tmp = take(n * 8);
+    m.w_thc = take((int64_t)N * G.pw * 8);
+    m.w_J = take((int64_t)E * JW * 8);
+    m.w_bx = take(n * 8);
+    m.w_bv = take(n * 8);
+    m.w_br = take(n * 8);
+    m.w_bhx = take(n * 8);
+    m.w_ebuf = take((int64_t)E * 4 * D * 8);
+    m.w_state = take(64);
+    if (off > ((int64_t)1 << 31) - 1) return DNLS_ERR_ARG;
+    m.ws = ws;
+    ws += off;
+
+    G.max_L_bytes = std::max(G.max_L_bytes, m.L_bytes);
+    G.max_nlev = std::max(G.max_nlev, nlev);
+    G.n_blocks_L += N + nnzL;
+    G.n_upd += n_upd;
+    const double D3 = (double)D * D * D;
+    const double ff = 2.0 * n_upd * D3 + (double)nnzL * D * D * (D + 1) + N * (2.0 * D3 / 3.0);
+    G.factor_flops += ff;
+    G.dense_flops += (double)n * n * n / 3.0;
+    cost[b] = ff + 200.0 * E;
+  }
+  G.ws_bytes = ws;
+  G.order.resize(B);
+  for (int b = 0; b < B; ++b) G.order[b] = b;
+  std::stable_sort(G.order.begin(), G.order.end(),
+                   [&](int a, int c) { return cost[a] > cost[c]; });
+  return DNLS_OK;
+}
+
+}  // namespace dnls
