@@ -153,6 +153,28 @@ dnls_status dnls_graph_backward(const dnls_graph* g, const dnls_solver_opts* opt
                                 void* workspace, size_t workspace_bytes, void* stream,
                                 dnls_info* info);
 
+/* Forward without any device allocation, for callers that are not allowed to allocate device
+ * memory when they solve: for example a host application whose memory manager has reserved the
+ * GPU's memory up front and forbids other allocators, or a control loop that cannot afford the
+ * device-wide synchronisation and unbounded latency of cudaMalloc in its cycle.  (The paper has
+ * no counterpart; this is a deployment convenience.)
+ * Same computation and arguments as dnls_graph_forward, except that the scratch memory lives
+ * in a fixed array inside libdnls of DNLS_NOALLOC_SCRATCH_BYTES (16 MiB), which every GPU that
+ * loads the library keeps reserved until the process exits; no workspace is passed.
+ *   - Batches whose dnls_graph_workspace_size exceeds DNLS_NOALLOC_SCRATCH_BYTES are rejected
+ *     with DNLS_ERR_WORKSPACE before anything is launched.
+ *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ *     with that device current; make that first call before any stream capture.
+ *   - Every call on a device shares the one array and leaves its contents behind (including the
+ *     cached factorization); the work counter it needs zeroed is cleared by each call.  Calls
+ *     whose executions overlap on the GPU (other streams, other host threads) race on the array
+ *     and must be serialised by the caller.  dnls_graph_backward cannot use this scratch.
+ *   - Errors: DNLS_ERR_ARG, DNLS_ERR_WORKSPACE (batch too large), DNLS_ERR_CUDA. */
+#define DNLS_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
+dnls_status dnls_graph_forward_noalloc(const dnls_graph* g, const dnls_solver_opts* opts,
+                                       const dnls_graph_inputs* in, double* theta, void* stream,
+                                       dnls_info* info);
+
 /* Linearise and assemble at theta without solving (for inspection and tests): writes the
  * undamped Gauss-Newton matrix H = J^T J (device, one dense n_b x n_b row-major block per
  * problem, packed one after another, n_b = dof * poses of b, in the caller's pose order),

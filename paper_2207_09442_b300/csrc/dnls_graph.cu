@@ -17,6 +17,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "../../include/dnls.h"
@@ -1089,3 +1090,63 @@ dnls_status dnls_graph_get_stats(const dnls_graph* g, dnls_graph_stats* out) {
 }
 
 }  // extern "C"
+
+// ----------------------------------------------------------------------------- no-allocation forward
+// Scratch for dnls_graph_forward_noalloc: a fixed array in the library's device image, so that
+// callers who may not allocate device memory can still run the forward.  Every GPU that loads
+// libdnls reserves it until the process exits.  Host code must not use the symbol itself as a
+// device pointer (on the host it names a host-side stand-in); the device address is obtained with
+// cudaGetSymbolAddress once per device, below.
+static __device__ __align__(256) unsigned char dnls_noalloc_scratch[DNLS_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kMaxDevices] = {nullptr};
+
+// Device address of the scratch array on the current device (looked up on the first call per
+// device, with that device current).
+dnls_status noalloc_scratch(void** out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return DNLS_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, dnls_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      cudaGetLastError();
+      return DNLS_ERR_CUDA;
+    }
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return DNLS_OK;
+}
+
+}  // namespace
+
+extern "C" dnls_status dnls_graph_forward_noalloc(const dnls_graph* g, const dnls_solver_opts* opts,
+                                                  const dnls_graph_inputs* in, double* theta,
+                                                  void* stream, dnls_info* info) {
+  if (!g || !in || !theta || !in->meas || !in->wdiag) return DNLS_ERR_ARG;
+  dnls_status s = check_opts(opts);
+  if (s != DNLS_OK) return s;
+  if (g->impl.h.ws_bytes > (int64_t)DNLS_NOALLOC_SCRATCH_BYTES) return DNLS_ERR_WORKSPACE;
+  void* scratch = nullptr;
+  if ((s = noalloc_scratch(&scratch)) != DNLS_OK) return s;
+  KArgs a = base_args(g, in, scratch);  // the work counter is cleared by the launch below
+  a.theta = theta;
+  a.info = info;
+  a.algo = opts->algo;
+  a.iters = opts->iters;
+  a.lam0 = opts->lambda0;
+  a.tau = opts->tau;
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool mixed = opts->precision == DNLS_MIXED_FP32;
+  if (g->impl.h.kind == DNLS_SE3)
+    return mixed ? launch_persistent(k_forward<3, float>, g, opts, a, st, true)
+                 : launch_persistent(k_forward<3, double>, g, opts, a, st, true);
+  return mixed ? launch_persistent(k_forward<2, float>, g, opts, a, st, true)
+               : launch_persistent(k_forward<2, double>, g, opts, a, st, true);
+}
