@@ -41,6 +41,8 @@ def _args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip baselines (for profiling)")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="first N problems only (profiling captures); default: the full workload")
     return ap.parse_args()
 
 
@@ -170,19 +172,23 @@ def main():
     if world > 1:
         dist.barrier()
 
-    batch = synth.workload(WORKLOAD)  # every rank solves its own 256-problem batch (weak scaling)
+    # every rank solves its own 256-problem batch (weak scaling)
+    batch = synth.workload(WORKLOAD, batch=args.batch or None)
     B = batch.batch
     st = layer.PoseGraphStructure.from_batch(batch)
     stats = st.stats()
     opts = layer.Options(algo="lm", iters=ITERS, precision="mixed_fp32", tau=0.0,
                          backward_mode="implicit")
-    solver = layer.PoseGraphSolver(st, opts, dev)
     t64 = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
     theta0 = t64(batch.theta_init)
     meas, wd = t64(batch.meas), t64(batch.wdiag)
     lw = torch.as_tensor(batch.logw, dtype=torch.float32, device=dev)
     rng = np.random.default_rng(1234)
     v = t64(rng.normal(size=(st.n_poses, 6)) * 1e-2)  # synthetic outer-loss tangent gradient
+    from paper_2207_09442_b300 import autotune
+    tuned = autotune.tune(st, opts, (theta0, meas, wd, lw), v, use_cache=False)
+    opts = autotune.apply(opts, tuned)
+    solver = layer.PoseGraphSolver(st, opts, dev)
     theta = torch.empty_like(theta0)
     gm = torch.empty(st.n_costs, 6, dtype=torch.float64, device=dev)
     gl = torch.empty(st.n_costs, dtype=torch.float64, device=dev)
@@ -199,8 +205,8 @@ def main():
         ev_mid = torch.cuda.Event(enable_timing=True)
         step()
     torch.cuda.synchronize()
-    info = solver.info_dict()
-    executed = int(info["iterations"].sum())
+    info_b = solver.info_dict()
+    executed = int(info_b["iterations"].sum())
 
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     mids = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -245,6 +251,10 @@ def main():
                       "parallelism": f"{world} GPU(s), batch sharded (weak)", "l2": "flushed between steps"},
            "fwd_ms": statistics.mean(fwd_ms), "bwd_ms": statistics.mean(a - b for a, b in zip(step_ms, fwd_ms)),
            "executed_lm_iterations_per_step": executed, "gpu_launches": 2 * args.steps,
+           "launch_shape": {k: tuned[k] for k in ("threads", "ctas_per_sm", "smem_factor")},
+           "autotune_table": tuned["table"],
+           "backward_refine_steps_mean": float(np.mean(info_b["refine_steps"])),
+           "backward_not_converged": int((info_b["status"] == 1).sum()),
            "clocks": clocks}
 
     if not args.no_extras:

@@ -1,0 +1,99 @@
+"""Launch-shape autotuner for the persistent pose-graph kernels.
+
+The numeric work does not depend on the launch shape; only speed does.  The tuner times the
+forward (and backward) of the caller's own batch for each candidate (threads per CTA, resident
+CTAs per SM, shared-memory staging of the factor) and keeps the fastest, caching it in a JSON file
+keyed by group, precision, a bucket of the largest pose count and the batch size, and the GPU.
+Launch shapes the GPU cannot run (too many registers or too much shared memory for the requested
+residency) fail at launch and are skipped.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+import time
+from typing import Optional
+
+import torch
+
+from . import dnls as _d
+from . import layer
+
+CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned_launch.json")
+CANDIDATES = [(256, 1, 1), (256, 1, 0), (128, 2, 0), (128, 2, 1), (128, 1, 1), (256, 2, 0),
+              (128, 3, 0), (128, 4, 0)]
+
+
+def _key(st: layer.PoseGraphStructure, opts: layer.Options) -> str:
+    sizes = st.pose_offsets[1:] - st.pose_offsets[:-1]
+    nb = int(2 ** math.ceil(math.log2(max(2, int(sizes.max())))))
+    bb = int(2 ** math.ceil(math.log2(max(1, st.batch))))
+    dev = torch.cuda.get_device_properties(torch.cuda.current_device())
+    return f"{st.kind}|{opts.precision}|{opts.backward_mode}|n<={nb}|B<={bb}|{dev.name}|{dev.multi_processor_count}"
+
+
+def _load() -> dict:
+    try:
+        with open(CACHE) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def tune(st: layer.PoseGraphStructure, opts: layer.Options, inputs, v: Optional[torch.Tensor] = None,
+         reps: int = 2, use_cache: bool = True, candidates=None) -> dict:
+    """Returns {"threads", "ctas_per_sm", "smem_factor", "ms", "table"} for this batch.
+
+    ``inputs`` = (theta0, meas, wdiag, logw) on the device; with ``v`` the backward is timed too."""
+    key = _key(st, opts)
+    cache = _load()
+    if use_cache and key in cache:
+        return cache[key]
+    table = []
+    theta0, meas, wd, lw = inputs
+    stream = torch.cuda.current_stream()
+    for thr, ctas, smem in (candidates or CANDIDATES):
+        o = layer.Options(**{**opts.__dict__, "threads": thr, "ctas_per_sm": ctas, "smem_factor": smem})
+        try:
+            sol = layer.PoseGraphSolver(st, o, theta0.device)
+            th = sol.forward(theta0, meas, wd, lw)
+            if v is not None:
+                sol.backward(th, v, meas, wd, lw)
+            torch.cuda.synchronize()
+            best = float("inf")
+            for _ in range(reps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                th = sol.forward(theta0, meas, wd, lw)
+                if v is not None:
+                    sol.backward(th, v, meas, wd, lw)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                best = min(best, e0.elapsed_time(e1))
+            table.append({"threads": thr, "ctas_per_sm": ctas, "smem_factor": smem, "ms": best})
+            del sol
+        except _d.DnlsError as err:
+            table.append({"threads": thr, "ctas_per_sm": ctas, "smem_factor": smem,
+                          "ms": None, "error": str(err)})
+            torch.cuda.synchronize()
+    ok = [r for r in table if r["ms"] is not None]
+    if not ok:
+        raise RuntimeError(f"no launch shape ran: {table}")
+    win = min(ok, key=lambda r: r["ms"])
+    out = {"threads": win["threads"], "ctas_per_sm": win["ctas_per_sm"],
+           "smem_factor": win["smem_factor"], "ms": win["ms"], "table": table,
+           "tuned_at": time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime())}
+    cache[key] = out
+    try:
+        with open(CACHE, "w") as f:
+            json.dump(cache, f, indent=1, sort_keys=True)
+    except OSError:
+        pass
+    return out
+
+
+def apply(opts: layer.Options, tuned: dict) -> layer.Options:
+    return layer.Options(**{**opts.__dict__, "threads": tuned["threads"],
+                            "ctas_per_sm": tuned["ctas_per_sm"], "smem_factor": tuned["smem_factor"]})

@@ -27,6 +27,7 @@
 namespace dnls {
 
 constexpr double kLamMin = 1e-12, kLamMax = 1e12, kDiagFloor = 1e-9;
+constexpr double kRefactorLambda = 1e-6;  // backward refactors when the cached damping exceeds this
 
 struct GraphDev {
   const ProbMeta* meta;
@@ -54,7 +55,7 @@ struct KArgs {
   dnls_info* info;
   int algo, iters, mode, refine_max;
   double lam0, tau, refine_tol;
-  int smem_L;           // bytes of dynamic shared memory available for a factor (0 = none)
+  int smem_bytes;       // dynamic shared memory per CTA for staging (0 = none)
 };
 
 // ----------------------------------------------------------------------------- helpers
@@ -81,19 +82,72 @@ struct Prob {
   const double *meas, *wdiag;
   const float* logw;
   double* theta;
-  double *H, *L, *Lg, *Linv, *g, *dx, *tmp, *thc, *bx, *bv, *br, *bhx, *ebuf;
+  double *H, *L, *Lg, *Linv, *g, *dx, *tmp, *thc, *bx, *bv, *br, *bhx, *ebuf, *W;
   void* J;
   ProbState* st;
   const ProbMeta* m;
 
-  __device__ void init(const KArgs& a, int b, double* smemL) {
+  int stage;           // 0: nothing staged; 1: blob + L; 2: + dx, tmp; 3: + L^-1
+  const int32_t* gsym;  // the problem's symbolic blob in global memory
+  double *Lg_inv, *dxg, *tmpg;
+
+  // Points every array at its global copy, then re-points the factor, its inverse diagonal
+  // blocks, the solve vectors and the symbolic blob at shared memory when `smem` can hold them
+  // (in that order of priority).  stage_in() must run before they are used.
+  __device__ void init(const KArgs& a, int b, char* smem, int smem_bytes) {
     m = a.g.meta + b;
     N = m->N;
     E = m->E;
     npair = m->npair;
     nnzL = m->nnzL;
     nlev = m->nlev;
-    const int32_t* s = a.g.sym + m->sym;
+    gsym = a.g.sym + m->sym;
+    ei = a.g.ei + m->edge_off;
+    ej = a.g.ej + m->edge_off;
+    meas = a.meas + m->edge_off * PW;
+    wdiag = a.wdiag + m->edge_off * D;
+    logw = a.logw ? a.logw + m->edge_off : nullptr;
+    theta = a.theta + m->pose_off * PW;
+    char* w = a.ws + m->ws;
+    H = (double*)(w + m->w_H);
+    Lg = (double*)(w + m->w_L);
+    L = Lg;
+    Lg_inv = (double*)(w + m->w_Linv);
+    Linv = Lg_inv;
+    g = (double*)(w + m->w_g);
+    dxg = (double*)(w + m->w_dx);
+    tmpg = (double*)(w + m->w_tmp);
+    dx = dxg;
+    tmp = tmpg;
+    thc = (double*)(w + m->w_thc);
+    J = (void*)(w + m->w_J);
+    bx = (double*)(w + m->w_bx);
+    bv = (double*)(w + m->w_bv);
+    br = (double*)(w + m->w_br);
+    bhx = (double*)(w + m->w_bhx);
+    ebuf = (double*)(w + m->w_ebuf);
+    st = (ProbState*)(w + m->w_state);
+    W = (double*)(w + m->w_W);
+    const int32_t* s = gsym;
+    stage = 0;
+    if (smem) {
+      const int a_blob = (m->blob_len * 4 + 15) & ~15;
+      const int a_L = (m->L_bytes + 15) & ~15;
+      const int a_vec = (N * D * 8 + 15) & ~15;
+      const int a_inv = (N * BS * 8 + 15) & ~15;
+      if (a_blob + a_L + 2 * a_vec + a_inv <= smem_bytes) stage = 3;
+      else if (a_blob + a_L + 2 * a_vec <= smem_bytes) stage = 2;
+      else if (a_blob + a_L <= smem_bytes) stage = 1;
+      if (stage >= 1) {
+        s = (const int32_t*)smem;
+        L = (double*)(smem + a_blob);
+      }
+      if (stage >= 2) {
+        dx = (double*)(smem + a_blob + a_L);
+        tmp = (double*)(smem + a_blob + a_L + a_vec);
+      }
+      if (stage >= 3) Linv = (double*)(smem + a_blob + a_L + 2 * a_vec);
+    }
     perm = s + m->o_perm;
     iperm = s + m->o_iperm;
     colptr = s + m->o_colptr;
@@ -114,34 +168,46 @@ struct Prob {
     pairs = s + m->o_pairs;
     pairtgt = s + m->o_pairtgt;
     lsrc = s + m->o_lsrc;
-    ei = a.g.ei + m->edge_off;
-    ej = a.g.ej + m->edge_off;
-    meas = a.meas + m->edge_off * PW;
-    wdiag = a.wdiag + m->edge_off * D;
-    logw = a.logw ? a.logw + m->edge_off : nullptr;
-    theta = a.theta + m->pose_off * PW;
-    char* w = a.ws + m->ws;
-    H = (double*)(w + m->w_H);
-    Lg = (double*)(w + m->w_L);
-    L = (smemL && m->L_bytes <= a.smem_L) ? smemL : Lg;
-    Linv = (double*)(w + m->w_Linv);
-    g = (double*)(w + m->w_g);
-    dx = (double*)(w + m->w_dx);
-    tmp = (double*)(w + m->w_tmp);
-    thc = (double*)(w + m->w_thc);
-    J = (void*)(w + m->w_J);
-    bx = (double*)(w + m->w_bx);
-    bv = (double*)(w + m->w_bv);
-    br = (double*)(w + m->w_br);
-    bhx = (double*)(w + m->w_bhx);
-    ebuf = (double*)(w + m->w_ebuf);
-    st = (ProbState*)(w + m->w_state);
   }
 
+  // Copies the symbolic blob (and, with `factor`, the cached factor) into shared memory.
+  __device__ void stage_in(bool factor) {
+    if (stage >= 1) {
+      const int4* src = (const int4*)gsym;
+      int4* dst = (int4*)(perm - m->o_perm);  // start of the staged blob
+      for (int k = threadIdx.x; k < m->blob_len / 4; k += blockDim.x) dst[k] = src[k];
+      if (factor) {
+        const int nb = (N + nnzL) * BS;
+        for (int k = threadIdx.x; k < nb; k += blockDim.x) L[k] = Lg[k];
+        if (stage >= 3)
+          for (int k = threadIdx.x; k < N * BS; k += blockDim.x) Linv[k] = Lg_inv[k];
+      }
+    }
+    __syncthreads();
+  }
+
+  // Writes a shared-memory factor back to the workspace (the backward reads it there).
+  __device__ void stage_out_factor() {
+    if (stage >= 1) {
+      const int nb = (N + nnzL) * BS;
+      for (int k = threadIdx.x; k < nb; k += blockDim.x) Lg[k] = L[k];
+      if (stage >= 3)
+        for (int k = threadIdx.x; k < N * BS; k += blockDim.x) Lg_inv[k] = Linv[k];
+    }
+  }
+
+  // w_e = exp(l_e) d_e, computed once per solve into W (one FP64 exp per cost instead of one
+  // per cost evaluation); prepare_weights() must have run.
   __device__ __forceinline__ void weight(int e, double* w) const {
-    const double s = logw ? exp((double)logw[e]) : 1.0;
 #pragma unroll
-    for (int a = 0; a < D; ++a) w[a] = s * wdiag[e * D + a];
+    for (int a = 0; a < D; ++a) w[a] = W[e * D + a];
+  }
+  __device__ void prepare_weights() {
+    for (int k = threadIdx.x; k < E * D; k += blockDim.x) {
+      const int e = k / D;
+      W[k] = (logw ? exp((double)logw[e]) : 1.0) * wdiag[k];
+    }
+    __syncthreads();
   }
 };
 
@@ -312,15 +378,17 @@ __device__ bool factor(Prob<KIND>& p, double lam, int* sflag, int gen) {
 #pragma unroll
       for (int e = 0; e < BS; ++e) A[e] = Lk[e];
       bool ok = true;
+      double inv[D];  // reciprocals of the pivots, reused by the inverse below
 #pragma unroll
       for (int jj = 0; jj < D; ++jj) {
         double d = A[jj * D + jj];
 #pragma unroll
         for (int mm = 0; mm < jj; ++mm) d -= A[jj * D + mm] * A[jj * D + mm];
         ok = ok && (d > 0.0) && isfinite(d);
-        const double l = sqrt(fmax(d, 1e-300));
-        const double il = 1.0 / l;
-        A[jj * D + jj] = l;
+        const double dd = fmax(d, 1e-300);
+        const double il = rsqrt(dd);
+        inv[jj] = il;
+        A[jj * D + jj] = dd * il;
 #pragma unroll
         for (int ii = jj + 1; ii < D; ++ii) {
           double s = A[ii * D + jj];
@@ -335,13 +403,13 @@ __device__ bool factor(Prob<KIND>& p, double lam, int* sflag, int gen) {
       for (int e = 0; e < BS; ++e) I[e] = 0.0;
 #pragma unroll
       for (int jj = 0; jj < D; ++jj) {
-        I[jj * D + jj] = 1.0 / A[jj * D + jj];
+        I[jj * D + jj] = inv[jj];
 #pragma unroll
         for (int ii = jj + 1; ii < D; ++ii) {
           double s = 0.0;
 #pragma unroll
           for (int mm = jj; mm < ii; ++mm) s += A[ii * D + mm] * I[mm * D + jj];
-          I[ii * D + jj] = -s / A[ii * D + ii];
+          I[ii * D + jj] = -s * inv[ii];
         }
       }
 #pragma unroll
@@ -458,10 +526,12 @@ __device__ void retract(Prob<KIND>& p, const double* src, const double* delta_po
 
 // ----------------------------------------------------------------------------- forward
 template <int KIND, class P>
-__device__ void forward_problem(const KArgs& a, int b, double* smemL, double* red, int* sflag) {
+__device__ void forward_problem(const KArgs& a, int b, char* smem, double* red, int* sflag) {
   constexpr int D = Group<KIND>::DOF, PW = Group<KIND>::PW;
   Prob<KIND> p;
-  p.init(a, b, smemL);
+  p.init(a, b, smem, a.smem_bytes);
+  p.stage_in(false);
+  p.prepare_weights();
   const int n = p.N * D;
   double S = eval_S<KIND>(p, p.theta, red);
   const double S0 = S;
@@ -518,10 +588,7 @@ __device__ void forward_problem(const KArgs& a, int b, double* smemL, double* re
     }
     if (frozen) break;
   }
-  if (p.L != p.Lg && factor_ok) {  // keep the factor for the backward
-    const int nb = (p.N + p.nnzL) * D * D;
-    for (int k = threadIdx.x; k < nb; k += blockDim.x) p.Lg[k] = p.L[k];
-  }
+  if (factor_ok) p.stage_out_factor();  // keep the factor for the backward
   if (threadIdx.x == 0) {
     p.st->lambda_fact = lam_fact;
     p.st->S = S;
@@ -541,7 +608,7 @@ __device__ void forward_problem(const KArgs& a, int b, double* smemL, double* re
   __syncthreads();
 }
 
-extern __shared__ double dyn_smem[];
+extern __shared__ __align__(16) char dyn_smem[];
 
 // Takes the next problem from the workspace counter (most expensive first).
 __device__ __forceinline__ int next_problem(const KArgs& a, int* slot) {
@@ -561,7 +628,7 @@ __global__ void __launch_bounds__(256) k_forward(KArgs a) {
     if (b < 0) break;
     if (threadIdx.x == 0) sflag = -1;
     __syncthreads();
-    forward_problem<KIND, P>(a, b, a.smem_L ? dyn_smem : nullptr, red, &sflag);
+    forward_problem<KIND, P>(a, b, a.smem_bytes ? dyn_smem : nullptr, red, &sflag);
   }
 }
 
@@ -690,21 +757,25 @@ __device__ void hvp_gn(Prob<KIND>& p, const double* x, double* hx) {
 }
 
 template <int KIND>
-__device__ void backward_problem(const KArgs& a, int b, double* smemL, double* red, int* sflag) {
+__device__ void backward_problem(const KArgs& a, int b, char* smem, double* red, int* sflag) {
   typedef Group<KIND> G;
   constexpr int D = G::DOF, PW = G::PW;
   typedef Dual<double> Dd;
   Prob<KIND> p;
-  p.init(a, b, nullptr);  // the cached factor lives in the workspace
-  (void)smemL;
+  p.init(a, b, smem, a.smem_bytes);
+  // the cached factor comes from the workspace; a factor damped by a large lambda (a problem
+  // that kept rejecting steps after convergence) is replaced by an undamped one at theta*
+  const bool refactor = !p.st->factor_ok || p.st->lambda_fact > kRefactorLambda;
+  p.stage_in(!refactor);
+  p.prepare_weights();
   const int n = p.N * D;
   int status = DNLS_PROBLEM_OK;
   const bool need_J = a.mode == DNLS_IMPLICIT_GN;
-  if (need_J || !p.st->factor_ok) {
+  if (need_J || refactor) {
     lin_costs<KIND, double>(p, p.theta);
     __syncthreads();
   }
-  if (!p.st->factor_ok) {  // no usable cached factor: factor H_GN(theta*) undamped
+  if (refactor) {  // no usable cached factor: factor H_GN(theta*) undamped
     assemble<KIND, double>(p);
     __syncthreads();
     if (!factor<KIND>(p, 0.0, sflag, 0)) status = DNLS_PROBLEM_NOT_SPD;
@@ -812,7 +883,7 @@ __global__ void __launch_bounds__(256) k_backward(KArgs a) {
     if (b < 0) break;
     if (threadIdx.x == 0) sflag = -1;
     __syncthreads();
-    backward_problem<KIND>(a, b, nullptr, red, &sflag);
+    backward_problem<KIND>(a, b, a.smem_bytes ? dyn_smem : nullptr, red, &sflag);
   }
 }
 
@@ -823,7 +894,8 @@ __global__ void __launch_bounds__(256) k_linearize(KArgs a) {
   __shared__ double red[256];
   const int b = blockIdx.x;
   Prob<KIND> p;
-  p.init(a, b, nullptr);
+  p.init(a, b, nullptr, 0);
+  p.prepare_weights();
   const double S = eval_S<KIND>(p, p.theta, red);
   lin_costs<KIND, double>(p, p.theta);
   __syncthreads();
@@ -935,19 +1007,18 @@ KArgs base_args(const dnls_graph* g, const dnls_graph_inputs* in, void* ws) {
 
 template <class K>
 dnls_status launch_persistent(K kernel, const dnls_graph* g, const dnls_solver_opts* o, KArgs& a,
-                              cudaStream_t st, bool use_smem_L) {
+                              cudaStream_t st, bool /*unused*/ = true) {
   const GraphHandle& G = g->impl;
   const int threads = o->threads ? o->threads : (G.h.dof == 6 ? 256 : 128);
-  int ctas = o->ctas_per_sm ? o->ctas_per_sm : 2;
+  const int ctas = o->ctas_per_sm ? o->ctas_per_sm : (G.h.dof == 6 ? 1 : 2);
   int smem = 0;
-  if (use_smem_L && o->smem_factor) {
-    const int budget = std::min(G.smem_optin, (228 * 1024) / ctas - 4096);
-    smem = std::min(G.h.max_L_bytes, budget);
-    if (smem < 0) smem = 0;
+  if (o->smem_factor) {
+    // per-CTA share of the SM's shared memory, less the kernel's static arrays and a margin
+    const int budget = std::min(G.smem_optin - 4096, (228 * 1024) / ctas - 4096);
+    smem = std::max(0, std::min(G.h.max_arena_bytes, budget));
   }
-  a.smem_L = smem;
-  if (smem > 0 &&
-      cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+  a.smem_bytes = smem;
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
     return DNLS_ERR_CUDA;
   const int grid = std::max(1, std::min(G.h.B, G.sm_count * ctas));
   if (cudaMemsetAsync(a.counter, 0, sizeof(int), st) != cudaSuccess) return DNLS_ERR_CUDA;

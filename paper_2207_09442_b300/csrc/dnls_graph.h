@@ -35,9 +35,10 @@ struct ProbMeta {
   int32_t o_pairtgt, o_lsrc;   // [npair]: L block id of each pair; [nnzL]: pair of each L block or -1
   int32_t w_H, w_L, w_Linv;    // workspace byte offsets
   int32_t w_g, w_dx, w_tmp, w_thc, w_J;
-  int32_t w_bx, w_bv, w_br, w_bhx, w_ebuf, w_state;
+  int32_t w_bx, w_bv, w_br, w_bhx, w_ebuf, w_state, w_W;
   int32_t L_bytes;             // bytes of this problem's factor storage
-  int32_t pad_;
+  int32_t blob_len;            // int32 count of this problem's symbolic data
+  int32_t arena_bytes;         // shared memory to stage blob + L + L^-1 + two solve vectors
 };
 
 // Mutable per-problem state kept in the workspace between forward and backward.
@@ -56,7 +57,7 @@ struct GraphHost {
   std::vector<int32_t> order;  // problems, most expensive first
   std::vector<int32_t> ei, ej;
   int64_t ws_bytes;            // total workspace bytes (header + problem regions)
-  int32_t max_L_bytes, max_nlev;
+  int32_t max_L_bytes, max_nlev, max_arena_bytes;
   int64_t n_blocks_L, n_upd;
   double factor_flops, dense_flops;
 };

@@ -105,6 +105,7 @@ int build_graph_host(int kind, int B, const int64_t* pose_offsets, const int64_t
   G.ej.assign(edge_j, edge_j + G.E_total);
   G.max_L_bytes = 0;
   G.max_nlev = 0;
+  G.max_arena_bytes = 0;
   G.n_blocks_L = 0;
   G.n_upd = 0;
   G.factor_flops = 0;
@@ -332,7 +333,11 @@ int build_graph_host(int kind, int B, const int64_t* pose_offsets, const int64_t
       blob.insert(blob.end(), lsrc.begin(), lsrc.end());
     }
     blob.push_back(0);  // keep every section non-empty-addressable
+    while (blob.size() % 4) blob.push_back(0);  // 16-byte multiple, for staging copies
+    m.blob_len = (int32_t)blob.size();
     G.sym.insert(G.sym.end(), blob.begin(), blob.end());
+    // the blob of the next problem must start 16-byte aligned as well
+    // (blob lengths are multiples of 4 int32, so every problem's start is)
 
     // ---- workspace plan (layout independent of the options)
     const int64_t n = (int64_t)N * D;
@@ -358,11 +363,19 @@ int build_graph_host(int kind, int B, const int64_t* pose_offsets, const int64_t
     m.w_bhx = take(n * 8);
     m.w_ebuf = take((int64_t)E * 4 * D * 8);
     m.w_state = take(64);
+    m.w_W = take((int64_t)E * D * 8);
+    {
+      auto a16 = [](int64_t x) { return (x + 15) & ~(int64_t)15; };
+      const int64_t arena = a16((int64_t)m.blob_len * 4) + a16(m.L_bytes) + a16((int64_t)N * BS * 8) +
+                            2 * a16(n * 8);
+      m.arena_bytes = (int32_t)std::min<int64_t>(arena, (int64_t)1 << 30);
+    }
     if (off > ((int64_t)1 << 31) - 1) return DNLS_ERR_ARG;
     m.ws = ws;
     ws += off;
 
     G.max_L_bytes = std::max(G.max_L_bytes, m.L_bytes);
+    G.max_arena_bytes = std::max(G.max_arena_bytes, m.arena_bytes);
     G.max_nlev = std::max(G.max_nlev, nlev);
     G.n_blocks_L += N + nnzL;
     G.n_upd += n_upd;

@@ -28,7 +28,7 @@ class Options:
     refine_max: int = 30
     lambda0: float = 1e-3
     tau: Optional[float] = None      # default: 1e-14 (fp64) / 1e-10 (mixed)
-    refine_tol: Optional[float] = None  # default: 1e-11 (fp64) / 1e-9 (mixed)
+    refine_tol: Optional[float] = None  # default: 1e-11 (fp64) / 1e-7 (mixed)
     threads: int = 0
     ctas_per_sm: int = 0
     smem_factor: int = 1
@@ -46,7 +46,7 @@ class Options:
         o.smem_factor = int(self.smem_factor)
         o.lambda0 = float(self.lambda0) if self.algo == "lm" else 0.0
         o.tau = float(self.tau if self.tau is not None else (1e-14 if fp64 else 1e-10))
-        o.refine_tol = float(self.refine_tol if self.refine_tol is not None else (1e-11 if fp64 else 1e-9))
+        o.refine_tol = float(self.refine_tol if self.refine_tol is not None else (1e-11 if fp64 else 1e-7))
         return o
 
 

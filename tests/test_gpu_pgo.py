@@ -131,7 +131,8 @@ def test_project_and_lift_grad():
 
 @pytest.mark.parametrize("mode", ["implicit", "implicit_gn"])
 def test_implicit_backward_fp64(mode):
-    """Implicit gradients w.r.t. measurements and log-weights (Eq. 3) against the oracle."""
+    """Implicit gradients w.r.t. measurements and log-weights (Eq. 3) against the oracle's,
+    both evaluated at the GPU's theta* (the forward's own parity is checked separately)."""
     b = synth.pgo_se3(batch=4, n_poses=16, n_lc=4, config_id=3, log_weights=True)
     opts = layer.Options(algo="lm", iters=20, precision="fp64", backward_mode=mode)
     sol, theta, (meas, wd, lw) = run_forward(b, opts)
@@ -139,16 +140,18 @@ def test_implicit_backward_fp64(mode):
     refs = []
     for k in range(b.batch):
         g, ref, _ = oracle_solve(b, k, opts)
+        assert rel(poses_of(b, theta, k), ref) < 1e-9
+        th_k = poses_of(b, theta, k)
         loss = lambda X: pgo.pose_error_loss(3, X, g.theta_gt)
-        vk = pgo.tangent_grad(3, loss, ref)
+        vk = pgo.tangent_grad(3, loss, th_k)
         v[b.pose_offsets[k]:b.pose_offsets[k + 1]] = vk
-        refs.append(pgo.implicit_grads(g, ref, vk, "exact" if mode == "implicit" else "gn"))
+        refs.append(pgo.implicit_grads(g, th_k, vk, "exact" if mode == "implicit" else "gn"))
     gm, gl = sol.backward(theta, v.to(DEV), meas, wd, lw)
     torch.cuda.synchronize()
     info = sol.info_dict()
     for k in range(b.batch):
         assert rel(edges_of(b, gm, k), refs[k][0]) < 1e-8, (k, rel(edges_of(b, gm, k), refs[k][0]))
-        assert rel(edges_of(b, gl, k), refs[k][1]) < 1e-8
+        assert rel(edges_of(b, gl, k), refs[k][1]) < 1e-8, (k, rel(edges_of(b, gl, k), refs[k][1]))
         assert info["status"][k] == 0
 
 

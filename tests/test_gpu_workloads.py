@@ -1,0 +1,141 @@
+"""Full-size workloads in the launch configuration the benchmark times, checked on sampled
+problems against the oracle (problems are independent, so a sample is exact evidence for the
+sampled problems), plus the uneven persistent batch, CUDA-graph replay and the autotuner."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import pgo
+from paper_2207_09442_b300 import layer, synth
+
+pytestmark = pytest.mark.gpu
+
+if torch.cuda.is_available():
+    from gpu_util import DEV, edges_of, oracle_solve, poses_of, rel, run_forward, t32, t64
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2207_09442_b300 import build
+    build.build()
+
+
+def _bench_opts(**kw):
+    return layer.Options(algo="lm", iters=20, precision="mixed_fp32", **kw)
+
+
+def test_full_se3_b256_mixed_sampled():
+    """256 SE(3) graphs x 128 poses, mixed precision, 20 LM iterations (the benchmark's forward,
+    freeze threshold 0): sampled problems within 1e-5 of the FP64 oracle."""
+    b = synth.workload("pgo_se3_b256")
+    opts = _bench_opts(tau=0.0)
+    sol, theta, _ = run_forward(b, opts)
+    info = sol.info_dict()
+    assert (info["status"] == 0).all()
+    for k in (0, 97, 255):
+        _, ref, _ = oracle_solve(b, k, opts)
+        assert rel(poses_of(b, theta, k), ref) < 1e-5, k
+
+
+def test_full_uneven_b1024_sampled():
+    """1024 graphs of 16..256 poses in one persistent launch: the largest, the smallest and a
+    middle problem against the oracle (mixed path, 15 LM iterations)."""
+    b = synth.workload("pgo_se3_uneven_b1024")
+    opts = layer.Options(algo="lm", iters=15, precision="mixed_fp32")
+    sol, theta, _ = run_forward(b, opts)
+    sizes = np.diff(b.pose_offsets)
+    info = sol.info_dict()
+    assert (info["status"] == 0).all()
+    for k in (int(sizes.argmax()), int(sizes.argmin()), 500):
+        _, ref, _ = oracle_solve(b, k, opts)
+        assert rel(poses_of(b, theta, k), ref) < 1e-5, (k, sizes[k])
+
+
+def test_full_implicit_b256_sampled_gradients():
+    """256 graphs x 64 poses with learnable log-weights: implicit gradients w.r.t. measurements
+    and log-weights on the mixed path within 1e-4 of the oracle's exact-Hessian gradients."""
+    b = synth.workload("pgo_se3_implicit_b256")
+    opts = layer.Options(algo="lm", iters=20, precision="mixed_fp32")
+    sol, theta, (meas, wd, lw) = run_forward(b, opts)
+    sample = (0, 131, 255)
+    v = torch.zeros(b.pose_offsets[-1], 6, dtype=torch.float64)
+    refs = {}
+    for k in sample:
+        g, ref, _ = oracle_solve(b, k, layer.Options(algo="lm", iters=20, precision="fp64"))
+        th_k = poses_of(b, theta, k)  # Eq. 3 evaluated at the GPU's theta*
+        vk = pgo.tangent_grad(3, lambda X: pgo.pose_error_loss(3, X, g.theta_gt), th_k)
+        v[b.pose_offsets[k]:b.pose_offsets[k + 1]] = vk
+        refs[k] = (ref, pgo.implicit_grads(g, th_k, vk, "exact"))
+    gm, gl = sol.backward(theta, v.to(DEV), meas, wd, lw)
+    torch.cuda.synchronize()
+    info = sol.info_dict()
+    for k in sample:
+        ref, (rm, rl, _) = refs[k]
+        assert rel(poses_of(b, theta, k), ref) < 1e-5
+        assert rel(edges_of(b, gm, k), rm) < 1e-4, (k, rel(edges_of(b, gm, k), rm))
+        assert rel(edges_of(b, gl, k), rl) < 1e-4
+        assert info["status"][k] == 0
+
+
+def test_uneven_small_fp64_every_problem():
+    parts = [synth.pgo_se3(batch=1, n_poses=n, n_lc=n // 4, config_id=40 + i)
+             for i, n in enumerate([16, 90, 33, 200, 17, 64, 128, 25])]
+    b = synth.concat_pose_graphs(parts)
+    opts = layer.Options(algo="lm", iters=15, precision="fp64")
+    sol, theta, _ = run_forward(b, opts)
+    for k in range(b.batch):
+        _, ref, _ = oracle_solve(b, k, opts)
+        assert rel(poses_of(b, theta, k), ref) < 1e-9, k
+
+
+def test_cuda_graph_capture_replays_forward_and_backward():
+    """Forward + implicit backward captured once in a CUDA graph and replayed on new inputs
+    give the same results as eager calls."""
+    b = synth.pgo_se3(batch=8, n_poses=20, n_lc=5, config_id=50, log_weights=True)
+    st = layer.PoseGraphStructure.from_batch(b)
+    opts = layer.Options(algo="lm", iters=10, precision="mixed_fp32")
+    sol = layer.PoseGraphSolver(st, opts)
+    th0, meas, wd, lw = t64(b.theta_init), t64(b.meas), t64(b.wdiag), t32(b.logw)
+    v = t64(np.random.default_rng(0).normal(size=(st.n_poses, 6)))
+    theta = torch.empty_like(th0)
+    gm = torch.empty(st.n_costs, 6, dtype=torch.float64, device=DEV)
+    gl = torch.empty(st.n_costs, dtype=torch.float64, device=DEV)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):  # warm-up outside capture
+        theta.copy_(th0)
+        sol.forward(theta, meas, wd, lw, out=theta)
+        sol.backward(theta, v, meas, wd, lw, gm, gl)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        theta.copy_(th0)
+        sol.forward(theta, meas, wd, lw, out=theta)
+        sol.backward(theta, v, meas, wd, lw, gm, gl)
+    # new inputs, replay
+    lw.mul_(0.5)
+    graph.replay()
+    torch.cuda.synchronize()
+    got = (theta.clone(), gm.clone(), gl.clone())
+    ref_sol = layer.PoseGraphSolver(st, opts)
+    th_e = ref_sol.forward(th0, meas, wd, lw)
+    gm_e, gl_e = ref_sol.backward(th_e, v, meas, wd, lw)
+    torch.cuda.synchronize()
+    assert rel(got[0], th_e) < 1e-12
+    assert rel(got[1], gm_e) < 1e-10 and rel(got[2], gl_e) < 1e-10
+
+
+def test_autotuner_returns_a_runnable_shape():
+    from paper_2207_09442_b300 import autotune
+    b = synth.pgo_se3(batch=16, n_poses=40, n_lc=10, config_id=51)
+    st = layer.PoseGraphStructure.from_batch(b)
+    opts = layer.Options(algo="lm", iters=5, precision="mixed_fp32")
+    inputs = (t64(b.theta_init), t64(b.meas), t64(b.wdiag), t32(b.logw))
+    tuned = autotune.tune(st, opts, inputs, use_cache=False, reps=1)
+    assert tuned["threads"] in (128, 256) and tuned["ms"] > 0
+    sol = layer.PoseGraphSolver(st, autotune.apply(opts, tuned))
+    th = sol.forward(*inputs)
+    ref = layer.PoseGraphSolver(st, opts).forward(*inputs)
+    torch.cuda.synchronize()
+    assert rel(th, ref) < 1e-6
