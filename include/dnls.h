@@ -195,6 +195,62 @@ dnls_status dnls_project_grad(int32_t kind, int64_t n, const double* theta, cons
 dnls_status dnls_lift_grad(int32_t kind, int64_t n, const double* T, const double* v, double* G,
                            void* stream);
 
+/* ------------------------------------------------------------------------------------------
+ * Bundle adjustment: SE(3) cameras (camera-to-world) and R^3 points with reprojection costs
+ * under a Huber loss (paper Sec. 3 "reprojection error", robust losses; App. D.3 bundle
+ * adjustment with a soft kernel) and SE(3) priors on cameras.  Each LM iteration eliminates the
+ * 3x3 point blocks by the Schur complement (Sec. 4.2, FP64) and factors the reduced camera
+ * system with the same level-scheduled block Cholesky as the pose graphs (FP64).
+ *   c_o = pi(T_cam, p) - obs_o,  pi(T, p) = f (x, y) / z  with (x, y, z) = R^T (p - t);
+ *   cost 1/2 rho(||c_o||^2), rho = Huber with radius huber_delta (pixels).
+ * ------------------------------------------------------------------------------------------ */
+typedef struct dnls_ba dnls_ba; /* opaque: structure + symbolic Schur/Cholesky plan of a batch */
+
+typedef struct {
+  int32_t batch;                 /* B >= 1 independent problems */
+  const int64_t* cam_offsets;    /* host [B+1] cameras of problem b */
+  const int64_t* pt_offsets;     /* host [B+1] points of problem b */
+  const int64_t* obs_offsets;    /* host [B+1] observations of problem b */
+  const int32_t* obs_cam;        /* host [O]: local camera index of each observation */
+  const int32_t* obs_pt;         /* host [O]: local point index of each observation */
+  const int64_t* prior_offsets;  /* host [B+1] camera priors of problem b */
+  const int32_t* prior_cam;      /* host [Q]: local camera index of each prior */
+} dnls_ba_desc;
+
+typedef struct {
+  const double* obs;         /* device [O, 2] observed pixels */
+  const double* prior_meas;  /* device [Q, 12] prior camera poses Z */
+  const double* prior_w;     /* device [Q, 6] prior square-root weights */
+  double focal;              /* focal length in pixels (principal point at 0) */
+  double huber_delta;        /* Huber radius in pixels; <= 0 for plain squares */
+} dnls_ba_inputs;
+
+/* Validates indices, builds the per-point and per-camera observation lists, the camera
+ * co-observation graph of each problem with its block ordering, symbolic factor and level
+ * schedule, and the fixed-order Schur gather lists (one list per 6x6 block of the reduced
+ * system); uploads them to the current device.  Errors: DNLS_ERR_ARG, DNLS_ERR_CUDA. */
+dnls_status dnls_ba_create(const dnls_ba_desc* desc, dnls_ba** out);
+void dnls_ba_destroy(dnls_ba* h);
+dnls_status dnls_ba_workspace_size(const dnls_ba* h, const dnls_solver_opts* opts, size_t* bytes);
+
+/* opts->iters GN/LM iterations on every problem (one launch sequence for the whole batch).
+ *   cams: device [C, 12] FP64 in/out;  pts: device [Pt, 3] FP64 in/out;  info: device [B] or NULL.
+ * LM damping D = diag(max(diag H, 1e-9)) acts on the full (camera + point) system before the
+ * elimination.  Errors: DNLS_ERR_ARG, DNLS_ERR_WORKSPACE, DNLS_ERR_CUDA. */
+dnls_status dnls_ba_forward(const dnls_ba* h, const dnls_solver_opts* opts, const dnls_ba_inputs* in,
+                            double* cams, double* pts, void* workspace, size_t workspace_bytes,
+                            void* stream, dnls_info* info);
+
+/* Implicit backward (Eq. 3, true Hessian including the Huber rho'' term) w.r.t. the
+ * observations at (cams, pts) from the preceding dnls_ba_forward on the same workspace:
+ *   v_cams device [C, 6] and v_pts device [Pt, 3] tangent gradient of the outer loss;
+ *   grad_obs device [O, 2] = -(D_obs g)^T x, x = H^-1 v (refinement preconditioned by the
+ *   Schur factorization).  Only DNLS_IMPLICIT_EXACT is supported (else DNLS_ERR_UNSUPPORTED). */
+dnls_status dnls_ba_backward(const dnls_ba* h, const dnls_solver_opts* opts, const dnls_ba_inputs* in,
+                             const double* cams, const double* pts, const double* v_cams,
+                             const double* v_pts, double* grad_obs, void* workspace,
+                             size_t workspace_bytes, void* stream, dnls_info* info);
+
 /* Sizes of the symbolic factorization (host values; for reports and tests). */
 typedef struct {
   int64_t n_poses, n_costs, n_blocks_L, n_block_updates, n_levels_max;

@@ -1,0 +1,208 @@
+// Level-scheduled, left-looking block Cholesky of a block-sparse SPD matrix and the matching
+// triangular solves, run by one CTA (Sec. 4.2's sparse Cholesky with a symbolic factorization
+// computed once per structure).  The view type F supplies the symbolic structure and buffers
+// (fields N, nnzL, nlev, H, L, Linv, tmp, lsrc, tgtptr, tgt, gptr, gsrc, lvlptr, lvlcols,
+// panptr, pan, rowptr, rowent, colptr, rows; see ProbMeta in dnls_graph.h for their meaning).
+// Every output element is produced by one thread in a fixed order: no atomics, bitwise
+// reproducible results.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace dnls {
+
+constexpr double kDiagFloor = 1e-9;
+
+// ----------------------------------------------------------------------------- helpers
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  const int t = threadIdx.x;
+  red[t] = v;
+  __syncthreads();
+  for (int s = blockDim.x >> 1; s > 0; s >>= 1) {
+    if (t < s) red[t] += red[t + s];
+    __syncthreads();
+  }
+  const double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+// L <- H + lam * diag(max(diag H, floor)), then left-looking block Cholesky level by level.
+// Returns false (uniformly across the CTA) if a pivot is not positive or not finite.  A failing
+// thread writes the call's generation number `gen` into *sflag; the flag is never reset, so a
+// slow thread can never see a later call's state.
+template <int D, class F>
+__device__ bool block_factor(F& p, double lam, int* sflag, int gen) {
+  constexpr int BS = D * D;
+  double* L = p.L;
+  const int nb = p.N + p.nnzL;
+  for (int it = threadIdx.x; it < nb * BS; it += blockDim.x) {
+    const int t = it / BS, el = it % BS;
+    double v;
+    if (t < p.N) {
+      v = p.H[(int64_t)t * BS + el];
+      if (el / D == el % D) v += lam * fmax(v, kDiagFloor);
+    } else {
+      const int src = p.lsrc[t - p.N];
+      v = src >= 0 ? p.H[(int64_t)(p.N + src) * BS + el] : 0.0;
+    }
+    L[(int64_t)t * BS + el] = v;
+  }
+  __syncthreads();
+  for (int lv = 0; lv < p.nlev; ++lv) {
+    // (1) subtract the products of already-factored descendant columns
+    const int t0 = p.tgtptr[lv], t1 = p.tgtptr[lv + 1];
+    for (int it = threadIdx.x; it < (t1 - t0) * BS; it += blockDim.x) {
+      const int q = t0 + it / BS, el = it % BS, a = el / D, b = el % D;
+      const int s0 = p.gptr[q], s1 = p.gptr[q + 1];
+      if (s0 == s1) continue;
+      double acc = 0.0;
+      for (int s = s0; s < s1; ++s) {
+        const double* X = L + (int64_t)p.gsrc[2 * s] * BS + a * D;
+        const double* Y = L + (int64_t)p.gsrc[2 * s + 1] * BS + b * D;
+#pragma unroll
+        for (int mm = 0; mm < D; ++mm) acc = fma(X[mm], Y[mm], acc);
+      }
+      L[(int64_t)p.tgt[q] * BS + el] -= acc;
+    }
+    __syncthreads();
+    // (2) dense Cholesky of each diagonal block of the level (one thread per column) and the
+    //     inverse of its factor
+    const int c0 = p.lvlptr[lv], c1 = p.lvlptr[lv + 1];
+    for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
+      const int k = p.lvlcols[c];
+      double A[BS];
+      double* Lk = L + (int64_t)k * BS;
+#pragma unroll
+      for (int e = 0; e < BS; ++e) A[e] = Lk[e];
+      bool ok = true;
+      double inv[D];  // reciprocals of the pivots, reused by the inverse below
+#pragma unroll
+      for (int jj = 0; jj < D; ++jj) {
+        double d = A[jj * D + jj];
+#pragma unroll
+        for (int mm = 0; mm < jj; ++mm) d -= A[jj * D + mm] * A[jj * D + mm];
+        ok = ok && (d > 0.0) && isfinite(d);
+        const double dd = fmax(d, 1e-300);
+        const double il = rsqrt(dd);
+        inv[jj] = il;
+        A[jj * D + jj] = dd * il;
+#pragma unroll
+        for (int ii = jj + 1; ii < D; ++ii) {
+          double s = A[ii * D + jj];
+#pragma unroll
+          for (int mm = 0; mm < jj; ++mm) s -= A[ii * D + mm] * A[jj * D + mm];
+          A[ii * D + jj] = s * il;
+        }
+      }
+      // inverse of the lower-triangular factor
+      double I[BS];
+#pragma unroll
+      for (int e = 0; e < BS; ++e) I[e] = 0.0;
+#pragma unroll
+      for (int jj = 0; jj < D; ++jj) {
+        I[jj * D + jj] = inv[jj];
+#pragma unroll
+        for (int ii = jj + 1; ii < D; ++ii) {
+          double s = 0.0;
+#pragma unroll
+          for (int mm = jj; mm < ii; ++mm) s += A[ii * D + mm] * I[mm * D + jj];
+          I[ii * D + jj] = -s * inv[ii];
+        }
+      }
+#pragma unroll
+      for (int ii = 0; ii < D; ++ii)
+#pragma unroll
+        for (int jj = 0; jj < D; ++jj) {
+          Lk[ii * D + jj] = jj <= ii ? A[ii * D + jj] : 0.0;
+          p.Linv[(int64_t)k * BS + ii * D + jj] = I[ii * D + jj];
+        }
+      if (!ok) *sflag = gen;
+    }
+    __syncthreads();
+    if (*sflag == gen) return false;
+    // (3) off-diagonal blocks of the level's columns: L(r,k) <- A(r,k) L(k,k)^-T, one row each
+    const int q0 = p.panptr[lv], q1 = p.panptr[lv + 1];
+    for (int it = threadIdx.x; it < (q1 - q0) * D; it += blockDim.x) {
+      const int q = q0 + it / D, row = it % D;
+      double* X = L + (int64_t)p.pan[2 * q] * BS + row * D;
+      const double* Ik = p.Linv + (int64_t)p.pan[2 * q + 1] * BS;
+      double a[D], o[D];
+#pragma unroll
+      for (int mm = 0; mm < D; ++mm) a[mm] = X[mm];
+#pragma unroll
+      for (int jj = 0; jj < D; ++jj) {
+        double s = 0.0;
+#pragma unroll
+        for (int mm = 0; mm <= jj; ++mm) s = fma(a[mm], Ik[jj * D + mm], s);
+        o[jj] = s;
+      }
+#pragma unroll
+      for (int jj = 0; jj < D; ++jj) X[jj] = o[jj];
+    }
+    __syncthreads();
+  }
+  return true;
+}
+
+// In place: x <- (L L^T)^-1 x (positions order, FP64), level by level.
+template <int D, class F>
+__device__ void block_solve(F& p, double* x) {
+  constexpr int BS = D * D;
+  const double* L = p.L;
+  for (int lv = 0; lv < p.nlev; ++lv) {
+    const int c0 = p.lvlptr[lv], c1 = p.lvlptr[lv + 1];
+    for (int it = threadIdx.x; it < (c1 - c0) * D; it += blockDim.x) {
+      const int k = p.lvlcols[c0 + it / D], i = it % D;
+      double s = x[k * D + i];
+      for (int q = p.rowptr[k]; q < p.rowptr[k + 1]; ++q) {
+        const double* B = L + (int64_t)p.rowent[2 * q] * BS + i * D;
+        const double* y = x + p.rowent[2 * q + 1] * D;
+#pragma unroll
+        for (int mm = 0; mm < D; ++mm) s = fma(-B[mm], y[mm], s);
+      }
+      p.tmp[k * D + i] = s;
+    }
+    __syncthreads();
+    for (int it = threadIdx.x; it < (c1 - c0) * D; it += blockDim.x) {
+      const int k = p.lvlcols[c0 + it / D], i = it % D;
+      const double* I = p.Linv + (int64_t)k * BS + i * D;
+      double s = 0.0;
+#pragma unroll
+      for (int mm = 0; mm < D; ++mm)
+        if (mm <= i) s = fma(I[mm], p.tmp[k * D + mm], s);
+      x[k * D + i] = s;
+    }
+    __syncthreads();
+  }
+  for (int lv = p.nlev - 1; lv >= 0; --lv) {
+    const int c0 = p.lvlptr[lv], c1 = p.lvlptr[lv + 1];
+    for (int it = threadIdx.x; it < (c1 - c0) * D; it += blockDim.x) {
+      const int k = p.lvlcols[c0 + it / D], i = it % D;
+      double s = x[k * D + i];
+      const int base = p.colptr[k];
+      const int cnt = p.colptr[k + 1] - base;
+      for (int aa = 0; aa < cnt; ++aa) {
+        const double* B = L + (int64_t)(p.N + base + aa) * BS + i;
+        const double* y = x + p.rows[base + aa] * D;
+#pragma unroll
+        for (int mm = 0; mm < D; ++mm) s = fma(-B[mm * D], y[mm], s);
+      }
+      p.tmp[k * D + i] = s;
+    }
+    __syncthreads();
+    for (int it = threadIdx.x; it < (c1 - c0) * D; it += blockDim.x) {
+      const int k = p.lvlcols[c0 + it / D], i = it % D;
+      const double* I = p.Linv + (int64_t)k * BS;
+      double s = 0.0;
+#pragma unroll
+      for (int mm = 0; mm < D; ++mm)
+        if (mm >= i) s = fma(I[mm * D + i], p.tmp[k * D + mm], s);
+      x[k * D + i] = s;
+    }
+    __syncthreads();
+  }
+}
+
+
+}  // namespace dnls

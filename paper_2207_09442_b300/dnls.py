@@ -49,6 +49,17 @@ class GraphStats(ctypes.Structure):
                 ("factor_flops", c_double), ("dense_flops", c_double)]
 
 
+class BADesc(ctypes.Structure):
+    _fields_ = [("batch", c_int32), ("cam_offsets", c_void_p), ("pt_offsets", c_void_p),
+                ("obs_offsets", c_void_p), ("obs_cam", c_void_p), ("obs_pt", c_void_p),
+                ("prior_offsets", c_void_p), ("prior_cam", c_void_p)]
+
+
+class BAInputs(ctypes.Structure):
+    _fields_ = [("obs", c_void_p), ("prior_meas", c_void_p), ("prior_w", c_void_p),
+                ("focal", c_double), ("huber_delta", c_double)]
+
+
 INFO_BYTES = 48  # dnls_info: 4 doubles + 4 int32
 
 
@@ -76,6 +87,14 @@ _SIGS = {
     "dnls_lift_grad": (c_int32, [c_int32, c_int64, c_void_p, c_void_p, c_void_p, c_void_p]),
     "dnls_graph_get_stats": (c_int32, [c_void_p, ctypes.POINTER(GraphStats)]),
     "dnls_status_string": (ctypes.c_char_p, [c_int32]),
+    "dnls_ba_create": (c_int32, [ctypes.POINTER(BADesc), ctypes.POINTER(c_void_p)]),
+    "dnls_ba_destroy": (None, [c_void_p]),
+    "dnls_ba_workspace_size": (c_int32, [c_void_p, ctypes.POINTER(SolverOpts), ctypes.POINTER(c_size_t)]),
+    "dnls_ba_forward": (c_int32, [c_void_p, ctypes.POINTER(SolverOpts), ctypes.POINTER(BAInputs),
+                                  c_void_p, c_void_p, c_void_p, c_size_t, c_void_p, c_void_p]),
+    "dnls_ba_backward": (c_int32, [c_void_p, ctypes.POINTER(SolverOpts), ctypes.POINTER(BAInputs),
+                                   c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                   c_size_t, c_void_p, c_void_p]),
     "dnls_probe_fp64_peak": (c_int32, [c_int32, c_void_p, ctypes.POINTER(c_double)]),
 }
 
