@@ -57,11 +57,15 @@ def damped_step(J, r, lam, damped):
 def lm_loop(linearize: Callable, objective: Callable, retract: Callable, theta0,
             algo="lm", iters=20, lam0=1e-3, tau=1e-14, record=False):
     """Run ``iters`` GN/LM iterations.  ``linearize(theta) -> (r, J)``, ``objective(theta) -> S``,
-    ``retract(theta, delta) -> theta'``.  Branch decisions are taken on values; the arithmetic
+    ``retract(theta, delta) -> theta'``.  S is always ``objective`` (for robust costs the
+    re-weighted residuals r of the linearisation give 1/2 rho'(s) s, not 1/2 rho(s)).  Branch
+    decisions are taken on values; the arithmetic
     stays on the autograd tape, so the loop can be differentiated (unrolled backward)."""
     theta = theta0
     r, J = linearize(theta)
-    S = 0.5 * (r * r).sum()
+    # the objective itself (Eq. 1); for robust costs the re-weighted residuals of the
+    # linearization do not sum to it
+    S = objective(theta)
     S0 = float(S.detach()) if isinstance(S, torch.Tensor) else float(S)
     lam = float(lam0)
     status = STATUS_OK

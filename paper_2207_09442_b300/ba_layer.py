@@ -51,6 +51,12 @@ class BASolver:
     def __init__(self, structure: BAStructure, opts: Options = None, device="cuda"):
         self.s = structure
         self.opts = opts or Options(iters=10)
+        if self.opts.refine_tol is None:
+            # the BA Hessian is far worse conditioned than a pose graph's (reduced camera system
+            # kappa ~ 1e8 at small damping), so ||v - H x|| / ||v|| bottoms out near 1e-9 in FP64
+            import dataclasses
+            self.opts = dataclasses.replace(
+                self.opts, refine_tol=1e-8 if self.opts.precision == "fp64" else 1e-6)
         self.device = torch.device(device)
         self._copts = self.opts.c()
         n = ctypes.c_size_t()

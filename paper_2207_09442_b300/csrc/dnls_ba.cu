@@ -38,7 +38,7 @@ constexpr double kLamMinBA = 1e-12, kLamMaxBA = 1e12, kRefactorLambdaBA = 1e-6;
 constexpr int kJW = 20;  // per observation: r (2), J_cam (12), J_pt (6)
 
 struct BAState {
-  double lam, S, Sc, lam_fact, rel, vnorm;
+  double lam, S, Sc, lam_fact, rel, vnorm, rz;
   int32_t active, need_lin, bad, accepted_last;
   int32_t iters, accepted, status, factor_ok;
   int32_t refine_steps, pad[3];
@@ -73,6 +73,7 @@ struct BAArgs {
   void* J;
   double *Y, *Hcp, *Hppi, *up, *gp, *Hcc, *gc, *bc, *dc, *ccam, *cpt, *cost;
   double *xc, *xp, *rc, *rp, *vc, *vp, *eb, *ebq;
+  double *solc, *solp, *zc, *zp, *hc, *hp;
   BAState* st;
   // options
   int algo, mixed, iters;
@@ -595,14 +596,14 @@ __global__ void __launch_bounds__(256) k_bab_start(BAArgs a, const int64_t* pt_o
     const double v = a.v_cams[k];
     a.vc[k] = v;
     a.rc[k] = v;
-    a.xc[k] = 0.0;
+    a.solc[k] = 0.0;
     acc += v * v;
   }
   for (int64_t k = pt_off[b] * 3 + threadIdx.x; k < pt_off[b + 1] * 3; k += blockDim.x) {
     const double v = a.v_pts[k];
     a.vp[k] = v;
     a.rp[k] = v;
-    a.xp[k] = 0.0;
+    a.solp[k] = 0.0;
     acc += v * v;
   }
   const double n = sqrt(block_sum(acc, red));
@@ -630,7 +631,7 @@ __global__ void k_bap_cams(BAArgs a) {
   for (int i = 0; i < 6; ++i) a.bc[c * 6 + i] = acc[i];
 }
 
-// preconditioner, point side: yp = Hppi (rp - sum_o H_cp(o)^T yc(o)); x_p += yp.  yc is in dc.
+// preconditioner, point side: z_p = Hppi (rp - sum_o H_cp(o)^T z_c(o)); z_c is in dc.
 __global__ void k_bap_pts(BAArgs a) {
   const int64_t q = gtid();
   if (q >= a.d.P || !a.st[a.d.pt_prob[q]].active) return;
@@ -646,13 +647,7 @@ __global__ void k_bap_pts(BAArgs a) {
   }
   const double* Hi = a.Hppi + q * 9;
 #pragma unroll
-  for (int j = 0; j < 3; ++j) a.xp[q * 3 + j] += Hi[3 * j] * w[0] + Hi[3 * j + 1] * w[1] + Hi[3 * j + 2] * w[2];
-}
-
-__global__ void k_bap_addc(BAArgs a) {
-  const int64_t k = gtid();
-  if (k >= a.d.C * 6 || !a.st[a.d.cam_prob[k / 6]].active) return;
-  a.xc[k] += a.dc[k];
+  for (int j = 0; j < 3; ++j) a.zp[q * 3 + j] = Hi[3 * j] * w[0] + Hi[3 * j + 1] * w[1] + Hi[3 * j + 2] * w[2];
 }
 
 // exact Hessian product per observation: dual evaluation of the local gradient
@@ -730,7 +725,7 @@ __global__ void k_bahvp_cams(BAArgs a) {
   double corr[6];
   se3_adT(x, gs, corr);
 #pragma unroll
-  for (int i = 0; i < 6; ++i) a.rc[c * 6 + i] = a.vc[c * 6 + i] - (h[i] - 0.5 * corr[i]);
+  for (int i = 0; i < 6; ++i) a.hc[c * 6 + i] = h[i] - 0.5 * corr[i];
 }
 
 __global__ void k_bahvp_pts(BAArgs a) {
@@ -743,26 +738,65 @@ __global__ void k_bahvp_pts(BAArgs a) {
     for (int j = 0; j < 3; ++j) h[j] += e[15 + j];
   }
 #pragma unroll
-  for (int j = 0; j < 3; ++j) a.rp[q * 3 + j] = a.vp[q * 3 + j] - h[j];
+  for (int j = 0; j < 3; ++j) a.hp[q * 3 + j] = h[j];
 }
 
-// ||r|| / ||v|| per problem; problems below the tolerance stop refining
-__global__ void __launch_bounds__(256) k_bab_check(BAArgs a, const int64_t* pt_off, int step) {
+// Preconditioned conjugate gradients on H x = v per problem (H the true Hessian, SPD at a
+// strict minimum; preconditioner M^-1 = the cached Schur factorization of the damped GN matrix).
+// The direction lives in xc/xp (the Hessian-product kernels differentiate along it).
+// mode 0 (after z = M^-1 v):  p = z, rz = r.z
+// mode 1 (after h = H p):     alpha = rz / p.h; sol += alpha p; r -= alpha h; ||r|| test
+// mode 2 (after z = M^-1 r):  beta = r.z / rz; rz = r.z; p = z + beta p
+__global__ void __launch_bounds__(256) k_pcg(BAArgs a, const int64_t* pt_off, int mode, int step) {
   __shared__ double red[256];
+  __shared__ double s_alpha;
   const int b = blockIdx.x;
   BAState& s = a.st[b];
   if (!s.active) return;
+  const int64_t k0 = a.d.cam_off[b] * 6, k1 = a.d.cam_off[b + 1] * 6;
+  const int64_t q0 = pt_off[b] * 3, q1 = pt_off[b + 1] * 3;
+  if (mode == 0 || mode == 2) {
+    double acc = 0.0;
+    for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) acc += a.rc[k] * a.dc[k];
+    for (int64_t k = q0 + threadIdx.x; k < q1; k += blockDim.x) acc += a.rp[k] * a.zp[k];
+    const double rz = block_sum(acc, red);
+    const double beta = mode == 0 ? 0.0 : rz / s.rz;
+    for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) a.xc[k] = a.dc[k] + beta * a.xc[k];
+    for (int64_t k = q0 + threadIdx.x; k < q1; k += blockDim.x) a.xp[k] = a.zp[k] + beta * a.xp[k];
+    if (threadIdx.x == 0) s.rz = rz;
+    return;
+  }
   double acc = 0.0;
-  for (int64_t k = a.d.cam_off[b] * 6 + threadIdx.x; k < a.d.cam_off[b + 1] * 6; k += blockDim.x)
-    acc += a.rc[k] * a.rc[k];
-  for (int64_t k = pt_off[b] * 3 + threadIdx.x; k < pt_off[b + 1] * 3; k += blockDim.x)
-    acc += a.rp[k] * a.rp[k];
-  const double n = sqrt(block_sum(acc, red));
+  for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) acc += a.xc[k] * a.hc[k];
+  for (int64_t k = q0 + threadIdx.x; k < q1; k += blockDim.x) acc += a.xp[k] * a.hp[k];
+  const double ph = block_sum(acc, red);
+  if (threadIdx.x == 0) s_alpha = s.rz / ph;
+  __syncthreads();
+  const double alpha = s_alpha;
+  double r2 = 0.0;
+  for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+    a.solc[k] += alpha * a.xc[k];
+    a.rc[k] -= alpha * a.hc[k];
+    r2 += a.rc[k] * a.rc[k];
+  }
+  for (int64_t k = q0 + threadIdx.x; k < q1; k += blockDim.x) {
+    a.solp[k] += alpha * a.xp[k];
+    a.rp[k] -= alpha * a.hp[k];
+    r2 += a.rp[k] * a.rp[k];
+  }
+  const double n = sqrt(block_sum(r2, red));
   if (threadIdx.x == 0) {
     s.rel = n / s.vnorm;
     s.refine_steps = step + 1;
-    if (!(s.rel > a.refine_tol)) s.active = 0;
+    if (!(s.rel > a.refine_tol) || !(ph > 0.0)) s.active = 0;
   }
+}
+
+// the solution becomes the direction the VJP kernel differentiates along
+__global__ void k_pcg_sol(BAArgs a) {
+  const int64_t k = gtid();
+  if (k < a.d.C * 6) a.xc[k] = a.solc[k];
+  else if (k - a.d.C * 6 < a.d.P * 3) a.xp[k - a.d.C * 6] = a.solp[k - a.d.C * 6];
 }
 
 __global__ void k_bab_finish(BAArgs a) {
@@ -785,7 +819,7 @@ struct BAHost {
       cam_prob, cam_prior_ptr, cam_prior, tgt_ptr, tgt_pairs, tgt_cam, tgt_prob;
   std::vector<int64_t> tgt_off, cam_off, pt_off, obs_off, prior_off;
   int64_t w_J, w_Y, w_Hcp, w_Hppi, w_up, w_gp, w_Hcc, w_gc, w_bc, w_dc, w_ccam, w_cpt, w_cost,
-      w_xc, w_xp, w_rc, w_rp, w_vc, w_vp, w_eb, w_ebq, w_st;
+      w_xc, w_xp, w_rc, w_rp, w_vc, w_vp, w_eb, w_ebq, w_st, w_solc, w_solp, w_zc, w_zp, w_hc, w_hp;
   int64_t ws_bytes = 0;
 };
 
@@ -962,6 +996,12 @@ int build_ba_host(const dnls_ba_desc* desc, BAHost& H) {
   H.w_eb = take(H.O * 18 * 8);
   H.w_ebq = take(8);
   H.w_st = take((int64_t)B * sizeof(BAState));
+  H.w_solc = take(H.C * 6 * 8);
+  H.w_solp = take(H.P * 3 * 8);
+  H.w_zc = take(H.C * 6 * 8);
+  H.w_zp = take(H.P * 3 * 8);
+  H.w_hc = take(H.C * 6 * 8);
+  H.w_hp = take(H.P * 3 * 8);
   H.ws_bytes = off;
   return DNLS_OK;
 }
@@ -1024,6 +1064,12 @@ BAArgs ba_args(const dnls_ba* h, const dnls_solver_opts* o, const dnls_ba_inputs
   a.eb = (double*)(w + H.w_eb);
   a.ebq = (double*)(w + H.w_ebq);
   a.st = (BAState*)(w + H.w_st);
+  a.solc = (double*)(w + H.w_solc);
+  a.solp = (double*)(w + H.w_solp);
+  a.zc = (double*)(w + H.w_zc);
+  a.zp = (double*)(w + H.w_zp);
+  a.hc = (double*)(w + H.w_hc);
+  a.hp = (double*)(w + H.w_hp);
   a.algo = o->algo;
   a.mixed = o->precision == DNLS_MIXED_FP32;
   a.iters = o->iters;
@@ -1040,11 +1086,11 @@ inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)std::max<int64_t
 void ba_eliminate_and_factor(const dnls_ba* h, BAArgs& a, cudaStream_t st, double lam_override) {
   const BAHost& H = h->impl.h;
   if (a.mixed && lam_override < 0.0)
-    k_ba_lin<float><<<nblk(H.O), 256, 0, st>>>(a);
+    k_ba_lin<float><<<nblk(H.O, 256), 256, 0, st>>>(a);
   else
-    k_ba_lin<double><<<nblk(H.O), 256, 0, st>>>(a);
-  k_ba_points<<<nblk(H.P), 128, 0, st>>>(a, lam_override);
-  k_ba_cameras<<<nblk(H.C), 64, 0, st>>>(a);
+    k_ba_lin<double><<<nblk(H.O, 256), 256, 0, st>>>(a);
+  k_ba_points<<<nblk(H.P, 128), 128, 0, st>>>(a, lam_override);
+  k_ba_cameras<<<nblk(H.C, 64), 64, 0, st>>>(a);
   k_ba_schur<<<nblk(H.red.meta.empty() ? 1 : (int64_t)H.tgt_cam.size() * 6, 128), 128, 0, st>>>(a, lam_override);
   k_ba_reduced<<<H.B, 256, 0, st>>>(a, 0, a.bc, a.dc, 0);
 }
@@ -1135,15 +1181,15 @@ dnls_status dnls_ba_forward(const dnls_ba* h, const dnls_solver_opts* opts, cons
   cudaStream_t st = (cudaStream_t)stream;
   const unsigned nb = nblk(H.B), nco = nblk(H.C + H.P);
   k_ba_init<<<nb, 256, 0, st>>>(a);
-  k_ba_eval<<<nblk(H.O), 256, 0, st>>>(a, 0);
-  k_ba_eval_priors<<<nblk(H.C), 128, 0, st>>>(a, 0);
+  k_ba_eval<<<nblk(H.O, 256), 256, 0, st>>>(a, 0);
+  k_ba_eval_priors<<<nblk(H.C, 128), 128, 0, st>>>(a, 0);
   k_ba_accept<<<H.B, 256, 0, st>>>(a, 0, h->impl.d_prior_off);
   k_ba_info_init<<<nb, 256, 0, st>>>(a);
   for (int it = 0; it < opts->iters; ++it) {
     ba_eliminate_and_factor(h, a, st, -1.0);
     k_ba_update<<<nco, 256, 0, st>>>(a);
-    k_ba_eval<<<nblk(H.O), 256, 0, st>>>(a, 1);
-    k_ba_eval_priors<<<nblk(H.C), 128, 0, st>>>(a, 1);
+    k_ba_eval<<<nblk(H.O, 256), 256, 0, st>>>(a, 1);
+    k_ba_eval_priors<<<nblk(H.C, 128), 128, 0, st>>>(a, 1);
     k_ba_accept<<<H.B, 256, 0, st>>>(a, 1, h->impl.d_prior_off);
     k_ba_commit<<<nco, 256, 0, st>>>(a);
   }
@@ -1180,20 +1226,25 @@ dnls_status dnls_ba_backward(const dnls_ba* h, const dnls_solver_opts* opts, con
   ba_eliminate_and_factor(h, a, st, 0.0);
   k_bab_refactored<<<nb, 256, 0, st>>>(a);
   k_bab_start<<<H.B, 256, 0, st>>>(a, h->impl.d_pt_off);
-  for (int it = 0; it < opts->refine_max; ++it) {
-    // x += M^-1 r (block elimination with the cached Schur factorization)
-    k_bap_cams<<<nblk(H.C), 64, 0, st>>>(a);
+  // z = M^-1 r (block elimination with the cached Schur factorization): camera side into dc
+  auto precondition = [&]() {
+    k_bap_cams<<<nblk(H.C, 64), 64, 0, st>>>(a);
     k_ba_reduced<<<H.B, 256, 0, st>>>(a, 1, a.bc, a.dc, 0);
-    k_bap_pts<<<nblk(H.P), 128, 0, st>>>(a);
-    k_bap_addc<<<nblk(H.C * 6), 256, 0, st>>>(a);
-    // r = v - H x with the true Hessian
-    k_bahvp_obs<<<nblk(H.O), 128, 0, st>>>(a, 0);
-    k_bahvp_cams<<<nblk(H.C), 64, 0, st>>>(a);
-    k_bahvp_pts<<<nblk(H.P), 128, 0, st>>>(a);
-    k_bab_check<<<H.B, 256, 0, st>>>(a, h->impl.d_pt_off, it);
+    k_bap_pts<<<nblk(H.P, 128), 128, 0, st>>>(a);
+  };
+  precondition();
+  k_pcg<<<H.B, 256, 0, st>>>(a, h->impl.d_pt_off, 0, 0);
+  for (int it = 0; it < opts->refine_max; ++it) {
+    k_bahvp_obs<<<nblk(H.O, 128), 128, 0, st>>>(a, 0);   // h = H p (true Hessian)
+    k_bahvp_cams<<<nblk(H.C, 64), 64, 0, st>>>(a);
+    k_bahvp_pts<<<nblk(H.P, 128), 128, 0, st>>>(a);
+    k_pcg<<<H.B, 256, 0, st>>>(a, h->impl.d_pt_off, 1, it);
+    precondition();
+    k_pcg<<<H.B, 256, 0, st>>>(a, h->impl.d_pt_off, 2, it);
   }
+  k_pcg_sol<<<nblk(H.C * 6 + H.P * 3, 256), 256, 0, st>>>(a);
   k_bab_finish<<<nb, 256, 0, st>>>(a);
-  k_bahvp_obs<<<nblk(H.O), 128, 0, st>>>(a, 1);
+  k_bahvp_obs<<<nblk(H.O, 128), 128, 0, st>>>(a, 1);
   k_ba_info<<<nb, 256, 0, st>>>(a, 1);
   return cudaGetLastError() == cudaSuccess ? DNLS_OK : DNLS_ERR_CUDA;
 }

@@ -69,7 +69,7 @@ def test_small_ba_implicit_backward_fp64():
         o0, o1 = b.obs_offsets[k], b.obs_offsets[k + 1]
         err = rel(g[o0:o1], refs[k])
         assert err < 1e-8, (k, err)
-        assert info["status"][k] == 0
+        assert info["status"][k] == 0, (k, info["refine_resid"][k], info["refine_steps"][k])
 
 
 def test_full_ba_b32_mixed_sampled():
