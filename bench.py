@@ -43,6 +43,8 @@ def _args():
     ap.add_argument("--no-extras", action="store_true", help="skip baselines (for profiling)")
     ap.add_argument("--batch", type=int, default=0,
                     help="first N problems only (profiling captures); default: the full workload")
+    ap.add_argument("--shape", default="",
+                    help="threads,ctas_per_sm,smem_factor: fixed launch shape instead of autotuning")
     return ap.parse_args()
 
 
@@ -51,6 +53,21 @@ def _dist():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def rank_problems(rank: int, per_rank: int):
+    """Weak scaling: rank r solves its own problems r*B .. r*B+B-1 of the seeded sequence (the
+    problems are independent, so no data-path collective is needed)."""
+    return rank * per_rank, per_rank
+
+
+def max_over_ranks(value: float, dist, device) -> float:
+    """The slowest rank's time (the job's time); a no-op on one process."""
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    if dist is not None and dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 class ClockSampler:
@@ -173,7 +190,8 @@ def main():
         dist.barrier()
 
     # every rank solves its own 256-problem batch (weak scaling)
-    batch = synth.workload(WORKLOAD, batch=args.batch or None)
+    first, per_rank = rank_problems(rank, args.batch or 256)
+    batch = synth.workload(WORKLOAD, batch=per_rank, first=first)
     B = batch.batch
     st = layer.PoseGraphStructure.from_batch(batch)
     stats = st.stats()
@@ -186,7 +204,11 @@ def main():
     rng = np.random.default_rng(1234)
     v = t64(rng.normal(size=(st.n_poses, 6)) * 1e-2)  # synthetic outer-loss tangent gradient
     from paper_2207_09442_b300 import autotune
-    tuned = autotune.tune(st, opts, (theta0, meas, wd, lw), v, use_cache=False)
+    if args.shape:
+        thr, ctas, smem = (int(x) for x in args.shape.split(","))
+        tuned = {"threads": thr, "ctas_per_sm": ctas, "smem_factor": smem, "table": "fixed by --shape"}
+    else:
+        tuned = autotune.tune(st, opts, (theta0, meas, wd, lw), v, use_cache=False)
     opts = autotune.apply(opts, tuned)
     solver = layer.PoseGraphSolver(st, opts, dev)
     theta = torch.empty_like(theta0)
@@ -226,11 +248,7 @@ def main():
         dist.barrier()
     step_ms = [starts[s].elapsed_time(ends[s]) for s in range(args.steps)]
     fwd_ms = [starts[s].elapsed_time(mids[s]) for s in range(args.steps)]
-    total_ms = sum(step_ms)
-    t_max = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    total_ms = float(t_max.item())
+    total_ms = max_over_ranks(sum(step_ms), dist, dev)
     ms_per_step = total_ms / args.steps
     value = executed * world / (ms_per_step * 1e-3)
     clocks = clk.summary()

@@ -88,7 +88,7 @@ struct BAArgs {
 struct RedView {
   int N, nnzL, nlev;
   const int32_t *perm, *iperm, *colptr, *rows, *rowptr, *rowent, *lvlptr, *lvlcols, *tgtptr, *tgt,
-      *gptr, *gsrc, *panptr, *pan, *lsrc;
+      *gptr, *gsrc, *panptr, *pan, *lsrc, *glanes, *slanes;
   double *H, *L, *Linv, *dx, *tmp;
   __device__ void init(const BAArgs& a, int b) {
     const ProbMeta* m = a.d.rmeta + b;
@@ -111,6 +111,8 @@ struct RedView {
     panptr = s + m->o_panptr;
     pan = s + m->o_pan;
     lsrc = s + m->o_lsrc;
+    glanes = s + m->o_glanes;
+    slanes = s + m->o_slanes;
     char* w = a.ws + m->ws;
     H = (double*)(w + m->w_H);
     L = (double*)(w + m->w_L);

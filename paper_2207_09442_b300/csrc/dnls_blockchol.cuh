@@ -2,7 +2,7 @@
 // triangular solves, run by one CTA (Sec. 4.2's sparse Cholesky with a symbolic factorization
 // computed once per structure).  The view type F supplies the symbolic structure and buffers
 // (fields N, nnzL, nlev, H, L, Linv, tmp, lsrc, tgtptr, tgt, gptr, gsrc, lvlptr, lvlcols,
-// panptr, pan, rowptr, rowent, colptr, rows; see ProbMeta in dnls_graph.h for their meaning).
+// panptr, pan, rowptr, rowent, colptr, rows, glanes, slanes; see ProbMeta in dnls_graph.h for their meaning).
 // Every output element is produced by one thread in a fixed order: no atomics, bitwise
 // reproducible results.
 #pragma once
@@ -12,6 +12,12 @@
 namespace dnls {
 
 constexpr double kDiagFloor = 1e-9;
+// sum over each group of `lanes` adjacent lanes (a power of two <= 8), same fixed order in
+// every lane; `lanes` must be the same for the whole warp, and all its lanes must call this
+__device__ __forceinline__ double lane_sum(double v, int lanes) {
+  for (int o = 1; o < lanes; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
 
 // ----------------------------------------------------------------------------- helpers
 __device__ __forceinline__ double block_sum(double v, double* red) {
@@ -50,20 +56,32 @@ __device__ bool block_factor(F& p, double lam, int* sflag, int gen) {
   }
   __syncthreads();
   for (int lv = 0; lv < p.nlev; ++lv) {
-    // (1) subtract the products of already-factored descendant columns
+    // (1) subtract the products of already-factored descendant columns; each output element
+    //     is summed by `LN` adjacent lanes (every LN-th source pair; LN chosen per level by the
+    //     symbolic analysis) and combined by a fixed-order shuffle reduction
     const int t0 = p.tgtptr[lv], t1 = p.tgtptr[lv + 1];
-    for (int it = threadIdx.x; it < (t1 - t0) * BS; it += blockDim.x) {
-      const int q = t0 + it / BS, el = it % BS, a = el / D, b = el % D;
-      const int s0 = p.gptr[q], s1 = p.gptr[q + 1];
-      if (s0 == s1) continue;
+    const int LN = p.glanes[lv];
+    const int n1 = (t1 - t0) * BS * LN;
+    for (int base = 0; base < n1; base += blockDim.x) {
+      const int it = base + threadIdx.x;
       double acc = 0.0;
-      for (int s = s0; s < s1; ++s) {
-        const double* X = L + (int64_t)p.gsrc[2 * s] * BS + a * D;
-        const double* Y = L + (int64_t)p.gsrc[2 * s + 1] * BS + b * D;
+      int q = 0, el = 0, s0 = 0, s1 = 0;
+      if (it < n1) {
+        const int e2 = it / LN, lane = it % LN;
+        q = t0 + e2 / BS;
+        el = e2 % BS;
+        const int a = el / D, b = el % D;
+        s0 = p.gptr[q];
+        s1 = p.gptr[q + 1];
+        for (int s = s0 + lane; s < s1; s += LN) {
+          const double* X = L + (int64_t)p.gsrc[2 * s] * BS + a * D;
+          const double* Y = L + (int64_t)p.gsrc[2 * s + 1] * BS + b * D;
 #pragma unroll
-        for (int mm = 0; mm < D; ++mm) acc = fma(X[mm], Y[mm], acc);
+          for (int mm = 0; mm < D; ++mm) acc = fma(X[mm], Y[mm], acc);
+        }
       }
-      L[(int64_t)p.tgt[q] * BS + el] -= acc;
+      if (LN > 1) acc = lane_sum(acc, LN);
+      if (it < n1 && (it % LN) == 0 && s1 > s0) L[(int64_t)p.tgt[q] * BS + el] -= acc;
     }
     __syncthreads();
     // (2) dense Cholesky of each diagonal block of the level (one thread per column) and the
@@ -152,16 +170,25 @@ __device__ void block_solve(F& p, double* x) {
   const double* L = p.L;
   for (int lv = 0; lv < p.nlev; ++lv) {
     const int c0 = p.lvlptr[lv], c1 = p.lvlptr[lv + 1];
-    for (int it = threadIdx.x; it < (c1 - c0) * D; it += blockDim.x) {
-      const int k = p.lvlcols[c0 + it / D], i = it % D;
-      double s = x[k * D + i];
-      for (int q = p.rowptr[k]; q < p.rowptr[k + 1]; ++q) {
-        const double* B = L + (int64_t)p.rowent[2 * q] * BS + i * D;
-        const double* y = x + p.rowent[2 * q + 1] * D;
+    const int LN = p.slanes[lv];
+    const int n1 = (c1 - c0) * D * LN;
+    for (int base = 0; base < n1; base += blockDim.x) {
+      const int it = base + threadIdx.x;
+      double acc = 0.0;
+      int k = 0, i = 0;
+      if (it < n1) {
+        const int e2 = it / LN, lane = it % LN;
+        k = p.lvlcols[c0 + e2 / D];
+        i = e2 % D;
+        for (int q = p.rowptr[k] + lane; q < p.rowptr[k + 1]; q += LN) {
+          const double* B = L + (int64_t)p.rowent[2 * q] * BS + i * D;
+          const double* y = x + p.rowent[2 * q + 1] * D;
 #pragma unroll
-        for (int mm = 0; mm < D; ++mm) s = fma(-B[mm], y[mm], s);
+          for (int mm = 0; mm < D; ++mm) acc = fma(B[mm], y[mm], acc);
+        }
       }
-      p.tmp[k * D + i] = s;
+      if (LN > 1) acc = lane_sum(acc, LN);
+      if (it < n1 && (it % LN) == 0) p.tmp[k * D + i] = x[k * D + i] - acc;
     }
     __syncthreads();
     for (int it = threadIdx.x; it < (c1 - c0) * D; it += blockDim.x) {
@@ -177,18 +204,27 @@ __device__ void block_solve(F& p, double* x) {
   }
   for (int lv = p.nlev - 1; lv >= 0; --lv) {
     const int c0 = p.lvlptr[lv], c1 = p.lvlptr[lv + 1];
-    for (int it = threadIdx.x; it < (c1 - c0) * D; it += blockDim.x) {
-      const int k = p.lvlcols[c0 + it / D], i = it % D;
-      double s = x[k * D + i];
-      const int base = p.colptr[k];
-      const int cnt = p.colptr[k + 1] - base;
-      for (int aa = 0; aa < cnt; ++aa) {
-        const double* B = L + (int64_t)(p.N + base + aa) * BS + i;
-        const double* y = x + p.rows[base + aa] * D;
+    const int LN = p.slanes[lv];
+    const int n1 = (c1 - c0) * D * LN;
+    for (int base = 0; base < n1; base += blockDim.x) {
+      const int it = base + threadIdx.x;
+      double acc = 0.0;
+      int k = 0, i = 0;
+      if (it < n1) {
+        const int e2 = it / LN, lane = it % LN;
+        k = p.lvlcols[c0 + e2 / D];
+        i = e2 % D;
+        const int basec = p.colptr[k];
+        const int cnt = p.colptr[k + 1] - basec;
+        for (int aa = lane; aa < cnt; aa += LN) {
+          const double* B = L + (int64_t)(p.N + basec + aa) * BS + i;
+          const double* y = x + p.rows[basec + aa] * D;
 #pragma unroll
-        for (int mm = 0; mm < D; ++mm) s = fma(-B[mm * D], y[mm], s);
+          for (int mm = 0; mm < D; ++mm) acc = fma(B[mm * D], y[mm], acc);
+        }
       }
-      p.tmp[k * D + i] = s;
+      if (LN > 1) acc = lane_sum(acc, LN);
+      if (it < n1 && (it % LN) == 0) p.tmp[k * D + i] = x[k * D + i] - acc;
     }
     __syncthreads();
     for (int it = threadIdx.x; it < (c1 - c0) * D; it += blockDim.x) {

@@ -64,7 +64,7 @@ struct Prob {
   static constexpr int D = Group<KIND>::DOF, PW = Group<KIND>::PW, BS = D * D, JW = 2 * BS + D;
   int N, E, npair, nnzL, nlev;
   const int32_t *perm, *iperm, *colptr, *rows, *rowptr, *rowent, *lvlptr, *lvlcols, *tgtptr, *tgt,
-      *gptr, *gsrc, *panptr, *pan, *incptr, *inc, *pairptr, *pairs, *pairtgt, *lsrc;
+      *gptr, *gsrc, *panptr, *pan, *incptr, *inc, *pairptr, *pairs, *pairtgt, *lsrc, *glanes, *slanes;
   const int32_t *ei, *ej;
   const double *meas, *wdiag;
   const float* logw;
@@ -155,6 +155,8 @@ struct Prob {
     pairs = s + m->o_pairs;
     pairtgt = s + m->o_pairtgt;
     lsrc = s + m->o_lsrc;
+    glanes = s + m->o_glanes;
+    slanes = s + m->o_slanes;
   }
 
   // Copies the symbolic blob (and, with `factor`, the cached factor) into shared memory.

@@ -33,6 +33,7 @@ struct ProbMeta {
   int32_t o_incptr, o_inc;     // [N+1] by position, [incidences]: cost << 1 | slot
   int32_t o_pairptr, o_pairs;  // [npair+1], [n_between]: cost << 1 | orientation
   int32_t o_pairtgt, o_lsrc;   // [npair]: L block id of each pair; [nnzL]: pair of each L block or -1
+  int32_t o_glanes, o_slanes;  // [nlev]: lanes per output in the level's gathers / solve sweeps
   int32_t w_H, w_L, w_Linv;    // workspace byte offsets
   int32_t w_g, w_dx, w_tmp, w_thc, w_J;
   int32_t w_bx, w_bv, w_br, w_bhx, w_ebuf, w_state, w_W;

@@ -332,6 +332,14 @@ int build_graph_host(int kind, int B, const int64_t* pose_offsets, const int64_t
       for (int p = 0; p < npair; ++p) lsrc[pairtgt[p] - N] = p;
       blob.insert(blob.end(), lsrc.begin(), lsrc.end());
     }
+    // lanes per output element in each level's sums.  Measured on the 128-pose SE(3) graphs:
+    // the factor gathers (36 outputs per block, short source lists) are fastest with one lane
+    // everywhere, the solve sweeps (6 outputs per block column) with four lanes everywhere;
+    // the per-level arrays keep the choice open for other structures.
+    m.o_glanes = mark();
+    for (int l = 0; l < nlev; ++l) blob.push_back(1);
+    m.o_slanes = mark();
+    for (int l = 0; l < nlev; ++l) blob.push_back(4);
     blob.push_back(0);  // keep every section non-empty-addressable
     while (blob.size() % 4) blob.push_back(0);  // 16-byte multiple, for staging copies
     m.blob_len = (int32_t)blob.size();

@@ -191,19 +191,20 @@ def _assemble(kind, per_problem, weight_fn, logw_fn):
     return concat_pose_graphs(parts)
 
 
-def pgo_se2(batch=16, n_poses=32, n_lc=8, config_id=1) -> PoseGraphBatch:
+def pgo_se2(batch=16, n_poses=32, n_lc=8, config_id=1, first=0) -> PoseGraphBatch:
     probs = []
-    for b in range(batch):
+    for b in range(first, first + batch):
         rng = _rng(config_id, b)
         probs.append(_pose_graph_se2(rng, n_poses, n_lc, 0.05, 0.01) + (rng,))
     return _assemble(SE2, probs, lambda r, E, d: np.ones((E, d)), lambda r, E: np.zeros(E, np.float32))
 
 
 def pgo_se3(batch=256, n_poses=128, n_lc=None, config_id=2, log_weights=False,
-            n_poses_range: Optional[tuple] = None) -> PoseGraphBatch:
-    """SE(3) pose graphs; ``n_poses_range=(lo, hi)`` draws N_b ~ U{lo..hi} per problem."""
+            n_poses_range: Optional[tuple] = None, first=0) -> PoseGraphBatch:
+    """SE(3) pose graphs; ``n_poses_range=(lo, hi)`` draws N_b ~ U{lo..hi} per problem;
+    problems ``first .. first+batch-1`` of the seeded sequence."""
     probs = []
-    for b in range(batch):
+    for b in range(first, first + batch):
         rng = _rng(config_id, b)
         n = int(rng.integers(n_poses_range[0], n_poses_range[1] + 1)) if n_poses_range else n_poses
         lc = (n // 4) if n_lc is None else n_lc
@@ -284,9 +285,9 @@ def _ring_camera(k: int, n_cams: int, radius: float) -> np.ndarray:
 
 
 def ba(batch=32, n_cams=64, n_pts=4096, k_range=(4, 8), config_id=5, focal=500.0,
-       pixel_sigma=1.0, huber_delta=2.0, prior_weight=100.0) -> BABatch:
+       pixel_sigma=1.0, huber_delta=2.0, prior_weight=100.0, first=0) -> BABatch:
     parts = []
-    for b in range(batch):
+    for b in range(first, first + batch):
         rng = _rng(config_id, b)
         cams_gt = [_ring_camera(k, n_cams, 10.0) for k in range(n_cams)]
         pts_gt = rng.uniform(-2.0, 2.0, size=(n_pts, 3))
@@ -318,7 +319,8 @@ def ba(batch=32, n_cams=64, n_pts=4096, k_range=(4, 8), config_id=5, focal=500.0
 
 # ----------------------------------------------------------------------------- named workloads
 def workload(name: str, batch: Optional[int] = None, **kw):
-    """The five named workloads; ``batch`` shrinks a workload to its first problems (same seeds)."""
+    """The five named workloads; ``batch`` shrinks a workload to its first problems (same seeds);
+    ``first=k`` starts at problem k of the seeded sequence."""
     if name == "pgo_se2_b16":
         return pgo_se2(batch=batch or 16, **kw)
     if name == "pgo_se3_b256":
