@@ -1,18 +1,21 @@
-"""Benchmark: batched LM iterations/s and forward + implicit-backward time on one B300.
+"""Benchmark: batched LM iterations/s and forward + implicit-backward time on B300.
 
-Workload (per GPU): 256 SE(3) pose graphs, 128 poses each (127 chain + 32 loop-closure between
-costs + 1 prior), seeded synthetic data; 20 LM iterations in mixed precision (FP32 residuals,
-Jacobians and J^T W J; FP64 relative poses, gradient, block Cholesky and acceptance), then the
-implicit backward (true Hessian, adjoint solve on the cached factor) w.r.t. measurements and
-log-weights.  One step = reset poses + forward + backward.  Every iteration runs in full: the
-freeze threshold is 0, so each problem executes exactly 20 iterations.
+Default workload (per GPU): 256 SE(3) pose graphs, 128 poses each (127 chain + 32 loop-closure
+between costs + 1 prior), seeded synthetic data; 20 LM iterations in mixed precision (FP32
+residuals, Jacobians and J^T W J; FP64 relative poses, gradient, block Cholesky and acceptance),
+then the implicit backward (true Hessian, adjoint solve preconditioned by the cached factor)
+w.r.t. measurements and log-weights.  One step = reset poses + forward + backward.  Every
+iteration runs in full: the freeze threshold is 0, so each problem executes all its iterations.
+``--workload`` selects the other synthetic workloads: 16 SE(2) graphs (GN, FP64), 256 x 64-pose
+SE(3) graphs with log-weights, 1024 SE(3) graphs of 16..256 poses, and 32 bundle-adjustment
+problems (64 cameras, 4096 points, Huber reprojection costs; backward w.r.t. observations).
 
 Reported next to it: the same solver on the plain FP64 per-problem path (one problem per
 launch, FP64 everywhere), the oracle on the host cores (cpu_baseline), the roofline of the
-dominant kernel (the FP64-bound forward), clocks sampled during the timed region, and an
+dominant work (FP64-bound factorizations), clocks sampled during the timed region, and an
 end-to-end number through the public API with host buffers.
 
-Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--workload W]
 """
 from __future__ import annotations
 
@@ -30,7 +33,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "pgo_se3_b256"
-ITERS = 20
+# problems per GPU of each named workload (algorithm, iterations, precision and lambda0 come
+# from the workload table of the synthetic-data module)
+PER_GPU = {"pgo_se2_b16": 16, "pgo_se3_b256": 256, "pgo_se3_implicit_b256": 256,
+           "pgo_se3_uneven_b1024": 1024, "ba_b32": 32}
 METRIC = "batched LM iters/s (fwd + implicit bwd) vs plain FP64 GPU path at 1e-5"
 
 
@@ -40,6 +46,8 @@ def _args():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(PER_GPU),
+                    help="which synthetic workload (default: the 256 x 128-pose SE(3) batch)")
     ap.add_argument("--no-extras", action="store_true", help="skip baselines (for profiling)")
     ap.add_argument("--batch", type=int, default=0,
                     help="first N problems only (profiling captures); default: the full workload")
@@ -53,6 +61,12 @@ def _dist():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def _setting(name):
+    from paper_2207_09442_b300 import synth
+    algo, iters, precision, lam0 = synth.WORKLOADS[name]
+    return algo, iters, precision, lam0
 
 
 def rank_problems(rank: int, per_rank: int):
@@ -80,6 +94,7 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
+        self.lines = []
 
     def __enter__(self):
         try:
@@ -119,53 +134,395 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def _oracle_sample(batch, idxs, iters, tau, backward=True):
-    """Oracle (FP64 CPU) forward (+ exact implicit backward) on the listed problems; returns
+# ----------------------------------------------------------------------------- oracle samples
+def _oracle_sample(name, batch, idxs, iters, backward=True):
+    """The oracle (FP64 CPU) on the listed problems, forward (+ exact implicit backward):
     (seconds, executed iterations, solutions)."""
-    import torch
-    from oracle import pgo
+    algo, _, _, lam0 = _setting(name)
     t0 = time.perf_counter()
-    n_it = 0
-    sols = {}
+    n_it, sols = 0, {}
+    if name.startswith("ba"):
+        from oracle import ba
+        for b in idxs:
+            P = ba.ba_from_batch(batch, b)
+            th, info = ba.solve(P, algo=algo, iters=iters, lam0=lam0, tau=0.0)
+            n_it += info.iterations
+            sols[b] = th
+            if backward:
+                ba.implicit_grad_obs(P, th, ba.tangent_grad(P, th[0]))
+        return time.perf_counter() - t0, n_it, sols
+    from oracle import pgo
     for b in idxs:
         g = pgo.graph_from_batch(batch, b)
-        th, info = pgo.solve(g, algo="lm", iters=iters, lam0=1e-3, tau=tau)
+        th, info = pgo.solve(g, algo=algo, iters=iters, lam0=lam0, tau=0.0)
         n_it += info.iterations
         sols[b] = th
         if backward:
-            v = pgo.tangent_grad(3, lambda X: pgo.pose_error_loss(3, X, g.theta_gt), th)
+            v = pgo.tangent_grad(g.kind, lambda X: pgo.pose_error_loss(g.kind, X, g.theta_gt), th)
             pgo.implicit_grads(g, th, v, "exact")
     return time.perf_counter() - t0, n_it, sols
 
 
 def run_reference(args):
-    """Reference arm: the FP64 oracle on the host cores, on a bounded sample of the workload."""
+    """Reference arm: the FP64 oracle on the host cores, on a bounded sample of the workload
+    (pose graphs: one problem with all its iterations and the exact implicit backward per step;
+    bundle adjustment: two LM iterations of one problem per step)."""
     rank, world, _ = _dist()
     if rank != 0:
         return
     import torch
     from paper_2207_09442_b300 import synth
-    batch = synth.workload(WORKLOAD, batch=2)
+    name = args.workload
+    algo, iters, _, _ = _setting(name)
+    is_ba = name.startswith("ba")
+    batch = synth.workload(name, batch=2)
+    its_per = 2 if is_ba else iters
     cores = torch.get_num_threads()
-    for _ in range(args.warmup):
-        _oracle_sample(batch, [0], ITERS, 0.0)
+    for _ in range(1 if is_ba else args.warmup):
+        _oracle_sample(name, batch, [0], its_per, backward=not is_ba)
     secs, its = 0.0, 0
     for s in range(args.steps):
-        dt, n, _ = _oracle_sample(batch, [s % 2], ITERS, 0.0)
+        dt, n, _ = _oracle_sample(name, batch, [s % 2], its_per, backward=not is_ba)
         secs += dt
         its += n
     value = its / secs
+    sample = (f"1 problem x {its_per} LM its (whole-system sparse solve) per step" if is_ba else
+              f"1 problem x ({iters} {algo.upper()} its + exact implicit bwd) per step")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "LM iters/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded generator)",
-            "config": {"workload": WORKLOAD, "problems_per_step": 1, "poses": 128,
-                       "lm_iterations": ITERS, "backward": "implicit exact"},
+            "config": {"workload": name, "problems_per_step": 1, "iterations": its_per,
+                       "backward": "none" if is_ba else "implicit exact"},
             "cpu_baseline": {"value": value, "unit": "LM iters/s", "cores": cores, "kind": "oracle",
-                             "sample": "1 problem (128 poses, 20 LM its + implicit bwd) per step"},
+                             "sample": sample},
             "e2e": {"value": value, "unit": "LM iters/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- shared timing
+def _time_steps(step, steps, stream, flush, local):
+    """Per-step CUDA-event times (whole step, forward part) with an L2 flush between steps
+    (outside the events) and clocks sampled during the region."""
+    import torch
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    mids = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for s in range(steps):
+            flush.fill_(s & 0xFF)  # evict the working set from L2 between steps
+            starts[s].record(stream)
+            step(mids[s])
+            ends[s].record(stream)
+        torch.cuda.synchronize()
+    step_ms = [starts[s].elapsed_time(ends[s]) for s in range(steps)]
+    fwd_ms = [starts[s].elapsed_time(mids[s]) for s in range(steps)]
+    return step_ms, fwd_ms, clk.summary()
+
+
+def _timed_region(step, args, world, dist, dev, stream, local):
+    """Warm-up, then exactly ``args.steps`` timed steps between barriers; the max over ranks."""
+    import torch
+    for _ in range(max(3, args.warmup)):
+        step(torch.cuda.Event(enable_timing=True))
+    torch.cuda.synchronize()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 126 MB L2
+    if world > 1:
+        dist.barrier()
+    step_ms, fwd_ms, clocks = _time_steps(step, args.steps, stream, flush, local)
+    if world > 1:
+        dist.barrier()
+    del flush
+    ms_per_step = max_over_ranks(sum(step_ms), dist, dev) / args.steps
+    return ms_per_step, statistics.mean(fwd_ms), statistics.mean(a - b for a, b in zip(step_ms, fwd_ms)), clocks
+
+
+def _fp64_peak(stream):
+    from paper_2207_09442_b300 import dnls
+    f = dnls.c_double()
+    dnls.check(dnls.lib().dnls_probe_fp64_peak(4096, stream.cuda_stream, dnls.ctypes.byref(f)), "probe")
+    return f.value / 1e12
+
+
+def _e2e(run, h_in, h_out, d_in, steps, stream, executed):
+    """End to end through the public API: pinned host inputs copied in, the step, results
+    copied out, all inside the events."""
+    import torch
+
+    def one():
+        for d_, h_ in zip(d_in, h_in):
+            d_.copy_(h_, non_blocking=True)
+        outs = run()
+        for h_, d_ in zip(h_out, outs):
+            h_.copy_(d_, non_blocking=True)
+
+    one()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        one()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    return {"value": executed / (ms * 1e-3), "unit": "LM iters/s",
+            "h2d_bytes_per_step": int(sum(x.numel() * x.element_size() for x in h_in)),
+            "d2h_bytes_per_step": int(sum(x.numel() * x.element_size() for x in h_out)),
+            "ms_per_step": ms}
+
+
+# ----------------------------------------------------------------------------- pose graphs
+def run_pose_graphs(args, rank, world, local, dist, out):
+    import torch
+    from paper_2207_09442_b300 import autotune, layer, synth
+
+    name = args.workload
+    algo, iters, precision, lam0 = _setting(name)
+    dev = torch.device("cuda", local)
+    first, per_rank = rank_problems(rank, args.batch or PER_GPU[name])
+    batch = synth.workload(name, batch=per_rank, first=first)
+    B, dof = batch.batch, batch.dof
+    st = layer.PoseGraphStructure.from_batch(batch)
+    stats = st.stats()
+    opts = layer.Options(algo=algo, iters=iters, precision=precision, tau=0.0,
+                         backward_mode="implicit", lambda0=lam0)
+    t64 = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+    theta0 = t64(batch.theta_init)
+    meas, wd = t64(batch.meas), t64(batch.wdiag)
+    lw = torch.as_tensor(batch.logw, dtype=torch.float32, device=dev)
+    rng = np.random.default_rng(1234)
+    v = t64(rng.normal(size=(st.n_poses, dof)) * 1e-2)  # synthetic outer-loss tangent gradient
+    if args.shape:
+        thr, ctas, smem = (int(x) for x in args.shape.split(","))
+        tuned = {"threads": thr, "ctas_per_sm": ctas, "smem_factor": smem, "table": "fixed by --shape"}
+    else:
+        tuned = autotune.tune(st, opts, (theta0, meas, wd, lw), v, use_cache=False)
+    opts = autotune.apply(opts, tuned)
+    solver = layer.PoseGraphSolver(st, opts, dev)
+    theta = torch.empty_like(theta0)
+    gm = torch.empty(st.n_costs, dof, dtype=torch.float64, device=dev)
+    gl = torch.empty(st.n_costs, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(mid):
+        theta.copy_(theta0)
+        solver.forward(theta, meas, wd, lw, out=theta)
+        mid.record(stream)
+        solver.backward(theta, v, meas, wd, lw, gm, gl)
+
+    step(torch.cuda.Event(enable_timing=True))
+    torch.cuda.synchronize()
+    info = solver.info_dict()
+    executed = int(info["iterations"].sum())
+    ms_per_step, fwd_ms, bwd_ms, clocks = _timed_region(step, args, world, dist, dev, stream, local)
+    sizes = np.diff(batch.pose_offsets)
+    out.update({
+        "value": executed * world / (ms_per_step * 1e-3), "ms_per_step": ms_per_step,
+        "dtype": ("f64" if precision == "fp64" else
+                  "mixed: f32 linearize/assemble, f64 factor/solve/accept/backward"),
+        "data": f"synthetic (seeded generator, random-walk SE({batch.kind}) graphs)",
+        "config": {"workload": name, "problems": B,
+                   "poses": (int(sizes[0]) if sizes.min() == sizes.max()
+                             else f"{int(sizes.min())}..{int(sizes.max())}"),
+                   "costs": st.n_costs, "iterations": iters, "algorithm": algo.upper(),
+                   "precision": precision,
+                   "backward": "implicit, true Hessian, cached factor + refinement",
+                   "parallelism": f"{world} GPU(s), problems sharded by rank (weak)",
+                   "l2": "flushed between steps"},
+        "fwd_ms": fwd_ms, "bwd_ms": bwd_ms,
+        "executed_lm_iterations_per_step": executed, "gpu_launches": 2 * args.steps,
+        "launch_shape": {k: tuned[k] for k in ("threads", "ctas_per_sm", "smem_factor")},
+        "autotune_table": tuned["table"],
+        "backward_refine_steps_mean": float(np.mean(info["refine_steps"])),
+        "backward_not_converged": int((info["status"] == 1).sum()),
+        "clocks": clocks})
+    if args.no_extras or rank != 0:
+        return
+    # roofline of the dominant kernel (the forward, FP64-factorization bound): algorithmic FP64
+    # flops of the factorizations it runs / its duration, against the FP64 FMA peak probed now
+    peak = _fp64_peak(stream)
+    achieved = stats["factor_flops"] / B * executed / (fwd_ms * 1e-3) / 1e12
+    out["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                       "frac": achieved / peak, "traffic": None,
+                       "kernel": f"k_forward<{batch.kind},{'double' if precision == 'fp64' else 'float'}>"
+                                 " (FP64 block Cholesky flops)",
+                       "peak_source": "FP64 FMA probe on this GPU (dnls_probe_fp64_peak), of measured"}
+    out["factor"] = {"flops_per_factorization_batch": stats["factor_flops"],
+                     "dense_equivalent_flops": stats["dense_flops"],
+                     "block_updates": stats["n_block_updates"], "levels_max": stats["n_levels_max"]}
+    # accuracy at this configuration against the oracle on sampled problems
+    sample = sorted({0, B // 2, B - 1, int(sizes.argmax())})
+    _, _, sols = _oracle_sample(name, batch, sample, iters, backward=False)
+    th_cpu = theta.cpu()
+    errs = [float((th_cpu[int(batch.pose_offsets[b]):int(batch.pose_offsets[b + 1])] - sols[b]).norm()
+                  / sols[b].norm()) for b in sample]
+    out["accuracy"] = {"max_rel_err_vs_oracle": max(errs), "sampled_problems": sample,
+                       "tolerance": 1e-9 if precision == "fp64" else 1e-5}
+    # plain FP64 per-problem GPU path: same kernels, FP64 everywhere, one problem per launch
+    nplain = min(8, B)
+    per = []
+    for b_ in range(nplain):
+        one = batch.problem(b_)
+        s1 = layer.PoseGraphSolver(layer.PoseGraphStructure.from_batch(one),
+                                   layer.Options(algo=algo, iters=iters, precision="fp64", tau=0.0,
+                                                 lambda0=lam0), dev)
+        a1 = [t64(one.theta_init), t64(one.meas), t64(one.wdiag),
+              torch.as_tensor(one.logw, dtype=torch.float32, device=dev)]
+        v1 = t64(rng.normal(size=(int(one.pose_offsets[-1]), dof)) * 1e-2)
+        s1.backward(s1.forward(*a1), v1, *a1[1:])
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s1.backward(s1.forward(*a1), v1, *a1[1:])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        per.append(e0.elapsed_time(e1))
+    plain_ms = statistics.mean(per) * B
+    out["plain_fp64_per_problem"] = {"ms_per_batch": plain_ms, "lm_iters_per_s": executed / (plain_ms * 1e-3),
+                                     "sample": f"{nplain} problems timed one launch each, x{B}"}
+    out["speedup_vs_plain_fp64"] = plain_ms / ms_per_step
+    # end to end through the public API with host (pinned) buffers
+    h_in = [torch.as_tensor(np.ascontiguousarray(a)).pin_memory() for a in
+            (batch.theta_init, batch.meas, batch.wdiag, batch.logw)] + [v.cpu().pin_memory()]
+    d_in = [torch.empty_like(x, device=dev) for x in h_in]
+    h_out = [torch.empty(x.shape, dtype=x.dtype).pin_memory() for x in (theta, gm, gl)]
+
+    def run():
+        solver.forward(d_in[0], d_in[1], d_in[2], d_in[3], out=d_in[0])
+        solver.backward(d_in[0], d_in[4], d_in[1], d_in[2], d_in[3], gm, gl)
+        return d_in[0], gm, gl
+
+    out["e2e"] = _e2e(run, h_in, h_out, d_in, args.steps, stream, executed)
+    # CPU baseline: the oracle as it stands on a bounded sample (2 problems, fwd + bwd)
+    secs, its, _ = _oracle_sample(name, batch, list(range(min(2, B))), iters)
+    out["cpu_baseline"] = {"value": its / secs, "unit": "LM iters/s", "cores": torch.get_num_threads(),
+                           "kind": "oracle",
+                           "sample": f"{min(2, B)} problems x ({iters} {algo.upper()} its + exact "
+                                     "implicit bwd), FP64 torch CPU"}
+
+
+# ----------------------------------------------------------------------------- bundle adjustment
+def ba_launches(iters: int, refine_max: int) -> int:
+    """Kernels one bundle-adjustment forward + backward launches (the launch sequence of the
+    library's BA entry points: 6 + 10 per iteration forward, 16 + 8 per PCG step backward)."""
+    return 6 + 10 * iters + 16 + 8 * refine_max
+
+
+def run_ba(args, rank, world, local, dist, out):
+    import torch
+    from paper_2207_09442_b300 import ba_layer, layer, synth
+
+    name = args.workload
+    algo, iters, precision, lam0 = _setting(name)
+    dev = torch.device("cuda", local)
+    first, per_rank = rank_problems(rank, args.batch or PER_GPU[name])
+    b = synth.workload(name, batch=per_rank, first=first)
+    st = ba_layer.BAStructure.from_batch(b)
+    opts = layer.Options(algo=algo, iters=iters, precision=precision, tau=0.0, lambda0=lam0)
+    solver = ba_layer.BASolver(st, opts, dev)
+    t64 = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+    cams0, pts0 = t64(b.cams_init), t64(b.pts_init)
+    obs, pm, pw = t64(b.obs_uv), t64(b.prior_meas), t64(b.prior_wdiag)
+    rng = np.random.default_rng(1234)
+    v_c = t64(rng.normal(size=(st.n_cams, 6)) * 1e-2)  # synthetic outer-loss camera gradient
+    v_p = torch.zeros(st.n_pts, 3, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    res = {}
+
+    def step(mid):
+        cams, pts = solver.forward(cams0, pts0, obs, pm, pw, b.focal, b.huber_delta)
+        mid.record(stream)
+        res["g"] = solver.backward(cams, pts, v_c, v_p, obs, pm, pw, b.focal, b.huber_delta)
+        res["sol"] = (cams, pts)
+
+    step(torch.cuda.Event(enable_timing=True))
+    torch.cuda.synchronize()
+    info = solver.info_dict()
+    executed = int(info["iterations"].sum())
+    ms_per_step, fwd_ms, bwd_ms, clocks = _timed_region(step, args, world, dist, dev, stream, local)
+    C, Pn = int(np.diff(b.cam_offsets)[0]), int(np.diff(b.pt_offsets)[0])
+    out.update({
+        "value": executed * world / (ms_per_step * 1e-3), "ms_per_step": ms_per_step,
+        "dtype": "mixed: f32 reprojection linearize, f64 Schur/factor/solve/accept/backward",
+        "data": "synthetic (seeded generator: ring of cameras, uniform points, 1 px noise)",
+        "config": {"workload": name, "problems": b.batch, "cameras": C, "points": Pn,
+                   "observations": int(b.obs_offsets[-1]), "iterations": iters,
+                   "algorithm": algo.upper(), "precision": precision,
+                   "robust_loss": f"Huber, delta {b.huber_delta} px",
+                   "backward": "implicit w.r.t. observations, true Hessian, PCG on the Schur factor",
+                   "parallelism": f"{world} GPU(s), problems sharded by rank (weak)",
+                   "l2": "flushed between steps"},
+        "fwd_ms": fwd_ms, "bwd_ms": bwd_ms,
+        "executed_lm_iterations_per_step": executed,
+        "gpu_launches": args.steps * ba_launches(iters, opts.refine_max),
+        "backward_refine_steps_mean": float(np.mean(info["refine_steps"])),
+        "backward_not_converged": int((info["status"] == 1).sum()),
+        "clocks": clocks})
+    if args.no_extras or rank != 0:
+        return
+    # roofline of the forward: per iteration the Schur gathers (a point seen k times adds
+    # k(k+1)/2 products Y_i W_j^T of 6x3x6 FMAs) plus the Cholesky of the reduced camera system
+    # (dense: every camera pair shares points), FP64 flops / forward time vs the FP64 peak
+    peak = _fp64_peak(stream)
+    pairs = 0
+    for p in range(b.batch):
+        k = np.bincount(b.obs_pt[b.obs_offsets[p]:b.obs_offsets[p + 1]])
+        pairs += int((k * (k + 1) // 2).sum())
+    n_red = 6 * C
+    flops_iter = (2.0 * 108 * pairs + b.batch * n_red ** 3 / 3.0) / b.batch
+    achieved = flops_iter * executed / (fwd_ms * 1e-3) / 1e12
+    out["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                       "frac": achieved / peak, "traffic": None,
+                       "kernel": "BA forward launch sequence (Schur gathers + reduced Cholesky)",
+                       "peak_source": "FP64 FMA probe on this GPU (dnls_probe_fp64_peak), of measured"}
+    # accuracy on problem 0 against the oracle's whole-system sparse LM
+    _, _, sols = _oracle_sample(name, b, [0], iters, backward=False)
+    cams, pts = res["sol"]
+    ref = torch.cat([sols[0][0].reshape(-1), sols[0][1].reshape(-1)])
+    got = torch.cat([cams[:C].cpu().reshape(-1), pts[:Pn].cpu().reshape(-1)])
+    out["accuracy"] = {"max_rel_err_vs_oracle": float((got - ref).norm() / ref.norm()),
+                       "sampled_problems": [0], "tolerance": 1e-5}
+    # plain FP64 per-problem GPU path: problem 0 alone, FP64 everywhere, times the batch size
+    one = b.problem(0)
+    s1 = ba_layer.BASolver(ba_layer.BAStructure.from_batch(one),
+                           layer.Options(algo=algo, iters=iters, precision="fp64", tau=0.0,
+                                         lambda0=lam0), dev)
+    a1 = (t64(one.cams_init), t64(one.pts_init), t64(one.obs_uv), t64(one.prior_meas), t64(one.prior_wdiag))
+
+    def plain():
+        c1, p1 = s1.forward(*a1, one.focal, one.huber_delta)
+        s1.backward(c1, p1, v_c[:C], v_p[:Pn], *a1[2:], one.focal, one.huber_delta)
+
+    plain()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    plain()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    plain_ms = e0.elapsed_time(e1) * b.batch
+    out["plain_fp64_per_problem"] = {"ms_per_batch": plain_ms, "lm_iters_per_s": executed / (plain_ms * 1e-3),
+                                     "sample": f"problem 0 timed alone, x{b.batch}"}
+    out["speedup_vs_plain_fp64"] = plain_ms / ms_per_step
+    # end to end through the public API with host (pinned) buffers
+    h_in = [torch.as_tensor(np.ascontiguousarray(a)).pin_memory() for a in
+            (b.cams_init, b.pts_init, b.obs_uv)] + [v_c.cpu().pin_memory()]
+    d_in = [torch.empty_like(x, device=dev) for x in h_in]
+    h_out = [torch.empty(s, dtype=torch.float64).pin_memory()
+             for s in ((st.n_cams, 12), (st.n_pts, 3), (st.n_obs, 2))]
+
+    def run():
+        c, p = solver.forward(d_in[0], d_in[1], d_in[2], pm, pw, b.focal, b.huber_delta)
+        g = solver.backward(c, p, d_in[3], v_p, d_in[2], pm, pw, b.focal, b.huber_delta)
+        return c, p, g
+
+    out["e2e"] = _e2e(run, h_in, h_out, d_in, args.steps, stream, executed)
+    secs, its, _ = _oracle_sample(name, b, [0], 2, backward=False)
+    out["cpu_baseline"] = {"value": its / secs, "unit": "LM iters/s", "cores": torch.get_num_threads(),
+                           "kind": "oracle",
+                           "sample": "problem 0 x 2 LM iterations (whole-system sparse solve, no Schur)"}
 
 
 def main():
@@ -178,201 +535,23 @@ def main():
     import torch.distributed as dist
 
     from paper_2207_09442_b300 import build as _build
-    from paper_2207_09442_b300 import dnls, layer, synth
 
     if world > 1:
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
     if rank == 0:
         _build.build()
     if world > 1:
         dist.barrier()
-
-    # every rank solves its own 256-problem batch (weak scaling)
-    first, per_rank = rank_problems(rank, args.batch or 256)
-    batch = synth.workload(WORKLOAD, batch=per_rank, first=first)
-    B = batch.batch
-    st = layer.PoseGraphStructure.from_batch(batch)
-    stats = st.stats()
-    opts = layer.Options(algo="lm", iters=ITERS, precision="mixed_fp32", tau=0.0,
-                         backward_mode="implicit")
-    t64 = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
-    theta0 = t64(batch.theta_init)
-    meas, wd = t64(batch.meas), t64(batch.wdiag)
-    lw = torch.as_tensor(batch.logw, dtype=torch.float32, device=dev)
-    rng = np.random.default_rng(1234)
-    v = t64(rng.normal(size=(st.n_poses, 6)) * 1e-2)  # synthetic outer-loss tangent gradient
-    from paper_2207_09442_b300 import autotune
-    if args.shape:
-        thr, ctas, smem = (int(x) for x in args.shape.split(","))
-        tuned = {"threads": thr, "ctas_per_sm": ctas, "smem_factor": smem, "table": "fixed by --shape"}
+    out = {"metric": METRIC, "value": None, "unit": "LM iters/s", "n_gpus": world,
+           "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": None,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None}
+    if args.workload.startswith("ba"):
+        run_ba(args, rank, world, local, dist, out)
     else:
-        tuned = autotune.tune(st, opts, (theta0, meas, wd, lw), v, use_cache=False)
-    opts = autotune.apply(opts, tuned)
-    solver = layer.PoseGraphSolver(st, opts, dev)
-    theta = torch.empty_like(theta0)
-    gm = torch.empty(st.n_costs, 6, dtype=torch.float64, device=dev)
-    gl = torch.empty(st.n_costs, dtype=torch.float64, device=dev)
-    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 126 MB L2
-    stream = torch.cuda.current_stream()
-
-    def step():
-        theta.copy_(theta0)
-        solver.forward(theta, meas, wd, lw, out=theta)
-        ev_mid.record(stream)
-        solver.backward(theta, v, meas, wd, lw, gm, gl)
-
-    for _ in range(max(3, args.warmup)):
-        ev_mid = torch.cuda.Event(enable_timing=True)
-        step()
-    torch.cuda.synchronize()
-    info_b = solver.info_dict()
-    executed = int(info_b["iterations"].sum())
-
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    mids = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        for s in range(args.steps):
-            flush.fill_(s & 0xFF)  # evict the workspace from L2 between steps (not timed)
-            starts[s].record(stream)
-            ev_mid = mids[s]
-            step()
-            ends[s].record(stream)
-        torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    step_ms = [starts[s].elapsed_time(ends[s]) for s in range(args.steps)]
-    fwd_ms = [starts[s].elapsed_time(mids[s]) for s in range(args.steps)]
-    total_ms = max_over_ranks(sum(step_ms), dist, dev)
-    ms_per_step = total_ms / args.steps
-    value = executed * world / (ms_per_step * 1e-3)
-    clocks = clk.summary()
-
-    if rank != 0:
-        if world > 1:
-            dist.barrier()
-        return
-
-    out = {"metric": METRIC, "value": value, "unit": "LM iters/s", "n_gpus": world,
-           "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms_per_step,
-           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": "mixed: f32 linearize/assemble, f64 factor/solve/accept/backward",
-           "data": "synthetic (seeded generator, random-walk SE(3) graphs)",
-           "config": {"workload": WORKLOAD, "problems": B, "poses": 128, "costs_per_problem": 160,
-                      "lm_iterations": ITERS, "precision": "mixed_fp32",
-                      "backward": "implicit, true Hessian, cached factor + refinement",
-                      "parallelism": f"{world} GPU(s), batch sharded (weak)", "l2": "flushed between steps"},
-           "fwd_ms": statistics.mean(fwd_ms), "bwd_ms": statistics.mean(a - b for a, b in zip(step_ms, fwd_ms)),
-           "executed_lm_iterations_per_step": executed, "gpu_launches": 2 * args.steps,
-           "launch_shape": {k: tuned[k] for k in ("threads", "ctas_per_sm", "smem_factor")},
-           "autotune_table": tuned["table"],
-           "backward_refine_steps_mean": float(np.mean(info_b["refine_steps"])),
-           "backward_not_converged": int((info_b["status"] == 1).sum()),
-           "clocks": clocks}
-
-    if not args.no_extras:
-        # roofline of the dominant kernel (forward, FP64 factorization bound): algorithmic FP64
-        # flops of the factorizations it runs / its duration, against the FP64 FMA peak probed now
-        f = dnls.c_double()
-        dnls.check(dnls.lib().dnls_probe_fp64_peak(4096, stream.cuda_stream, dnls.ctypes.byref(f)),
-                   "probe")
-        peak = f.value / 1e12
-        flops_fwd = stats["factor_flops"] / B * executed
-        achieved = flops_fwd / (statistics.mean(fwd_ms) * 1e-3) / 1e12
-        out["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                           "frac": achieved / peak, "traffic": None,
-                           "kernel": "k_forward<3,float> (FP64 block Cholesky flops)",
-                           "peak_source": "FP64 FMA probe on this GPU (dnls_probe_fp64_peak)"}
-        out["factor"] = {"flops_per_factorization_batch": stats["factor_flops"],
-                         "dense_equivalent_flops": stats["dense_flops"],
-                         "block_updates": stats["n_block_updates"], "levels_max": stats["n_levels_max"]}
-        # accuracy at this configuration against the oracle on sampled problems
-        from oracle import pgo
-        sample = [0, B // 2, B - 1]
-        _, _, sols = _oracle_sample(batch, sample, ITERS, 0.0, backward=False)
-        errs = []
-        th_cpu = theta.cpu()
-        for b_ in sample:
-            ref = sols[b_]
-            got = th_cpu[int(batch.pose_offsets[b_]):int(batch.pose_offsets[b_ + 1])]
-            errs.append(float((got - ref).norm() / ref.norm()))
-        out["accuracy"] = {"max_rel_err_vs_oracle": max(errs), "sampled_problems": sample,
-                           "tolerance": 1e-5}
-        # plain FP64 per-problem GPU path: same kernels, FP64 everywhere, one problem per launch
-        nplain = 8
-        per = []
-        for b_ in range(nplain):
-            one = batch.problem(b_)
-            st1 = layer.PoseGraphStructure.from_batch(one)
-            s1 = layer.PoseGraphSolver(st1, layer.Options(algo="lm", iters=ITERS, precision="fp64",
-                                                          tau=0.0), dev)
-            a = [t64(one.theta_init), t64(one.meas), t64(one.wdiag),
-                 torch.as_tensor(one.logw, dtype=torch.float32, device=dev)]
-            v1 = t64(rng.normal(size=(st1.n_poses, 6)) * 1e-2)
-            th1 = s1.forward(*a)
-            s1.backward(th1, v1, *a[1:])
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            th1 = s1.forward(*a)
-            s1.backward(th1, v1, *a[1:])
-            e1.record(stream)
-            torch.cuda.synchronize()
-            per.append(e0.elapsed_time(e1))
-        plain_ms = statistics.mean(per) * B
-        out["plain_fp64_per_problem"] = {"ms_per_batch": plain_ms,
-                                         "lm_iters_per_s": B * ITERS / (plain_ms * 1e-3),
-                                         "sample": f"{nplain} problems timed one launch each, x{B}"}
-        out["speedup_vs_plain_fp64"] = plain_ms / ms_per_step
-        # end to end through the public API with host buffers (pinned), copies inside the region
-        h_in = [torch.as_tensor(a).pin_memory() for a in
-                (np.ascontiguousarray(batch.theta_init), np.ascontiguousarray(batch.meas),
-                 np.ascontiguousarray(batch.wdiag))]
-        h_lw = torch.as_tensor(batch.logw).pin_memory()
-        h_v = v.cpu().pin_memory()
-        h_out = [torch.empty(theta.shape, dtype=torch.float64).pin_memory(),
-                 torch.empty(gm.shape, dtype=torch.float64).pin_memory(),
-                 torch.empty(gl.shape, dtype=torch.float64).pin_memory()]
-        d_in = [torch.empty_like(x, device=dev) for x in h_in]
-        d_lw = torch.empty_like(h_lw, device=dev)
-        d_v = torch.empty_like(h_v, device=dev)
-        h2d = sum(x.numel() * x.element_size() for x in h_in) + h_lw.numel() * 4 + h_v.numel() * 8
-        d2h = sum(x.numel() * x.element_size() for x in h_out)
-
-        def e2e_step():
-            for d, h in zip(d_in, h_in):
-                d.copy_(h, non_blocking=True)
-            d_lw.copy_(h_lw, non_blocking=True)
-            d_v.copy_(h_v, non_blocking=True)
-            solver.forward(d_in[0], d_in[1], d_in[2], d_lw, out=d_in[0])
-            solver.backward(d_in[0], d_v, d_in[1], d_in[2], d_lw, gm, gl)
-            h_out[0].copy_(d_in[0], non_blocking=True)
-            h_out[1].copy_(gm, non_blocking=True)
-            h_out[2].copy_(gl, non_blocking=True)
-
-        e2e_step()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.steps):
-            e2e_step()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        e2e_ms = e0.elapsed_time(e1) / args.steps
-        out["e2e"] = {"value": executed / (e2e_ms * 1e-3), "unit": "LM iters/s",
-                      "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                      "ms_per_step": e2e_ms}
-        # CPU baseline: the oracle as it stands on a bounded sample (2 problems, fwd + bwd)
-        secs, its, _ = _oracle_sample(batch, [0, 1], ITERS, 0.0)
-        out["cpu_baseline"] = {"value": its / secs, "unit": "LM iters/s",
-                               "cores": torch.get_num_threads(), "kind": "oracle",
-                               "sample": "2 problems x (20 LM its + exact implicit bwd), FP64 torch CPU"}
-    print(json.dumps(out), flush=True)
+        run_pose_graphs(args, rank, world, local, dist, out)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
