@@ -38,6 +38,31 @@ WORKLOAD = "pgo_se3_b256"
 PER_GPU = {"pgo_se2_b16": 16, "pgo_se3_b256": 256, "pgo_se3_implicit_b256": 256,
            "pgo_se3_uneven_b1024": 1024, "ba_b32": 32}
 METRIC = "batched LM iters/s (fwd + implicit bwd) vs plain FP64 GPU path at 1e-5"
+# DRAM bytes (read + write) per launch of the dominant kernel, from an ncu capture of the forward
+# kernel's sources as they hash here (profiles/k_forward_pgo_se3_b64_full.md: 64-problem case,
+# scaled by 256/64 since every problem owns its own inputs and workspace region).  Reported only
+# while the sources still hash to the captured build; null otherwise.
+FORWARD_SOURCES = ["dnls_graph.cu", "dnls_blockchol.cuh", "dnls_cost.cuh", "dnls_lie.cuh",
+                   "dnls_graph.h", "dnls_symbolic.cpp"]
+CAPTURED_TRAFFIC = {"pgo_se3_b256": ("6a7bbcca69d88f6b", (4.624384e6 + 1.931264e6) * 256 / 64)}
+
+
+def forward_sources_sha() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in FORWARD_SOURCES:
+        with open(os.path.join(ROOT, "paper_2207_09442_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def captured_traffic(workload: str, batch: int):
+    """Captured DRAM bytes per forward launch for this workload, or None when the capture does
+    not apply (other workload or batch size, or kernel sources changed since)."""
+    rec = CAPTURED_TRAFFIC.get(workload)
+    if rec is None or batch != PER_GPU[workload] or forward_sources_sha() != rec[0]:
+        return None
+    return rec[1]
 
 
 def _args():
@@ -100,14 +125,23 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
         return self
 
+    def wait_first_sample(self, timeout=5.0):
+        """Block until nvidia-smi has printed its first sample (it takes ~0.1-0.5 s to start)."""
+        if self.proc is None:
+            return
+        import select
+        r, _, _ = select.select([self.proc.stdout], [], [], timeout)
+        if r:
+            self.first = self.proc.stdout.readline()
+
     def __exit__(self, *a):
-        self.lines = []
+        self.lines = [self.first] if getattr(self, "first", "").strip() else []
         if self.proc is not None:
             self.proc.terminate()
             try:
@@ -115,7 +149,7 @@ class ClockSampler:
             except subprocess.TimeoutExpired:
                 self.proc.kill()
                 out, _ = self.proc.communicate()
-            self.lines = [l for l in out.splitlines() if l.strip()]
+            self.lines += [l for l in out.splitlines() if l.strip()]
 
     def summary(self):
         sm, mx, reasons = [], None, set()
@@ -131,7 +165,8 @@ class ClockSampler:
                 if v.lower() == "active":
                     reasons.add(n)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
-                "samples": len(sm), "reasons": sorted(reasons)}
+                "samples": len(sm), "window": "warm-up + timed steps, 100 ms period",
+                "reasons": sorted(reasons)}
 
 
 # ----------------------------------------------------------------------------- oracle samples
@@ -202,39 +237,37 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------- shared timing
-def _time_steps(step, steps, stream, flush, local):
-    """Per-step CUDA-event times (whole step, forward part) with an L2 flush between steps
-    (outside the events) and clocks sampled during the region."""
+def _timed_region(step, args, world, dist, dev, stream, local):
+    """Warm-up, then exactly ``args.steps`` timed steps between barriers (per-step CUDA events
+    for the whole step and its forward part, an L2 flush between steps outside the events); the
+    max over ranks.  Clocks are sampled from before the warm-up to the end of the timed steps,
+    so that short timed regions still get samples taken under the same load."""
     import torch
+    steps = args.steps
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 126 MB L2
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     mids = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
-    torch.cuda.synchronize()
     with ClockSampler(local) as clk:
+        clk.wait_first_sample()
+        for _ in range(max(3, args.warmup)):
+            step(torch.cuda.Event(enable_timing=True))
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
         for s in range(steps):
             flush.fill_(s & 0xFF)  # evict the working set from L2 between steps
             starts[s].record(stream)
             step(mids[s])
             ends[s].record(stream)
         torch.cuda.synchronize()
-    step_ms = [starts[s].elapsed_time(ends[s]) for s in range(steps)]
-    fwd_ms = [starts[s].elapsed_time(mids[s]) for s in range(steps)]
-    return step_ms, fwd_ms, clk.summary()
-
-
-def _timed_region(step, args, world, dist, dev, stream, local):
-    """Warm-up, then exactly ``args.steps`` timed steps between barriers; the max over ranks."""
-    import torch
-    for _ in range(max(3, args.warmup)):
-        step(torch.cuda.Event(enable_timing=True))
-    torch.cuda.synchronize()
-    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 126 MB L2
-    if world > 1:
-        dist.barrier()
-    step_ms, fwd_ms, clocks = _time_steps(step, args.steps, stream, flush, local)
     if world > 1:
         dist.barrier()
     del flush
+    step_ms = [starts[s].elapsed_time(ends[s]) for s in range(steps)]
+    fwd_ms = [starts[s].elapsed_time(mids[s]) for s in range(steps)]
+    clocks = clk.summary()
     ms_per_step = max_over_ranks(sum(step_ms), dist, dev) / args.steps
     return ms_per_step, statistics.mean(fwd_ms), statistics.mean(a - b for a, b in zip(step_ms, fwd_ms)), clocks
 
@@ -345,7 +378,7 @@ def run_pose_graphs(args, rank, world, local, dist, out):
     peak = _fp64_peak(stream)
     achieved = stats["factor_flops"] / B * executed / (fwd_ms * 1e-3) / 1e12
     out["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                       "frac": achieved / peak, "traffic": None,
+                       "frac": achieved / peak, "traffic": captured_traffic(name, B),
                        "kernel": f"k_forward<{batch.kind},{'double' if precision == 'fp64' else 'float'}>"
                                  " (FP64 block Cholesky flops)",
                        "peak_source": "FP64 FMA probe on this GPU (dnls_probe_fp64_peak), of measured"}
@@ -358,8 +391,21 @@ def run_pose_graphs(args, rank, world, local, dist, out):
     th_cpu = theta.cpu()
     errs = [float((th_cpu[int(batch.pose_offsets[b]):int(batch.pose_offsets[b + 1])] - sols[b]).norm()
                   / sols[b].norm()) for b in sample]
+    # implicit gradients of two sampled problems against the oracle's exact-Hessian gradients,
+    # both at the GPU's theta* (Eq. 3 is evaluated where the forward stopped)
+    from oracle import pgo
+    gerrs = []
+    gm_cpu, gl_cpu, v_cpu = gm.cpu(), gl.cpu(), v.cpu()
+    for b_ in sample[:2]:
+        p0, p1 = int(batch.pose_offsets[b_]), int(batch.pose_offsets[b_ + 1])
+        e0, e1 = int(batch.edge_offsets[b_]), int(batch.edge_offsets[b_ + 1])
+        rm, rl, _ = pgo.implicit_grads(pgo.graph_from_batch(batch, b_), th_cpu[p0:p1], v_cpu[p0:p1], "exact")
+        gerrs.append(max(float((gm_cpu[e0:e1] - rm).norm() / rm.norm()),
+                         float((gl_cpu[e0:e1] - rl).norm() / rl.norm())))
     out["accuracy"] = {"max_rel_err_vs_oracle": max(errs), "sampled_problems": sample,
-                       "tolerance": 1e-9 if precision == "fp64" else 1e-5}
+                       "tolerance": 1e-9 if precision == "fp64" else 1e-5,
+                       "grad_max_rel_err_vs_oracle": max(gerrs), "grad_sampled_problems": sample[:2],
+                       "grad_tolerance": 1e-8 if precision == "fp64" else 1e-4}
     # plain FP64 per-problem GPU path: same kernels, FP64 everywhere, one problem per launch
     nplain = min(8, B)
     per = []
@@ -478,12 +524,20 @@ def run_ba(args, rank, world, local, dist, out):
                        "kernel": "BA forward launch sequence (Schur gathers + reduced Cholesky)",
                        "peak_source": "FP64 FMA probe on this GPU (dnls_probe_fp64_peak), of measured"}
     # accuracy on problem 0 against the oracle's whole-system sparse LM
+    from oracle import ba as oba
     _, _, sols = _oracle_sample(name, b, [0], iters, backward=False)
     cams, pts = res["sol"]
     ref = torch.cat([sols[0][0].reshape(-1), sols[0][1].reshape(-1)])
     got = torch.cat([cams[:C].cpu().reshape(-1), pts[:Pn].cpu().reshape(-1)])
+    P0 = oba.ba_from_batch(b, 0)
+    th0 = (cams[:C].cpu(), pts[:Pn].cpu())
+    v0 = torch.cat([v_c[:C].cpu().reshape(-1), torch.zeros(3 * Pn, dtype=torch.float64)])
+    rg, _ = oba.implicit_grad_obs(P0, th0, v0)
+    g0 = res["g"][:int(b.obs_offsets[1])].cpu()
     out["accuracy"] = {"max_rel_err_vs_oracle": float((got - ref).norm() / ref.norm()),
-                       "sampled_problems": [0], "tolerance": 1e-5}
+                       "sampled_problems": [0], "tolerance": 1e-5,
+                       "grad_max_rel_err_vs_oracle": float((g0 - rg).norm() / rg.norm()),
+                       "grad_sampled_problems": [0], "grad_tolerance": 1e-4}
     # plain FP64 per-problem GPU path: problem 0 alone, FP64 everywhere, times the batch size
     one = b.problem(0)
     s1 = ba_layer.BASolver(ba_layer.BAStructure.from_batch(one),
