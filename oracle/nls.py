@@ -107,3 +107,20 @@ def lm_loop(linearize: Callable, objective: Callable, retract: Callable, theta0,
         if frozen:
             break
     return theta, SolveInfo(S0, float(S), done, accepted, lam, status, hist if record else [])
+
+
+def dlm_direct_step(J, r, v, eps):
+    """The one Gauss-Newton step from theta* that gives theta_direct in direct loss minimization
+    (Sec. 4.3 "Direct loss minimization"; App. G, "DLM for use in Theseus"):
+
+        theta_direct = argmin_xi  S(theta* (+) xi) + || eps xi - v / 2 ||^2
+
+    with the added term measured in the tangent chart at theta* (so theta* sits at xi = 0).
+    Written as a sum of squares, 1/2 ||r||^2 + 1/2 ||sqrt(2) (eps xi - v/2)||^2, its GN normal
+    equations at xi = 0 are (J^T J + 2 eps^2 I) delta = eps v - J^T r.  J, r dense torch."""
+    n = J.shape[1]
+    A = J.T @ J + 2.0 * eps * eps * torch.eye(n, dtype=J.dtype)
+    rhs = eps * v - J.T @ r
+    L = torch.linalg.cholesky(A)
+    return torch.cholesky_solve(rhs[:, None], L)[:, 0]
+

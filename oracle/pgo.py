@@ -19,6 +19,8 @@ What it follows:
     theta* (+) xi the "exact" mode uses the true Hessian d^2 S / d xi^2 at xi = 0; the "gn" mode
     uses sum J^T J (what a Gauss-Newton implementation differentiates).
   * Unrolled backward (Sec. 4.3 "Unrolling"): autograd through every iteration of this solver.
+  * Direct loss minimization (Sec. 4.3, App. G): g_DLM = (dS/dphi(theta*) - dS/dphi(theta_direct))
+    / eps, theta_direct one GN step from theta* on S + ||eps xi - v/2||^2 (see nls.dlm_direct_step).
 
 J, the exact Hessian and the mixed derivatives D_phi g all come from autograd through the residual
 definitions (per-cost local derivatives, vmapped), scattered into dense matrices; linear systems
@@ -289,6 +291,31 @@ def implicit_grads(g: Graph, theta_star, v, mode="exact"):
                                           x[g.ej.clamp(min=0)])], 1)
     gphi = -torch.einsum('ekp,ek->ep', M, xe)
     return gphi[:, :dof], gphi[:, dof], x
+
+
+def dphi_objective(g: Graph, theta):
+    """dS/dphi at theta for phi = (measurement tangents eps_e [E, dof], log-weights l_e [E]),
+    by autograd through Eq. 1."""
+    E, dof = g.ei.shape[0], g.dof
+    eps = torch.zeros(E, dof, dtype=F64, requires_grad=True)
+    logw = g.logw.clone().requires_grad_(True)
+    S = objective(g, theta, eps=eps, logw=logw)
+    ge, gl = torch.autograd.grad(S, (eps, logw))
+    return ge, gl
+
+
+def dlm_grads(g: Graph, theta_star, v, eps=1e-2):
+    """Direct-loss-minimization gradient (Sec. 4.3, App. G) for the tangent gradient v [N, dof]:
+    theta_direct = theta* (+) delta from one GN step on S + ||eps xi - v/2||^2, then
+    (dS/dphi(theta*) - dS/dphi(theta_direct)) / eps.  Returns (grad_meas [E, dof],
+    grad_logw [E], theta_direct)."""
+    dof = g.dof
+    r, J = jacobian(g, theta_star)
+    delta = nls.dlm_direct_step(J, r, v.reshape(-1), eps)
+    theta_d = lie.pose_retract(g.kind, theta_star, delta.reshape(-1, dof))
+    ge0, gl0 = dphi_objective(g, theta_star)
+    ge1, gl1 = dphi_objective(g, theta_d)
+    return (ge0 - ge1) / eps, (gl0 - gl1) / eps, theta_d
 
 
 def unrolled_grads(g: Graph, loss_fn: Callable, algo="lm", iters=20, lam0=1e-3, tau=1e-14):

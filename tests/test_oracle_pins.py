@@ -355,6 +355,67 @@ def test_implicit_exact_matches_fd_and_unrolled_noisy():
     assert float((gn_e - ge).norm() / ge.norm()) > 1e-5
 
 
+# ----------------------------------------------------------------------------- direct loss minimization
+def test_dlm_direct_step_is_the_argmin_of_the_augmented_linear_problem():
+    """On a linear least-squares problem one GN step is exact, so theta_direct must be the
+    minimiser of 1/2||A t - b||^2 + ||eps (t - t*) - v/2||^2, found here by LAPACK's
+    least-squares solve of the stacked residual (pins the factor 2 eps^2, the sign of eps v and
+    the v/2)."""
+    rng = np.random.default_rng(11)
+    A = rng.normal(size=(9, 4))
+    b = rng.normal(size=9)
+    v = rng.normal(size=4)
+    t_star = np.linalg.lstsq(A, b, rcond=None)[0]
+    for eps in (0.3, 1e-2):
+        # residual [A t - b; sqrt(2) (eps t - eps t* - v/2)] is linear in t
+        M = np.vstack([A, math.sqrt(2.0) * eps * np.eye(4)])
+        rhs = np.concatenate([b, math.sqrt(2.0) * (eps * t_star + 0.5 * v)])
+        ref = np.linalg.lstsq(M, rhs, rcond=None)[0]
+        At = torch.as_tensor(A)
+        delta = nls.dlm_direct_step(At, At @ torch.as_tensor(t_star) - torch.as_tensor(b),
+                                    torch.as_tensor(v), eps).numpy()
+        assert np.abs(t_star + delta - ref).max() < 1e-10
+
+
+def test_dlm_linear_limit_is_the_solution_map_vjp():
+    """Linear least squares with phi = b: g_DLM = (dS/db(t*) - dS/db(t_direct)) / eps must tend
+    to v^T d t*/d b, taken here by autograd through LAPACK's least-squares solve."""
+    rng = np.random.default_rng(12)
+    A = torch.as_tensor(rng.normal(size=(10, 5)))
+    b = torch.as_tensor(rng.normal(size=10), dtype=F64).requires_grad_(True)
+    v = torch.as_tensor(rng.normal(size=5))
+    t_star = torch.linalg.lstsq(A, b[:, None]).solution[:, 0]
+    (ref,) = torch.autograd.grad(t_star, b, v)
+    t_star = t_star.detach()
+
+    def dS_db(t):
+        bb = b.detach().clone().requires_grad_(True)
+        S = 0.5 * ((A @ t - bb) ** 2).sum()
+        return torch.autograd.grad(S, bb)[0]
+    eps = 1e-6
+    delta = nls.dlm_direct_step(A, A @ t_star - b.detach(), v, eps)
+    g = (dS_db(t_star) - dS_db(t_star + delta)) / eps
+    assert float((g - ref).norm() / ref.norm()) < 1e-8
+
+
+def test_dlm_pose_graph_tends_to_the_gauss_newton_implicit_gradient():
+    """At a converged pose graph the DLM gradient approaches the implicit gradient with the GN
+    Hessian (one GN step defines theta_direct), with an error linear in eps."""
+    b = synth.pgo_se2(batch=1, n_poses=10, n_lc=3, config_id=70)
+    g = pgo.graph_from_batch(b, 0)
+    g.logw = torch.as_tensor(np.random.default_rng(3).normal(0.0, 0.1, size=g.ei.shape[0]))
+    th = pgo.solve_to_convergence(g, pgo.solve(g, algo="gn", iters=10, lam0=0.0, tau=0.0)[0])
+    v = pgo.tangent_grad(2, lambda X: pgo.pose_error_loss(2, X, g.theta_gt), th)
+    rm, rl, _ = pgo.implicit_grads(g, th, v, "gn")
+    errs = []
+    for eps in (1e-4, 1e-5):
+        dm, dl, _ = pgo.dlm_grads(g, th, v, eps)
+        errs.append((float((dm - rm).norm() / rm.norm()), float((dl - rl).norm() / rl.norm())))
+    assert errs[1][0] < 1e-5 and errs[1][1] < 1e-3
+    for k in (0, 1):
+        assert 5.0 < errs[0][k] / errs[1][k] < 20.0  # first order in eps
+
+
 # ----------------------------------------------------------------------------- bundle adjustment
 def test_huber_definition():
     d = 2.0
