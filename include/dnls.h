@@ -59,7 +59,9 @@ enum {
 enum { DNLS_SE2 = 2, DNLS_SE3 = 3 };
 enum { DNLS_GN = 0, DNLS_LM = 1 };
 enum { DNLS_FP64 = 0, DNLS_MIXED_FP32 = 1 };
-enum { DNLS_IMPLICIT_EXACT = 0, DNLS_IMPLICIT_GN = 1 };
+/* backward modes: implicit differentiation (Eq. 3 / Prop. 1) with the true Hessian or the
+ * Gauss-Newton matrix, or direct loss minimization (Sec. 4.3, App. G; pose graphs only) */
+enum { DNLS_IMPLICIT_EXACT = 0, DNLS_IMPLICIT_GN = 1, DNLS_BACKWARD_DLM = 2 };
 enum { DNLS_ORDER_MIN_DEGREE = 0, DNLS_ORDER_NATURAL = 1 };
 
 /* Solver options (paper Sec. 3: optimizer choice, max_iterations, backward_mode).  The LM
@@ -72,14 +74,16 @@ typedef struct {
   int32_t iters;           /* number of iterations K (>= 0) */
   int32_t precision;       /* DNLS_FP64, or DNLS_MIXED_FP32 (residuals, Jacobians and H in FP32;
                               relative poses, g, the factorization and the acceptance in FP64) */
-  int32_t backward_mode;   /* DNLS_IMPLICIT_EXACT (true Hessian of S) or DNLS_IMPLICIT_GN */
+  int32_t backward_mode;   /* DNLS_IMPLICIT_EXACT (true Hessian of S), DNLS_IMPLICIT_GN or
+                              DNLS_BACKWARD_DLM */
   int32_t refine_max;      /* max refinement steps of the adjoint solve (>= 1) */
-  int32_t threads;         /* threads per CTA: 0 = library choice, else 128, 256 or 512 */
+  int32_t threads;         /* threads per CTA: 0 = library choice, else 128 or 256 */
   int32_t ctas_per_sm;     /* resident CTAs per SM of the persistent launch: 0 = library choice */
   int32_t smem_factor;     /* 1: keep a problem's Cholesky factor in shared memory when it fits */
   double lambda0;          /* initial LM damping */
   double tau;              /* freeze threshold on the relative decrease of S */
   double refine_tol;       /* adjoint solve stops once ||v - H x|| <= refine_tol * ||v|| */
+  double dlm_eps;          /* DNLS_BACKWARD_DLM: the finite-difference scale eps (> 0) */
 } dnls_solver_opts;
 
 /* Per-problem report (device array of `batch` entries, written by forward/backward). */
@@ -147,6 +151,16 @@ dnls_status dnls_graph_forward(const dnls_graph* g, const dnls_solver_opts* opts
  * v: device [P, dof] tangent gradient dL/dxi of the outer loss at theta*.
  * Either output may be NULL.  info (device [B], may be NULL) receives refine_resid,
  * refine_steps and DNLS_PROBLEM_NOT_CONVERGED where the tolerance was not reached. */
+/* With backward_mode = DNLS_BACKWARD_DLM the same call computes the direct-loss-minimization
+ * gradient instead (Sec. 4.3 "Direct loss minimization", App. G): one Gauss-Newton step from
+ * theta* on S(theta* (+) xi) + ||eps xi - v/2||^2 (the added term taken in the tangent chart at
+ * theta*), i.e. theta_direct = theta* (+) delta with (J^T J + 2 eps^2 I) delta = eps v - J^T r,
+ * all at theta* in FP64, then
+ *   grad_meas[e] = (dS/d eps_e (theta*) - dS/d eps_e (theta_direct)) / eps
+ *   grad_logw[e] = (dS/d l_e (theta*)   - dS/d l_e (theta_direct))   / eps
+ * with eps = opts->dlm_eps.  It needs no cached factor (the workspace's factor is overwritten
+ * and marked stale, so a later implicit backward refactors); refine_* are unused and info gets
+ * refine_steps = 1.  A non-SPD shifted matrix gives zero gradients and DNLS_PROBLEM_NOT_SPD. */
 dnls_status dnls_graph_backward(const dnls_graph* g, const dnls_solver_opts* opts,
                                 const dnls_graph_inputs* in, const double* theta_star,
                                 const double* v, double* grad_meas, double* grad_logw,

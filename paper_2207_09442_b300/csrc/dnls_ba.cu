@@ -285,31 +285,58 @@ __device__ void prior_lin64(const BAArgs& a, int64_t q, const double* T, double*
   prior_lin<3, double>(E, a.prior_w + q * 6, r, J);
 }
 
+// sum of N values over the 32 lanes of a warp (xor butterfly: every lane ends with the total,
+// in the same fixed order on every run)
+template <int N>
+__device__ __forceinline__ void warp_sum(double* v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+    for (int i = 0; i < N; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], off);
+}
+
+// one warp per camera: lane l takes observations l, l+32, ... of the camera
+__device__ __forceinline__ int64_t warp_item() { return gtid() >> 5; }
+
 // per camera: undamped H_cc (+ priors), g_c and b_c = -g_c + sum_o H_cp(o) u_p(o)
 __global__ void k_ba_cameras(BAArgs a) {
-  const int64_t c = gtid();
+  const int64_t c = warp_item();
+  const int lane = threadIdx.x & 31;
   if (c >= a.d.C) return;
   const int b = a.d.cam_prob[c];
   if (!a.st[b].active) return;
-  double H[36], g[6], bc[6];
+  double v[33];  // upper triangle of H (21), g (6), sum H_cp u (6)
 #pragma unroll
-  for (int k = 0; k < 36; ++k) H[k] = 0.0;
-#pragma unroll
-  for (int k = 0; k < 6; ++k) g[k] = bc[k] = 0.0;
-  for (int k = a.d.cam_ptr[c]; k < a.d.cam_ptr[c + 1]; ++k) {
+  for (int k = 0; k < 33; ++k) v[k] = 0.0;
+  for (int k = a.d.cam_ptr[c] + lane; k < a.d.cam_ptr[c + 1]; k += 32) {
     const int64_t o = a.d.cam_obs[k];
     double r[2], Jc[12], Jp[6];
     load_obsJ(a, o, r, Jc, Jp);
+    int t = 0;
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
-      g[i] += Jc[i] * r[0] + Jc[6 + i] * r[1];
+      v[21 + i] += Jc[i] * r[0] + Jc[6 + i] * r[1];
 #pragma unroll
-      for (int j = 0; j < 6; ++j) H[6 * i + j] += Jc[i] * Jc[j] + Jc[6 + i] * Jc[6 + j];
+      for (int j = i; j < 6; ++j) v[t++] += Jc[i] * Jc[j] + Jc[6 + i] * Jc[6 + j];
     }
     const double* u = a.up + (int64_t)a.d.obs_pt[o] * 3;
     const double* Hc = a.Hcp + o * 18;
 #pragma unroll
-    for (int i = 0; i < 6; ++i) bc[i] += Hc[3 * i] * u[0] + Hc[3 * i + 1] * u[1] + Hc[3 * i + 2] * u[2];
+    for (int i = 0; i < 6; ++i) v[27 + i] += Hc[3 * i] * u[0] + Hc[3 * i + 1] * u[1] + Hc[3 * i + 2] * u[2];
+  }
+  warp_sum<33>(v);
+  if (lane != 0) return;
+  double H[36], g[6];
+  int t = 0;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    g[i] = v[21 + i];
+#pragma unroll
+    for (int j = i; j < 6; ++j) {
+      H[6 * i + j] = v[t];
+      H[6 * j + i] = v[t];
+      ++t;
+    }
   }
   for (int k = a.d.cam_prior_ptr[c]; k < a.d.cam_prior_ptr[c + 1]; ++k) {
     double r[6], J[36];
@@ -334,7 +361,7 @@ __global__ void k_ba_cameras(BAArgs a) {
 #pragma unroll
   for (int k = 0; k < 6; ++k) {
     a.gc[c * 6 + k] = g[k];
-    a.bc[c * 6 + k] = bc[k] - g[k];
+    a.bc[c * 6 + k] = v[27 + k] - g[k];
   }
 }
 
@@ -615,22 +642,23 @@ __global__ void __launch_bounds__(256) k_bab_start(BAArgs a, const int64_t* pt_o
   }
 }
 
-// preconditioner, camera side: rc' = rc - sum_o Y_o rp(o)  (into bc)
+// preconditioner, camera side: rc' = rc - sum_o Y_o rp(o)  (into bc); one warp per camera
 __global__ void k_bap_cams(BAArgs a) {
-  const int64_t c = gtid();
+  const int64_t c = warp_item();
+  const int lane = threadIdx.x & 31;
   if (c >= a.d.C || !a.st[a.d.cam_prob[c]].active) return;
-  double acc[6];
-#pragma unroll
-  for (int i = 0; i < 6; ++i) acc[i] = a.rc[c * 6 + i];
-  for (int k = a.d.cam_ptr[c]; k < a.d.cam_ptr[c + 1]; ++k) {
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  for (int k = a.d.cam_ptr[c] + lane; k < a.d.cam_ptr[c + 1]; k += 32) {
     const int64_t o = a.d.cam_obs[k];
     const double* Yo = a.Y + o * 18;
     const double* r = a.rp + (int64_t)a.d.obs_pt[o] * 3;
 #pragma unroll
-    for (int i = 0; i < 6; ++i) acc[i] -= Yo[3 * i] * r[0] + Yo[3 * i + 1] * r[1] + Yo[3 * i + 2] * r[2];
+    for (int i = 0; i < 6; ++i) acc[i] += Yo[3 * i] * r[0] + Yo[3 * i + 1] * r[1] + Yo[3 * i + 2] * r[2];
   }
+  warp_sum<6>(acc);
+  if (lane != 0) return;
 #pragma unroll
-  for (int i = 0; i < 6; ++i) a.bc[c * 6 + i] = acc[i];
+  for (int i = 0; i < 6; ++i) a.bc[c * 6 + i] = a.rc[c * 6 + i] - acc[i];
 }
 
 // preconditioner, point side: z_p = Hppi (rp - sum_o H_cp(o)^T z_c(o)); z_c is in dc.
@@ -692,19 +720,28 @@ __global__ void k_bahvp_obs(BAArgs a, int vjp) {
   }
 }
 
-// camera side of the exact product (+ priors, + chart term) and r_c = v_c - (H x)_c
+// camera side of the exact product (+ priors, + chart term); one warp per camera
 __global__ void k_bahvp_cams(BAArgs a) {
-  const int64_t c = gtid();
+  const int64_t c = warp_item();
+  const int lane = threadIdx.x & 31;
   if (c >= a.d.C || !a.st[a.d.cam_prob[c]].active) return;
   typedef Dual<double> Dd;
-  double h[6] = {0, 0, 0, 0, 0, 0}, gs[6] = {0, 0, 0, 0, 0, 0};
-  for (int k = a.d.cam_ptr[c]; k < a.d.cam_ptr[c + 1]; ++k) {
+  double sums[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};  // local gradients, their derivatives
+  for (int k = a.d.cam_ptr[c] + lane; k < a.d.cam_ptr[c + 1]; k += 32) {
     const double* e = a.eb + (int64_t)a.d.cam_obs[k] * 18;
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
-      gs[i] += e[i];
-      h[i] += e[9 + i];
+      sums[i] += e[i];
+      sums[6 + i] += e[9 + i];
     }
+  }
+  warp_sum<12>(sums);
+  if (lane != 0) return;
+  double gs[6], h[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    gs[i] = sums[i];
+    h[i] = sums[6 + i];
   }
   const double* x = a.xc + c * 6;
   for (int k = a.d.cam_prior_ptr[c]; k < a.d.cam_prior_ptr[c + 1]; ++k) {
@@ -1092,7 +1129,7 @@ void ba_eliminate_and_factor(const dnls_ba* h, BAArgs& a, cudaStream_t st, doubl
   else
     k_ba_lin<double><<<nblk(H.O, 256), 256, 0, st>>>(a);
   k_ba_points<<<nblk(H.P, 128), 128, 0, st>>>(a, lam_override);
-  k_ba_cameras<<<nblk(H.C, 64), 64, 0, st>>>(a);
+  k_ba_cameras<<<nblk((int64_t)H.C * 32, 256), 256, 0, st>>>(a);  // one warp per camera
   k_ba_schur<<<nblk(H.red.meta.empty() ? 1 : (int64_t)H.tgt_cam.size() * 6, 128), 128, 0, st>>>(a, lam_override);
   k_ba_reduced<<<H.B, 256, 0, st>>>(a, 0, a.bc, a.dc, 0);
 }
@@ -1230,7 +1267,7 @@ dnls_status dnls_ba_backward(const dnls_ba* h, const dnls_solver_opts* opts, con
   k_bab_start<<<H.B, 256, 0, st>>>(a, h->impl.d_pt_off);
   // z = M^-1 r (block elimination with the cached Schur factorization): camera side into dc
   auto precondition = [&]() {
-    k_bap_cams<<<nblk(H.C, 64), 64, 0, st>>>(a);
+    k_bap_cams<<<nblk((int64_t)H.C * 32, 256), 256, 0, st>>>(a);
     k_ba_reduced<<<H.B, 256, 0, st>>>(a, 1, a.bc, a.dc, 0);
     k_bap_pts<<<nblk(H.P, 128), 128, 0, st>>>(a);
   };
@@ -1238,7 +1275,7 @@ dnls_status dnls_ba_backward(const dnls_ba* h, const dnls_solver_opts* opts, con
   k_pcg<<<H.B, 256, 0, st>>>(a, h->impl.d_pt_off, 0, 0);
   for (int it = 0; it < opts->refine_max; ++it) {
     k_bahvp_obs<<<nblk(H.O, 128), 128, 0, st>>>(a, 0);   // h = H p (true Hessian)
-    k_bahvp_cams<<<nblk(H.C, 64), 64, 0, st>>>(a);
+    k_bahvp_cams<<<nblk((int64_t)H.C * 32, 256), 256, 0, st>>>(a);
     k_bahvp_pts<<<nblk(H.P, 128), 128, 0, st>>>(a);
     k_pcg<<<H.B, 256, 0, st>>>(a, h->impl.d_pt_off, 1, it);
     precondition();

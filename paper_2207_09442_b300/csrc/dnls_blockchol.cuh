@@ -33,12 +33,13 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return r;
 }
 
-// L <- H + lam * diag(max(diag H, floor)), then left-looking block Cholesky level by level.
+// L <- H + lam * diag(max(diag H, floor)) + shift * I, then left-looking block Cholesky level
+// by level.
 // Returns false (uniformly across the CTA) if a pivot is not positive or not finite.  A failing
 // thread writes the call's generation number `gen` into *sflag; the flag is never reset, so a
 // slow thread can never see a later call's state.
 template <int D, class F>
-__device__ bool block_factor(F& p, double lam, int* sflag, int gen) {
+__device__ bool block_factor(F& p, double lam, int* sflag, int gen, double shift = 0.0) {
   constexpr int BS = D * D;
   double* L = p.L;
   const int nb = p.N + p.nnzL;
@@ -47,7 +48,7 @@ __device__ bool block_factor(F& p, double lam, int* sflag, int gen) {
     double v;
     if (t < p.N) {
       v = p.H[(int64_t)t * BS + el];
-      if (el / D == el % D) v += lam * fmax(v, kDiagFloor);
+      if (el / D == el % D) v += lam * fmax(v, kDiagFloor) + shift;
     } else {
       const int src = p.lsrc[t - p.N];
       v = src >= 0 ? p.H[(int64_t)(p.N + src) * BS + el] : 0.0;

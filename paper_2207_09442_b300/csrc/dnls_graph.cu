@@ -55,7 +55,7 @@ struct KArgs {
   int* counter;
   dnls_info* info;
   int algo, iters, mode, refine_max;
-  double lam0, tau, refine_tol;
+  double lam0, tau, refine_tol, dlm_eps;
   int smem_bytes;       // dynamic shared memory per CTA for staging (0 = none)
 };
 
@@ -319,8 +319,9 @@ __device__ void assemble(Prob<KIND>& p) {
 
 // ----------------------------------------------------------------------------- factor / solve
 template <int KIND>
-__device__ __forceinline__ bool factor(Prob<KIND>& p, double lam, int* sflag, int gen) {
-  return block_factor<Group<KIND>::DOF>(p, lam, sflag, gen);
+__device__ __forceinline__ bool factor(Prob<KIND>& p, double lam, int* sflag, int gen,
+                                       double shift = 0.0) {
+  return block_factor<Group<KIND>::DOF>(p, lam, sflag, gen, shift);
 }
 template <int KIND>
 __device__ __forceinline__ void chol_solve(Prob<KIND>& p, double* x) {
@@ -577,6 +578,81 @@ __device__ void hvp_gn(Prob<KIND>& p, const double* x, double* hx) {
   __syncthreads();
 }
 
+// Direct loss minimization (Sec. 4.3, App. G) for one problem: one GN step from theta* on
+// S(theta* (+) xi) + ||eps xi - v/2||^2, i.e. (J^T J + 2 eps^2 I) delta = eps v - J^T r (FP64),
+// theta_direct = theta* (+) delta, then per cost (dS_e/dphi(theta*) - dS_e/dphi(theta_direct))/eps
+// for phi = (measurement tangent, log-weight):  dS_e/d eps = -J_l^-1(c)^T w^2 c,
+// dS_e/d l = ||r_e||^2.
+template <int KIND>
+__device__ void dlm_problem(const KArgs& a, int b, char* smem, double* red, int* sflag) {
+  typedef Group<KIND> G;
+  constexpr int D = G::DOF, PW = G::PW;
+  Prob<KIND> p;
+  p.init(a, b, smem, a.smem_bytes);
+  p.stage_in(false);
+  p.prepare_weights();
+  const int n = p.N * D;
+  const double eps = a.dlm_eps;
+  lin_costs<KIND, double>(p, p.theta);
+  __syncthreads();
+  assemble<KIND, double>(p);
+  __syncthreads();
+  const bool ok = factor<KIND>(p, 0.0, sflag, 0, 2.0 * eps * eps);
+  if (ok) {
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+      const int pos = k / D, c = k % D;
+      p.dx[k] = eps * a.v[(p.m->pose_off + p.perm[pos]) * D + c] - p.g[k];
+    }
+    __syncthreads();
+    chol_solve<KIND>(p, p.dx);
+    retract<KIND>(p, p.theta, p.dx, p.thc);
+    __syncthreads();
+  }
+  const double inv_eps = 1.0 / eps;
+  for (int e = threadIdx.x; e < p.E; e += blockDim.x) {
+    const int64_t ge = p.m->edge_off + e;
+    if (!ok) {
+      if (a.grad_logw) a.grad_logw[ge] = 0.0;
+      if (a.grad_meas)
+        for (int k = 0; k < D; ++k) a.grad_meas[ge * D + k] = 0.0;
+      continue;
+    }
+    const int i = p.ei[e], j = p.ej[e];
+    double w[D], mg[2][D], rr[2] = {0.0, 0.0};
+    p.weight(e, w);
+    const double* Z = p.meas + (int64_t)e * PW;
+    for (int side = 0; side < 2; ++side) {  // 0: theta*, 1: theta_direct
+      const double* poses = side ? p.thc : p.theta;
+      const double* Ti = poses + (int64_t)i * PW;
+      double Em[PW], c[D];
+      if (j >= 0) {
+        double A[PW];
+        G::invmul(Ti, poses + (int64_t)j * PW, A);
+        G::invmul(Z, A, Em);
+      } else {
+        G::invmul(Z, Ti, Em);
+      }
+      G::log(Em, c);
+#pragma unroll
+      for (int k = 0; k < D; ++k) rr[side] += (w[k] * c[k]) * (w[k] * c[k]);
+      meas_grad_neg<KIND, double>(Em, w, mg[side]);  // = -dS_e/d eps
+    }
+    if (a.grad_logw) a.grad_logw[ge] = (rr[0] - rr[1]) * inv_eps;
+    if (a.grad_meas)
+#pragma unroll
+      for (int k = 0; k < D; ++k) a.grad_meas[ge * D + k] = (mg[1][k] - mg[0][k]) * inv_eps;
+  }
+  if (threadIdx.x == 0) {
+    p.st->factor_ok = 0;  // L now holds the shifted GN factor, not the forward's
+    if (a.info) {
+      a.info[b].refine_resid = 0.0;
+      a.info[b].refine_steps = 1;
+      if (!ok) a.info[b].status = DNLS_PROBLEM_NOT_SPD;
+    }
+  }
+  __syncthreads();
+}
+
 template <int KIND>
 __device__ void backward_problem(const KArgs& a, int b, char* smem, double* red, int* sflag) {
   typedef Group<KIND> G;
@@ -704,7 +780,10 @@ __global__ void __launch_bounds__(256) k_backward(KArgs a) {
     if (b < 0) break;
     if (threadIdx.x == 0) sflag = -1;
     __syncthreads();
-    backward_problem<KIND>(a, b, a.smem_bytes ? dyn_smem : nullptr, red, &sflag);
+    if (a.mode == DNLS_BACKWARD_DLM)
+      dlm_problem<KIND>(a, b, a.smem_bytes ? dyn_smem : nullptr, red, &sflag);
+    else
+      backward_problem<KIND>(a, b, a.smem_bytes ? dyn_smem : nullptr, red, &sflag);
   }
 }
 
@@ -795,7 +874,10 @@ dnls_status check_opts(const dnls_solver_opts* o) {
   if (o->algo != DNLS_GN && o->algo != DNLS_LM) return DNLS_ERR_ARG;
   if (o->iters < 0 || o->iters > 100000) return DNLS_ERR_ARG;
   if (o->precision != DNLS_FP64 && o->precision != DNLS_MIXED_FP32) return DNLS_ERR_ARG;
-  if (o->backward_mode != DNLS_IMPLICIT_EXACT && o->backward_mode != DNLS_IMPLICIT_GN)
+  if (o->backward_mode != DNLS_IMPLICIT_EXACT && o->backward_mode != DNLS_IMPLICIT_GN &&
+      o->backward_mode != DNLS_BACKWARD_DLM)
+    return DNLS_ERR_ARG;
+  if (o->backward_mode == DNLS_BACKWARD_DLM && !(o->dlm_eps > 0.0 && std::isfinite(o->dlm_eps)))
     return DNLS_ERR_ARG;
   if (o->threads != 0 && o->threads != 128 && o->threads != 256) return DNLS_ERR_ARG;
   if (o->ctas_per_sm < 0 || o->ctas_per_sm > 16) return DNLS_ERR_ARG;
@@ -940,6 +1022,7 @@ dnls_status dnls_graph_backward(const dnls_graph* g, const dnls_solver_opts* opt
   a.mode = opts->backward_mode;
   a.refine_max = opts->refine_max;
   a.refine_tol = opts->refine_tol;
+  a.dlm_eps = opts->dlm_eps;
   a.counter = (int*)workspace + 1;
   cudaStream_t st = (cudaStream_t)stream;
   if (g->impl.h.kind == DNLS_SE3) return launch_persistent(k_backward<3>, g, opts, a, st, false);

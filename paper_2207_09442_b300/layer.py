@@ -24,7 +24,7 @@ class Options:
     algo: str = "lm"                 # "gn" | "lm"
     iters: int = 20
     precision: str = "mixed_fp32"    # "fp64" | "mixed_fp32"
-    backward_mode: str = "implicit"  # "implicit" (true Hessian) | "implicit_gn"
+    backward_mode: str = "implicit"  # "implicit" (true Hessian) | "implicit_gn" | "dlm"
     refine_max: int = 30
     lambda0: float = 1e-3
     tau: Optional[float] = None      # default: 1e-14 (fp64) / 1e-10 (mixed)
@@ -32,6 +32,7 @@ class Options:
     threads: int = 0
     ctas_per_sm: int = 0
     smem_factor: int = 1
+    dlm_eps: float = 1e-2            # backward_mode "dlm": finite-difference scale eps
 
     def c(self) -> _d.SolverOpts:
         fp64 = self.precision == "fp64"
@@ -39,7 +40,10 @@ class Options:
         o.algo = _d.GN if self.algo == "gn" else _d.LM
         o.iters = int(self.iters)
         o.precision = _d.FP64 if fp64 else _d.MIXED_FP32
-        o.backward_mode = _d.IMPLICIT_GN if self.backward_mode == "implicit_gn" else _d.IMPLICIT_EXACT
+        modes = {"implicit": _d.IMPLICIT_EXACT, "implicit_gn": _d.IMPLICIT_GN, "dlm": _d.BACKWARD_DLM}
+        if self.backward_mode not in modes:
+            raise ValueError(f"unknown backward_mode {self.backward_mode!r}")
+        o.backward_mode = modes[self.backward_mode]
         o.refine_max = int(self.refine_max)
         o.threads = int(self.threads)
         o.ctas_per_sm = int(self.ctas_per_sm)
@@ -47,6 +51,7 @@ class Options:
         o.lambda0 = float(self.lambda0) if self.algo == "lm" else 0.0
         o.tau = float(self.tau if self.tau is not None else (1e-14 if fp64 else 1e-10))
         o.refine_tol = float(self.refine_tol if self.refine_tol is not None else (1e-11 if fp64 else 1e-7))
+        o.dlm_eps = float(self.dlm_eps)
         return o
 
 
