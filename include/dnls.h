@@ -67,7 +67,9 @@ enum { DNLS_ORDER_MIN_DEGREE = 0, DNLS_ORDER_NATURAL = 1 };
 /* Solver options (paper Sec. 3: optimizer choice, max_iterations, backward_mode).  The LM
  * damping rule is not given in the paper; this library uses: damping matrix
  * D = diag(max(diag H, 1e-9)), lambda *= 10 on reject, /= 10 on accept, lambda clamped to
- * [1e-12, 1e12], accept iff S_new < S_old; a problem stops once |S_old - S_new| <= tau*S_old.
+ * [1e-12, 1e12], accept iff S_new <= S_old (a tie is accepted: near an ill-conditioned optimum
+ * S is flat to FP64 resolution along weak directions, where the GN step must still move); with
+ * tau > 0 a problem stops once |S_old - S_new| <= tau*S_old (tau = 0: every iteration runs).
  * A rejected step counts as an iteration. */
 typedef struct {
   int32_t algo;            /* DNLS_GN or DNLS_LM */

@@ -6,7 +6,10 @@ One iteration: H = J^T J, g = J^T r; LM adds lambda * D with D = diag(max(diag H
 delta = -(H + lambda D)^-1 g (Cholesky, dense via torch.linalg, or sparse LU via SciPy);
 theta_c = theta (+) delta; accept iff S(theta_c) < S(theta) (GN always accepts); on accept
 lambda <- max(lambda/10, 1e-12) and the problem is re-linearised at theta_c, on reject
-lambda <- min(10 lambda, 1e12).  A problem stops ("freezes") once |S_old - S_c| <= tau S_old.
+lambda <- min(10 lambda, 1e12).  A tie (S(theta_c) == S(theta)) is accepted: near the optimum
+of an ill-conditioned problem S is flat to FP64 resolution along weak directions, and the GN step
+(computed from the accurate gradient) must still be allowed to move there.  With tau > 0 a
+problem stops ("freezes") once |S_old - S_c| <= tau S_old; tau = 0 runs every iteration.
 The paper names LM with adaptive damping without its rule; these constants are this project's
 reading and are used identically by the CUDA path.
 """
@@ -92,8 +95,8 @@ def lm_loop(linearize: Callable, objective: Callable, retract: Callable, theta0,
             hist.append(float(S))
             continue
         S_old = float(S)
-        accept = (algo == "gn") or (float(S_c) < S_old)
-        frozen = abs(S_old - float(S_c)) <= tau * S_old
+        accept = (algo == "gn") or (float(S_c) <= S_old)
+        frozen = tau > 0.0 and abs(S_old - float(S_c)) <= tau * S_old
         if accept:
             theta = theta_c
             S = S_c

@@ -13,8 +13,8 @@ What it follows:
     (sum J^T J) delta = -sum J^T r, retract.  LM damps the system and adapts the damping
     (Sec. 3, "Levenberg-Marquardt (with adaptive damping)").  The exact damping rule is not
     given; the reading used: D = diag(max(diag H, 1e-9)), x10 on reject, /10 on accept, lambda
-    clamped to [1e-12, 1e12], accept iff S_new < S_old, freeze a problem once
-    |S_old - S_new| <= tau * S_old.  A rejected step still counts as an iteration.
+    clamped to [1e-12, 1e12], accept iff S_new <= S_old (ties accepted), with tau > 0 freeze a
+    problem once |S_old - S_new| <= tau * S_old.  A rejected step still counts as an iteration.
   * Eq. 3 and Prop. 1: D_phi theta* = -[D_theta g]^-1 D_phi g with g = grad_theta S.  In the chart
     theta* (+) xi the "exact" mode uses the true Hessian d^2 S / d xi^2 at xi = 0; the "gn" mode
     uses sum J^T J (what a Gauss-Newton implementation differentiates).

@@ -536,8 +536,8 @@ __global__ void __launch_bounds__(256) k_ba_accept(BAArgs a, int mode, const int
     s.lam = fmin(s.lam * 10.0, kLamMaxBA);
     s.need_lin = 0;
   } else {
-    const bool accept = !lm || S < s.S;
-    const bool frozen = fabs(s.S - S) <= a.tau * s.S;
+    const bool accept = !lm || S <= s.S;  // ties accepted, as for pose graphs
+    const bool frozen = a.tau > 0.0 && fabs(s.S - S) <= a.tau * s.S;
     if (accept) {
       s.accepted_last = 1;
       s.accepted += 1;

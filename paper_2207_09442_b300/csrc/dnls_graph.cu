@@ -391,8 +391,10 @@ __device__ void forward_problem(const KArgs& a, int b, char* smem, double* red, 
       lam = fmin(lam * 10.0, kLamMax);
       continue;
     }
-    const bool accept = !lm || Sc < S;
-    const bool frozen = fabs(S - Sc) <= a.tau * S;
+    // ties accepted (S flat to FP64 resolution along weak directions near the optimum);
+    // freezing only with tau > 0
+    const bool accept = !lm || Sc <= S;
+    const bool frozen = a.tau > 0.0 && fabs(S - Sc) <= a.tau * S;
     if (accept) {
       for (int k = threadIdx.x; k < p.N * PW; k += blockDim.x) p.theta[k] = p.thc[k];
       __syncthreads();
