@@ -33,6 +33,118 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return r;
 }
 
+// Cholesky and factor inverse of diagonal block k by one thread; a failed pivot writes `gen`.
+template <int D, class F>
+__device__ __forceinline__ void diag_thread(F& p, double* L, int k, int* sflag, int gen) {
+  constexpr int BS = D * D;
+  double A[BS];
+  double* Lk = L + (int64_t)k * BS;
+#pragma unroll
+  for (int e = 0; e < BS; ++e) A[e] = Lk[e];
+  bool ok = true;
+  double inv[D];  // reciprocals of the pivots, reused by the inverse below
+#pragma unroll
+  for (int jj = 0; jj < D; ++jj) {
+    double d = A[jj * D + jj];
+#pragma unroll
+    for (int mm = 0; mm < jj; ++mm) d -= A[jj * D + mm] * A[jj * D + mm];
+    ok = ok && (d > 0.0) && isfinite(d);
+    const double dd = fmax(d, 1e-300);
+    const double il = rsqrt(dd);
+    inv[jj] = il;
+    A[jj * D + jj] = dd * il;
+#pragma unroll
+    for (int ii = jj + 1; ii < D; ++ii) {
+      double s = A[ii * D + jj];
+#pragma unroll
+      for (int mm = 0; mm < jj; ++mm) s -= A[ii * D + mm] * A[jj * D + mm];
+      A[ii * D + jj] = s * il;
+    }
+  }
+  // inverse of the lower-triangular factor
+  double I[BS];
+#pragma unroll
+  for (int e = 0; e < BS; ++e) I[e] = 0.0;
+#pragma unroll
+  for (int jj = 0; jj < D; ++jj) {
+    I[jj * D + jj] = inv[jj];
+#pragma unroll
+    for (int ii = jj + 1; ii < D; ++ii) {
+      double s = 0.0;
+#pragma unroll
+      for (int mm = jj; mm < ii; ++mm) s += A[ii * D + mm] * I[mm * D + jj];
+      I[ii * D + jj] = -s * inv[ii];
+    }
+  }
+#pragma unroll
+  for (int ii = 0; ii < D; ++ii)
+#pragma unroll
+    for (int jj = 0; jj < D; ++jj) {
+      Lk[ii * D + jj] = jj <= ii ? A[ii * D + jj] : 0.0;
+      p.Linv[(int64_t)k * BS + ii * D + jj] = I[ii * D + jj];
+    }
+  if (!ok) *sflag = gen;
+}
+
+// The same for the diagonal blocks of level columns c0..c1-1 (c1 - c0 <= 32 / D) by the 32
+// lanes of one warp: lane r of group g holds row r of column lvlcols[c0 + g]; step j shares the
+// pivot row's entries by shuffles and updates the trailing rows (the same subtractions in the
+// same order as the one-thread version); then lane r computes column r of the factor's inverse.
+// All 32 lanes must call (lanes beyond the last group work on an identity block and store
+// nothing).
+template <int D, class F>
+__device__ __forceinline__ void diag_rows(F& p, double* L, int c0, int c1, int* sflag, int gen) {
+  constexpr int BS = D * D;
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int grp = lane / D, r = lane - grp * D, base = grp * D;
+  const bool act = grp < c1 - c0;
+  const int k = act ? p.lvlcols[c0 + grp] : 0;
+  double* Lk = L + (int64_t)k * BS;
+  double A[D], inv[D];
+#pragma unroll
+  for (int m = 0; m < D; ++m) A[m] = act ? Lk[r * D + m] : (m == r ? 1.0 : 0.0);
+  bool ok = true;
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    const double d = __shfl_sync(full, A[j], base + j);  // pivot A(j, j), already updated
+    ok = ok && (d > 0.0) && isfinite(d);
+    const double dd = fmax(d, 1e-300);
+    const double il = rsqrt(dd);
+    inv[j] = il;
+    const double lrj = r == j ? dd * il : (r > j ? A[j] * il : 0.0);
+    A[j] = lrj;
+#pragma unroll
+    for (int m = j + 1; m < D; ++m) {
+      const double lmj = __shfl_sync(full, lrj, base + m);
+      if (m <= r) A[m] = fma(-lrj, lmj, A[m]);
+    }
+  }
+  // column r of L^-1: I(r, r) = 1 / L(r, r); I(i, r) = -(sum_{m=r}^{i-1} L(i, m) I(m, r)) / L(i, i)
+  double I[D];
+#pragma unroll
+  for (int i = 0; i < D; ++i) I[i] = 0.0;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    if (i == r) I[i] = inv[i];
+    double s = 0.0;
+#pragma unroll
+    for (int m = 0; m < i; ++m) {
+      const double lim = __shfl_sync(full, A[m], base + i);  // L(i, m) from lane i
+      if (m >= r) s += lim * I[m];
+    }
+    if (i > r) I[i] = -s * inv[i];
+  }
+  if (act) {
+#pragma unroll
+    for (int m = 0; m < D; ++m) {
+      Lk[r * D + m] = m <= r ? A[m] : 0.0;
+      p.Linv[(int64_t)k * BS + m * D + r] = I[m];
+    }
+    if (!ok) *sflag = gen;
+  }
+}
+
 // L <- H + lam * diag(max(diag H, floor)) + shift * I, then left-looking block Cholesky level
 // by level.
 // Returns false (uniformly across the CTA) if a pivot is not positive or not finite.  A failing
@@ -85,58 +197,17 @@ __device__ bool block_factor(F& p, double lam, int* sflag, int gen, double shift
       if (it < n1 && (it % LN) == 0 && s1 > s0) L[(int64_t)p.tgt[q] * BS + el] -= acc;
     }
     __syncthreads();
-    // (2) dense Cholesky of each diagonal block of the level (one thread per column) and the
-    //     inverse of its factor
+    // (2) dense Cholesky of each diagonal block of the level and the inverse of its factor.
+    //     A warp issues one FP64 instruction per several dozen cycles whatever its active-lane
+    //     count, so narrow levels (at most 32/D columns, the upper part of the elimination tree)
+    //     run with D lanes per column in warp 0 (row-parallel, right-looking, pivots shared by
+    //     shuffles), which cuts the instructions on that warp's critical path; wider levels
+    //     take one thread per column.
     const int c0 = p.lvlptr[lv], c1 = p.lvlptr[lv + 1];
-    for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
-      const int k = p.lvlcols[c];
-      double A[BS];
-      double* Lk = L + (int64_t)k * BS;
-#pragma unroll
-      for (int e = 0; e < BS; ++e) A[e] = Lk[e];
-      bool ok = true;
-      double inv[D];  // reciprocals of the pivots, reused by the inverse below
-#pragma unroll
-      for (int jj = 0; jj < D; ++jj) {
-        double d = A[jj * D + jj];
-#pragma unroll
-        for (int mm = 0; mm < jj; ++mm) d -= A[jj * D + mm] * A[jj * D + mm];
-        ok = ok && (d > 0.0) && isfinite(d);
-        const double dd = fmax(d, 1e-300);
-        const double il = rsqrt(dd);
-        inv[jj] = il;
-        A[jj * D + jj] = dd * il;
-#pragma unroll
-        for (int ii = jj + 1; ii < D; ++ii) {
-          double s = A[ii * D + jj];
-#pragma unroll
-          for (int mm = 0; mm < jj; ++mm) s -= A[ii * D + mm] * A[jj * D + mm];
-          A[ii * D + jj] = s * il;
-        }
-      }
-      // inverse of the lower-triangular factor
-      double I[BS];
-#pragma unroll
-      for (int e = 0; e < BS; ++e) I[e] = 0.0;
-#pragma unroll
-      for (int jj = 0; jj < D; ++jj) {
-        I[jj * D + jj] = inv[jj];
-#pragma unroll
-        for (int ii = jj + 1; ii < D; ++ii) {
-          double s = 0.0;
-#pragma unroll
-          for (int mm = jj; mm < ii; ++mm) s += A[ii * D + mm] * I[mm * D + jj];
-          I[ii * D + jj] = -s * inv[ii];
-        }
-      }
-#pragma unroll
-      for (int ii = 0; ii < D; ++ii)
-#pragma unroll
-        for (int jj = 0; jj < D; ++jj) {
-          Lk[ii * D + jj] = jj <= ii ? A[ii * D + jj] : 0.0;
-          p.Linv[(int64_t)k * BS + ii * D + jj] = I[ii * D + jj];
-        }
-      if (!ok) *sflag = gen;
+    if (c1 - c0 <= 32 / D) {
+      if (threadIdx.x < 32) diag_rows<D>(p, L, c0, c1, sflag, gen);
+    } else {
+      for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) diag_thread<D>(p, L, p.lvlcols[c], sflag, gen);
     }
     __syncthreads();
     if (*sflag == gen) return false;

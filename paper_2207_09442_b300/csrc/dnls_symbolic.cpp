@@ -275,12 +275,24 @@ int build_graph_host(int kind, int B, const int64_t* pose_offsets, const int64_t
     for (int l = 0; l < nlev; ++l) {
       tgtptr.push_back((int)tgt.size());
       panptr.push_back((int)pan.size() / 2);
+      // targets with at least one source pair, longest source list first, so that the
+      // threads of a warp run gather loops of similar length (the order of the targets does
+      // not change any sum: each target is still summed by one thread group in list order)
+      struct LT {
+        int count, target, k, t;
+      };
+      std::vector<LT> lt;
+      for (int k : bylev[l])
+        for (int t = 0; t <= (int)rows[k].size(); ++t)
+          if (!gl[k][t].empty())
+            lt.push_back({(int)gl[k][t].size(), t == 0 ? k : N + colptr[k] + t - 1, k, t});
+      std::stable_sort(lt.begin(), lt.end(), [](const LT& x, const LT& y) { return x.count > y.count; });
+      for (const LT& e : lt) {
+        tgt.push_back(e.target);
+        gptr.push_back((int)gsrc.size() / 2);
+        gsrc.insert(gsrc.end(), gl[e.k][e.t].begin(), gl[e.k][e.t].end());
+      }
       for (int k : bylev[l]) {
-        for (int t = 0; t <= (int)rows[k].size(); ++t) {
-          tgt.push_back(t == 0 ? k : N + colptr[k] + t - 1);
-          gptr.push_back((int)gsrc.size() / 2);
-          gsrc.insert(gsrc.end(), gl[k][t].begin(), gl[k][t].end());
-        }
         for (int a = 0; a < (int)rows[k].size(); ++a) {
           pan.push_back(N + colptr[k] + a);
           pan.push_back(k);
@@ -333,13 +345,36 @@ int build_graph_host(int kind, int B, const int64_t* pose_offsets, const int64_t
       blob.insert(blob.end(), lsrc.begin(), lsrc.end());
     }
     // lanes per output element in each level's sums.  Measured on the 128-pose SE(3) graphs:
-    // the factor gathers (36 outputs per block, short source lists) are fastest with one lane
-    // everywhere, the solve sweeps (6 outputs per block column) with four lanes everywhere;
-    // the per-level arrays keep the choice open for other structures.
+    // Lanes per output of each level's gather (factor) and sweeps (solves).  A warp issues
+    // one FP64 instruction per several dozen cycles, so on levels with few outputs (the top of
+    // the elimination tree, where source lists are longest) splitting each output's sum over
+    // more lanes shortens the serial chains; on wide levels extra lanes only add instructions.
+    // Rule: double the lanes (up to 8) while the level's outputs x lanes still fit in the
+    // CTA's threads and each lane keeps at least one term on average.
+    const int threads_hint = D == 6 ? 256 : 128;
+    auto lanes_for = [&](int64_t outputs, double avg_terms, int min_lanes) {
+      int ln = min_lanes;
+      while (ln < 8 && outputs * ln * 2 <= threads_hint && avg_terms >= 2.0 * ln) ln *= 2;
+      return ln;
+    };
     m.o_glanes = mark();
-    for (int l = 0; l < nlev; ++l) blob.push_back(1);
+    for (int l = 0; l < nlev; ++l) {
+      const int t0 = tgtptr[l], t1 = tgtptr[l + 1];
+      const int64_t pairs_l = gptr[t1] - gptr[t0];
+      const double avg = t1 > t0 ? (double)pairs_l / (t1 - t0) : 0.0;
+      blob.push_back(lanes_for((int64_t)(t1 - t0) * BS, avg, 1));
+    }
     m.o_slanes = mark();
-    for (int l = 0; l < nlev; ++l) blob.push_back(4);
+    for (int l = 0; l < nlev; ++l) {
+      int64_t fwd = 0, bwd = 0;
+      for (int k : bylev[l]) {
+        fwd += (int64_t)rowl[k].size();
+        bwd += (int64_t)rows[k].size();
+      }
+      const int nc = (int)bylev[l].size();
+      const double avg = nc ? (double)std::max(fwd, bwd) / nc : 0.0;
+      blob.push_back(lanes_for((int64_t)nc * D, avg, 1));
+    }
     blob.push_back(0);  // keep every section non-empty-addressable
     while (blob.size() % 4) blob.push_back(0);  // 16-byte multiple, for staging copies
     m.blob_len = (int32_t)blob.size();
