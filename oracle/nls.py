@@ -16,6 +16,7 @@ reading and are used identically by the CUDA path.
 from __future__ import annotations
 
 import dataclasses
+import math
 from typing import Callable
 
 import numpy as np
@@ -127,3 +128,78 @@ def dlm_direct_step(J, r, v, eps):
     L = torch.linalg.cholesky(A)
     return torch.cholesky_solve(rhs[:, None], L)[:, 0]
 
+
+
+# ----------------------------------------------------------------------------- Dogleg
+DELTA_MIN, DELTA_MAX = 1e-12, 1e12
+
+
+def dogleg_step(J, r, delta):
+    """Powell's dogleg step for the model m(p) = S + g^T p + 1/2 p^T B p, B = J^T J, g = J^T r,
+    inside the trust region ||p|| <= delta (the trust-region method the paper lists next to GN
+    and LM, Sec. 2 and Sec. 3; the step as in Nocedal & Wright, Numerical Optimization, Sec. 4.1):
+      p_B = -B^-1 g (Gauss-Newton), p_U = -(g^T g / g^T B g) g (Cauchy point);
+      ||p_B|| <= delta: p = p_B;  ||p_U|| >= delta (or g^T B g <= 0): p = -delta g / ||g||;
+      otherwise p = p_U + s (p_B - p_U) with s in [0, 1] solving ||p|| = delta.
+    If B is not positive definite the Gauss-Newton branch is skipped.  Returns (p, boundary,
+    predicted reduction m(0) - m(p)).  J dense torch."""
+    B = J.T @ J
+    g = J.T @ r
+    gg = float(g @ g)
+    gBg = float(g @ (B @ g))
+    L, info = torch.linalg.cholesky_ex(B)
+    pB = -torch.cholesky_solve(g[:, None], L)[:, 0] if int(info) == 0 else None
+    if pB is not None and float(pB.norm()) <= delta:
+        p, boundary = pB, False
+    elif gBg <= 0.0 or (gg / gBg) * math.sqrt(gg) >= delta or pB is None:
+        p, boundary = -(delta / math.sqrt(gg)) * g, True
+    else:
+        pU = -(gg / gBg) * g
+        d = pB - pU
+        a = float(d @ d)
+        b = 2.0 * float(pU @ d)
+        c = float(pU @ pU) - delta * delta
+        s = (-b + math.sqrt(b * b - 4.0 * a * c)) / (2.0 * a)
+        p, boundary = pU + s * d, True
+    pred = -(float(g @ p) + 0.5 * float((J @ p) @ (J @ p)))
+    return p, boundary, pred
+
+
+def dogleg_loop(linearize: Callable, objective: Callable, retract: Callable, theta0,
+                iters=20, delta0=1.0, tau=1e-14, record=False):
+    """``iters`` trust-region iterations with the dogleg step.  rho = (S - S_c) / pred; the
+    radius becomes delta / 4 if rho < 1/4, min(2 delta, 1e12) if rho > 3/4 and the step reached
+    the boundary, and is clamped to [1e-12, 1e12]; the step is accepted iff S_c <= S (ties
+    accepted, as for LM).  After a rejection only the radius changes (same linearization).
+    SolveInfo.lam reports the final radius."""
+    theta = theta0
+    r, J = linearize(theta)
+    S = objective(theta)
+    S0 = float(S)
+    delta = float(delta0)
+    status, accepted, done = STATUS_OK, 0, 0
+    hist = [float(S)]
+    for it in range(iters):
+        done = it + 1
+        p, boundary, pred = dogleg_step(J, r, delta)
+        theta_c = retract(theta, p)
+        S_c = objective(theta_c)
+        ok = bool(torch.isfinite(torch.as_tensor(S_c)))
+        S_old = float(S)
+        rho = (S_old - float(S_c)) / pred if (ok and pred > 0.0) else -1.0
+        if rho < 0.25:
+            delta = 0.25 * delta
+        elif rho > 0.75 and boundary:
+            delta = 2.0 * delta
+        delta = min(max(delta, DELTA_MIN), DELTA_MAX)
+        accept = ok and float(S_c) <= S_old
+        frozen = ok and tau > 0.0 and abs(S_old - float(S_c)) <= tau * S_old
+        if accept:
+            theta, S = theta_c, S_c
+            accepted += 1
+            if not frozen and it + 1 < iters:
+                r, J = linearize(theta)
+        hist.append(float(S))
+        if frozen:
+            break
+    return theta, SolveInfo(S0, float(S), done, accepted, delta, status, hist if record else [])

@@ -181,12 +181,18 @@ def _place(J, rows, cols, blocks):
 
 # ----------------------------------------------------------------------------- solver
 def solve(g: Graph, theta0=None, algo="lm", iters=20, lam0=1e-3, tau=1e-14,
-          eps=None, logw=None, record=False):
-    """K iterations of GN (algo='gn': no damping, always accept) or LM from theta0 (default
-    theta_init).  Returns (theta, nls.SolveInfo).  Differentiable w.r.t. ``eps`` / ``logw`` when
-    they require grad (the unrolled backward)."""
+          eps=None, logw=None, record=False, radius0=1.0):
+    """K iterations of GN (algo='gn': no damping, always accept), LM, or the dogleg trust-region
+    method (algo='dogleg', initial radius ``radius0``) from theta0 (default theta_init).
+    Returns (theta, nls.SolveInfo).  Differentiable w.r.t. ``eps`` / ``logw`` when they require
+    grad (the unrolled backward; GN/LM only)."""
     theta = g.theta_init if theta0 is None else theta0
     dof = g.dof
+    if algo == "dogleg":
+        return nls.dogleg_loop(lambda th: jacobian(g, th, eps=eps, logw=logw),
+                               lambda th: objective(g, th, eps=eps, logw=logw),
+                               lambda th, d: lie.pose_retract(g.kind, th, d.reshape(-1, dof)),
+                               theta, iters=iters, delta0=radius0, tau=tau, record=record)
     return nls.lm_loop(lambda th: jacobian(g, th, eps=eps, logw=logw),
                        lambda th: objective(g, th, eps=eps, logw=logw),
                        lambda th, d: lie.pose_retract(g.kind, th, d.reshape(-1, dof)),

@@ -202,13 +202,14 @@ def _np_se2(x, y, p):
     return np.array([[math.cos(p), -math.sin(p), x], [math.sin(p), math.cos(p), y], [0, 0, 1]])
 
 
-@pytest.mark.parametrize("seed", [0, 1, 2])
-def test_tiny_se2_graph_against_scipy_least_squares(seed):
+@pytest.mark.parametrize("seed,algo", [(0, "gn"), (1, "gn"), (2, "gn"), (0, "dogleg"), (1, "dogleg")])
+def test_tiny_se2_graph_against_scipy_least_squares(seed, algo):
     """Brute force: scipy's trust-region least squares on (x, y, psi) coordinates with an
-    independent SE(2) log (a linear solve with V) finds the same optimum as the oracle's GN."""
+    independent SE(2) log (a linear solve with V) finds the same optimum as the oracle's GN and
+    dogleg solvers."""
     b = synth.pgo_se2(batch=1, n_poses=5, n_lc=2, config_id=100 + seed)
     g = pgo.graph_from_batch(b, 0)
-    th, info = pgo.solve(g, algo="gn", iters=30, tau=0.0)
+    th, info = pgo.solve(g, algo=algo, iters=30 if algo == "gn" else 80, tau=0.0)
     Zm = [_np_se2(z[0], z[1], math.atan2(z[3], z[2])) for z in b.meas]
 
     def resid(q):
@@ -353,6 +354,55 @@ def test_implicit_exact_matches_fd_and_unrolled_noisy():
         assert abs(f - ref) < 1e-6 * scale
     gn_e, _, _ = pgo.implicit_grads(g, th, v, "gn")
     assert float((gn_e - ge).norm() / ge.norm()) > 1e-5
+
+
+# ----------------------------------------------------------------------------- dogleg
+def test_dogleg_large_radius_is_one_gauss_newton_step_on_linear_least_squares():
+    rng = np.random.default_rng(21)
+    A = torch.as_tensor(rng.normal(size=(12, 5)))
+    b = torch.as_tensor(rng.normal(size=12))
+    x0 = torch.as_tensor(rng.normal(size=5))
+    x, info = nls.dogleg_loop(lambda x: (A @ x - b, A), lambda x: 0.5 * float(((A @ x - b) ** 2).sum()),
+                              lambda x, d: x + d, x0, iters=1, delta0=1e6, tau=0.0)
+    ref = torch.linalg.lstsq(A, b[:, None]).solution[:, 0]
+    assert float((x - ref).abs().max()) < 1e-12
+
+
+@pytest.mark.parametrize("frac", [0.3, 0.8, 1.5, 3.0])
+def test_dogleg_step_is_the_path_point_at_the_radius(frac):
+    """For radii inside the Gauss-Newton step the step is the point of the dogleg path (0 -> p_U
+    -> p_B) at distance delta, located here by bisection on the path parameter (the path's norm
+    is monotone); outside it the step is p_B itself."""
+    rng = np.random.default_rng(22)
+    J = torch.as_tensor(rng.normal(size=(10, 4)) @ np.diag([1.0, 3.0, 0.3, 8.0]))
+    r = torch.as_tensor(rng.normal(size=10))
+    B, g = J.T @ J, J.T @ r
+    pB = -torch.linalg.solve(B, g)
+    pU = -(g @ g) / (g @ B @ g) * g
+    path = lambda t: t * pU if t <= 1.0 else pU + (t - 1.0) * (pB - pU)
+    delta = frac * float(pU.norm()) if frac < 1.0 else min(frac * float(pU.norm()), 2.0 * float(pB.norm()))
+    p, boundary, pred = nls.dogleg_step(J, r, delta)
+    if delta >= float(pB.norm()):
+        assert not boundary and float((p - pB).abs().max()) < 1e-12
+    else:
+        lo, hi = 0.0, 2.0
+        for _ in range(200):
+            mid = 0.5 * (lo + hi)
+            lo, hi = (mid, hi) if float(path(mid).norm()) < delta else (lo, mid)
+        assert boundary and float((p - path(lo)).abs().max()) < 1e-10 * float(pB.norm())
+    model = lambda q: float(g @ q + 0.5 * q @ B @ q)
+    assert abs(pred + model(p)) < 1e-12 * max(1.0, abs(pred))
+
+
+def test_dogleg_monotone_on_se3_graph():
+    b = synth.pgo_se3(batch=1, n_poses=20, n_lc=5, config_id=90)
+    g = pgo.graph_from_batch(b, 0)
+    th, info = pgo.solve(g, algo="dogleg", iters=25, tau=0.0, record=True)
+    h = info.S_history
+    assert all(h[k + 1] <= h[k] for k in range(len(h) - 1))
+    th_lm, info_lm = pgo.solve(g, algo="lm", iters=25, tau=0.0)
+    assert abs(info.S_final - info_lm.S_final) < 1e-12 * info_lm.S_final
+    assert float((th - th_lm).abs().max()) < 1e-7
 
 
 # ----------------------------------------------------------------------------- direct loss minimization
