@@ -73,6 +73,10 @@ def _args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(PER_GPU),
                     help="which synthetic workload (default: the 256 x 128-pose SE(3) batch)")
+    ap.add_argument("--algo", default="", choices=["", "gn", "lm", "dogleg"],
+                    help="pose graphs: override the workload's optimizer")
+    ap.add_argument("--backward", default="implicit", choices=["implicit", "implicit_gn", "dlm"],
+                    help="pose graphs: backward mode (implicit true Hessian, implicit GN, or DLM)")
     ap.add_argument("--no-extras", action="store_true", help="skip baselines (for profiling)")
     ap.add_argument("--batch", type=int, default=0,
                     help="first N problems only (profiling captures); default: the full workload")
@@ -170,10 +174,11 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- oracle samples
-def _oracle_sample(name, batch, idxs, iters, backward=True):
-    """The oracle (FP64 CPU) on the listed problems, forward (+ exact implicit backward):
+def _oracle_sample(name, batch, idxs, iters, backward=True, algo=None, bmode="implicit"):
+    """The oracle (FP64 CPU) on the listed problems, forward (+ the backward ``bmode``):
     (seconds, executed iterations, solutions)."""
-    algo, _, _, lam0 = _setting(name)
+    walgo, _, _, lam0 = _setting(name)
+    algo = algo or walgo
     t0 = time.perf_counter()
     n_it, sols = 0, {}
     if name.startswith("ba"):
@@ -194,7 +199,10 @@ def _oracle_sample(name, batch, idxs, iters, backward=True):
         sols[b] = th
         if backward:
             v = pgo.tangent_grad(g.kind, lambda X: pgo.pose_error_loss(g.kind, X, g.theta_gt), th)
-            pgo.implicit_grads(g, th, v, "exact")
+            if bmode == "dlm":
+                pgo.dlm_grads(g, th, v)
+            else:
+                pgo.implicit_grads(g, th, v, "gn" if bmode == "implicit_gn" else "exact")
     return time.perf_counter() - t0, n_it, sols
 
 
@@ -210,25 +218,27 @@ def run_reference(args):
     name = args.workload
     algo, iters, _, _ = _setting(name)
     is_ba = name.startswith("ba")
+    algo = algo if is_ba else (args.algo or algo)
     batch = synth.workload(name, batch=2)
     its_per = 2 if is_ba else iters
     cores = torch.get_num_threads()
+    kw = dict(backward=not is_ba, algo=algo, bmode=args.backward)
     for _ in range(1 if is_ba else args.warmup):
-        _oracle_sample(name, batch, [0], its_per, backward=not is_ba)
+        _oracle_sample(name, batch, [0], its_per, **kw)
     secs, its = 0.0, 0
     for s in range(args.steps):
-        dt, n, _ = _oracle_sample(name, batch, [s % 2], its_per, backward=not is_ba)
+        dt, n, _ = _oracle_sample(name, batch, [s % 2], its_per, **kw)
         secs += dt
         its += n
     value = its / secs
     sample = (f"1 problem x {its_per} LM its (whole-system sparse solve) per step" if is_ba else
-              f"1 problem x ({iters} {algo.upper()} its + exact implicit bwd) per step")
+              f"1 problem x ({iters} {algo.upper()} its + {args.backward} bwd) per step")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "LM iters/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded generator)",
             "config": {"workload": name, "problems_per_step": 1, "iterations": its_per,
-                       "backward": "none" if is_ba else "implicit exact"},
+                       "algorithm": algo.upper(), "backward": "none" if is_ba else args.backward},
             "cpu_baseline": {"value": value, "unit": "LM iters/s", "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "LM iters/s", "h2d_bytes_per_step": 0,
@@ -313,6 +323,8 @@ def run_pose_graphs(args, rank, world, local, dist, out):
 
     name = args.workload
     algo, iters, precision, lam0 = _setting(name)
+    algo = args.algo or algo
+    bmode = args.backward
     dev = torch.device("cuda", local)
     first, per_rank = rank_problems(rank, args.batch or PER_GPU[name])
     batch = synth.workload(name, batch=per_rank, first=first)
@@ -320,7 +332,7 @@ def run_pose_graphs(args, rank, world, local, dist, out):
     st = layer.PoseGraphStructure.from_batch(batch)
     stats = st.stats()
     opts = layer.Options(algo=algo, iters=iters, precision=precision, tau=0.0,
-                         backward_mode="implicit", lambda0=lam0)
+                         backward_mode=bmode, lambda0=lam0)
     t64 = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
     theta0 = t64(batch.theta_init)
     meas, wd = t64(batch.meas), t64(batch.wdiag)
@@ -349,6 +361,7 @@ def run_pose_graphs(args, rank, world, local, dist, out):
     torch.cuda.synchronize()
     info = solver.info_dict()
     executed = int(info["iterations"].sum())
+    nfact = info["factorizations"].astype(np.float64)
     ms_per_step, fwd_ms, bwd_ms, clocks = _timed_region(step, args, world, dist, dev, stream, local)
     sizes = np.diff(batch.pose_offsets)
     out.update({
@@ -361,11 +374,14 @@ def run_pose_graphs(args, rank, world, local, dist, out):
                              else f"{int(sizes.min())}..{int(sizes.max())}"),
                    "costs": st.n_costs, "iterations": iters, "algorithm": algo.upper(),
                    "precision": precision,
-                   "backward": "implicit, true Hessian, cached factor + refinement",
+                   "backward": {"implicit": "implicit, true Hessian, cached factor + refinement",
+                                "implicit_gn": "implicit, Gauss-Newton Hessian, cached factor + refinement",
+                                "dlm": "direct loss minimization (one GN step, eps 1e-2)"}[bmode],
                    "parallelism": f"{world} GPU(s), problems sharded by rank (weak)",
                    "l2": "flushed between steps"},
         "fwd_ms": fwd_ms, "bwd_ms": bwd_ms,
-        "executed_lm_iterations_per_step": executed, "gpu_launches": 2 * args.steps,
+        "executed_lm_iterations_per_step": executed, "factorizations_per_step": int(nfact.sum()),
+        "gpu_launches": 2 * args.steps,
         "launch_shape": {k: tuned[k] for k in ("threads", "ctas_per_sm", "smem_factor")},
         "autotune_table": tuned["table"],
         "backward_refine_steps_mean": float(np.mean(info["refine_steps"])),
@@ -376,18 +392,22 @@ def run_pose_graphs(args, rank, world, local, dist, out):
     # roofline of the dominant kernel (the forward, FP64-factorization bound): algorithmic FP64
     # flops of the factorizations it runs / its duration, against the FP64 FMA peak probed now
     peak = _fp64_peak(stream)
-    achieved = stats["factor_flops"] / B * executed / (fwd_ms * 1e-3) / 1e12
+    # per-problem factorization flops x the factorizations each problem ran (GN/LM: one per
+    # iteration; dogleg: one per linearization)
+    achieved = float((np.asarray(st.factor_flops_per_problem()) * nfact).sum()) / (fwd_ms * 1e-3) / 1e12
+    kname = "k_forward_dogleg" if algo == "dogleg" else "k_forward"
     out["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                       "frac": achieved / peak, "traffic": captured_traffic(name, B),
-                       "kernel": f"k_forward<{batch.kind},{'double' if precision == 'fp64' else 'float'}>"
-                                 " (FP64 block Cholesky flops)",
+                       "frac": achieved / peak,
+                       "traffic": captured_traffic(name, B) if algo != "dogleg" else None,
+                       "kernel": f"{kname}<{batch.kind},{'double' if precision == 'fp64' else 'float'}>"
+                                 " (FP64 block Cholesky flops of the factorizations run)",
                        "peak_source": "FP64 FMA probe on this GPU (dnls_probe_fp64_peak), of measured"}
     out["factor"] = {"flops_per_factorization_batch": stats["factor_flops"],
                      "dense_equivalent_flops": stats["dense_flops"],
                      "block_updates": stats["n_block_updates"], "levels_max": stats["n_levels_max"]}
     # accuracy at this configuration against the oracle on sampled problems
     sample = sorted({0, B // 2, B - 1, int(sizes.argmax())})
-    _, _, sols = _oracle_sample(name, batch, sample, iters, backward=False)
+    _, _, sols = _oracle_sample(name, batch, sample, iters, backward=False, algo=algo)
     th_cpu = theta.cpu()
     errs = [float((th_cpu[int(batch.pose_offsets[b]):int(batch.pose_offsets[b + 1])] - sols[b]).norm()
                   / sols[b].norm()) for b in sample]
@@ -399,7 +419,12 @@ def run_pose_graphs(args, rank, world, local, dist, out):
     for b_ in sample[:2]:
         p0, p1 = int(batch.pose_offsets[b_]), int(batch.pose_offsets[b_ + 1])
         e0, e1 = int(batch.edge_offsets[b_]), int(batch.edge_offsets[b_ + 1])
-        rm, rl, _ = pgo.implicit_grads(pgo.graph_from_batch(batch, b_), th_cpu[p0:p1], v_cpu[p0:p1], "exact")
+        g_ = pgo.graph_from_batch(batch, b_)
+        if bmode == "dlm":
+            rm, rl, _ = pgo.dlm_grads(g_, th_cpu[p0:p1], v_cpu[p0:p1], opts.dlm_eps)
+        else:
+            rm, rl, _ = pgo.implicit_grads(g_, th_cpu[p0:p1], v_cpu[p0:p1],
+                                           "gn" if bmode == "implicit_gn" else "exact")
         gerrs.append(max(float((gm_cpu[e0:e1] - rm).norm() / rm.norm()),
                          float((gl_cpu[e0:e1] - rl).norm() / rl.norm())))
     out["accuracy"] = {"max_rel_err_vs_oracle": max(errs), "sampled_problems": sample,
@@ -413,7 +438,7 @@ def run_pose_graphs(args, rank, world, local, dist, out):
         one = batch.problem(b_)
         s1 = layer.PoseGraphSolver(layer.PoseGraphStructure.from_batch(one),
                                    layer.Options(algo=algo, iters=iters, precision="fp64", tau=0.0,
-                                                 lambda0=lam0), dev)
+                                                 lambda0=lam0, backward_mode=bmode), dev)
         a1 = [t64(one.theta_init), t64(one.meas), t64(one.wdiag),
               torch.as_tensor(one.logw, dtype=torch.float32, device=dev)]
         v1 = t64(rng.normal(size=(int(one.pose_offsets[-1]), dof)) * 1e-2)
@@ -442,11 +467,11 @@ def run_pose_graphs(args, rank, world, local, dist, out):
 
     out["e2e"] = _e2e(run, h_in, h_out, d_in, args.steps, stream, executed)
     # CPU baseline: the oracle as it stands on a bounded sample (2 problems, fwd + bwd)
-    secs, its, _ = _oracle_sample(name, batch, list(range(min(2, B))), iters)
+    secs, its, _ = _oracle_sample(name, batch, list(range(min(2, B))), iters, algo=algo, bmode=bmode)
     out["cpu_baseline"] = {"value": its / secs, "unit": "LM iters/s", "cores": torch.get_num_threads(),
                            "kind": "oracle",
-                           "sample": f"{min(2, B)} problems x ({iters} {algo.upper()} its + exact "
-                                     "implicit bwd), FP64 torch CPU"}
+                           "sample": f"{min(2, B)} problems x ({iters} {algo.upper()} its + {bmode} "
+                                     "bwd), FP64 torch CPU"}
 
 
 # ----------------------------------------------------------------------------- bundle adjustment

@@ -57,7 +57,7 @@ enum {
 };
 
 enum { DNLS_SE2 = 2, DNLS_SE3 = 3 };
-enum { DNLS_GN = 0, DNLS_LM = 1 };
+enum { DNLS_GN = 0, DNLS_LM = 1, DNLS_DOGLEG = 2 };
 enum { DNLS_FP64 = 0, DNLS_MIXED_FP32 = 1 };
 /* backward modes: implicit differentiation (Eq. 3 / Prop. 1) with the true Hessian or the
  * Gauss-Newton matrix, or direct loss minimization (Sec. 4.3, App. G; pose graphs only) */
@@ -70,9 +70,15 @@ enum { DNLS_ORDER_MIN_DEGREE = 0, DNLS_ORDER_NATURAL = 1 };
  * [1e-12, 1e12], accept iff S_new <= S_old (a tie is accepted: near an ill-conditioned optimum
  * S is flat to FP64 resolution along weak directions, where the GN step must still move); with
  * tau > 0 a problem stops once |S_old - S_new| <= tau*S_old (tau = 0: every iteration runs).
- * A rejected step counts as an iteration. */
+ * A rejected step counts as an iteration.
+ * DNLS_DOGLEG (the trust-region method listed next to GN and LM): Powell's dogleg step between
+ * the Cauchy point -(g'g / g'Hg) g and the Gauss-Newton step -H^-1 g (H = J'J undamped, FP64
+ * factor) inside ||p|| <= radius (Euclidean norm of the stacked tangent step); rho = actual /
+ * predicted reduction; radius /4 if rho < 1/4, x2 if rho > 3/4 and the step is on the boundary,
+ * clamped to [1e-12, 1e12]; accept iff S_new <= S_old; after a rejection only the radius
+ * changes.  dnls_info.lambda then reports the final radius. */
 typedef struct {
-  int32_t algo;            /* DNLS_GN or DNLS_LM */
+  int32_t algo;            /* DNLS_GN, DNLS_LM or DNLS_DOGLEG (pose graphs only) */
   int32_t iters;           /* number of iterations K (>= 0) */
   int32_t precision;       /* DNLS_FP64, or DNLS_MIXED_FP32 (residuals, Jacobians and H in FP32;
                               relative poses, g, the factorization and the acceptance in FP64) */
@@ -86,6 +92,7 @@ typedef struct {
   double tau;              /* freeze threshold on the relative decrease of S */
   double refine_tol;       /* adjoint solve stops once ||v - H x|| <= refine_tol * ||v|| */
   double dlm_eps;          /* DNLS_BACKWARD_DLM: the finite-difference scale eps (> 0) */
+  double radius0;          /* DNLS_DOGLEG: initial trust radius (> 0) */
 } dnls_solver_opts;
 
 /* Per-problem report (device array of `batch` entries, written by forward/backward). */
@@ -98,6 +105,9 @@ typedef struct {
   int32_t accepted;     /* accepted steps */
   int32_t status;       /* DNLS_PROBLEM_* (forward); backward overwrites on failure */
   int32_t refine_steps; /* backward: refinement steps taken */
+  int32_t factorizations; /* forward: numeric Cholesky factorizations run (GN/LM: one per
+                             iteration; dogleg: one per linearization) */
+  int32_t reserved;     /* zero */
 } dnls_info;
 
 /* ------------------------------------------------------------------------------------------
@@ -252,7 +262,8 @@ dnls_status dnls_ba_workspace_size(const dnls_ba* h, const dnls_solver_opts* opt
 /* opts->iters GN/LM iterations on every problem (one launch sequence for the whole batch).
  *   cams: device [C, 12] FP64 in/out;  pts: device [Pt, 3] FP64 in/out;  info: device [B] or NULL.
  * LM damping D = diag(max(diag H, 1e-9)) acts on the full (camera + point) system before the
- * elimination.  Errors: DNLS_ERR_ARG, DNLS_ERR_WORKSPACE, DNLS_ERR_CUDA. */
+ * elimination.  Errors: DNLS_ERR_ARG, DNLS_ERR_WORKSPACE, DNLS_ERR_CUDA, DNLS_ERR_UNSUPPORTED
+ * (algo DNLS_DOGLEG, which only the pose-graph solver implements). */
 dnls_status dnls_ba_forward(const dnls_ba* h, const dnls_solver_opts* opts, const dnls_ba_inputs* in,
                             double* cams, double* pts, void* workspace, size_t workspace_bytes,
                             void* stream, dnls_info* info);
@@ -274,6 +285,12 @@ typedef struct {
   double dense_flops;    /* flops an n^3/3 dense Cholesky would take on the same batch */
 } dnls_graph_stats;
 dnls_status dnls_graph_get_stats(const dnls_graph* g, dnls_graph_stats* out);
+
+/* FP64 flops of one numeric block Cholesky factorization of each problem (from the symbolic
+ * structure; the same count dnls_graph_stats.factor_flops sums), written to the host array
+ * flops[batch].  Used to state the achieved fraction of the FP64 roofline.
+ * Errors: DNLS_ERR_ARG. */
+dnls_status dnls_graph_get_problem_flops(const dnls_graph* g, double* flops);
 
 /* Human-readable name of a status code (static storage). */
 const char* dnls_status_string(dnls_status s);

@@ -151,6 +151,8 @@ def dogleg_step(J, r, delta):
     pB = -torch.cholesky_solve(g[:, None], L)[:, 0] if int(info) == 0 else None
     if pB is not None and float(pB.norm()) <= delta:
         p, boundary = pB, False
+    elif gg == 0.0:
+        p, boundary = torch.zeros_like(g), False
     elif gBg <= 0.0 or (gg / gBg) * math.sqrt(gg) >= delta or pB is None:
         p, boundary = -(delta / math.sqrt(gg)) * g, True
     else:

@@ -580,6 +580,8 @@ __global__ void k_ba_info(BAArgs a, int backward) {
     in.status = s.status;
     in.refine_resid = 0.0;
     in.refine_steps = 0;
+    in.factorizations = s.iters;  // one reduced-system factorization per iteration
+    in.reserved = 0;
   } else {
     in.refine_resid = s.rel;
     in.refine_steps = s.refine_steps;
@@ -1062,7 +1064,8 @@ dnls_status up(BAHandle& G, const T** dst, const std::vector<T>& src) {
 
 dnls_status ba_check_opts(const dnls_solver_opts* o) {
   if (!o) return DNLS_ERR_ARG;
-  if (o->algo != DNLS_GN && o->algo != DNLS_LM) return DNLS_ERR_ARG;
+  // DNLS_DOGLEG is a valid option value; dnls_ba_forward answers it with DNLS_ERR_UNSUPPORTED
+  if (o->algo != DNLS_GN && o->algo != DNLS_LM && o->algo != DNLS_DOGLEG) return DNLS_ERR_ARG;
   if (o->iters < 0 || o->iters > 100000) return DNLS_ERR_ARG;
   if (o->precision != DNLS_FP64 && o->precision != DNLS_MIXED_FP32) return DNLS_ERR_ARG;
   if (!(o->lambda0 >= 0.0) || !(o->tau >= 0.0)) return DNLS_ERR_ARG;
@@ -1208,6 +1211,7 @@ dnls_status dnls_ba_forward(const dnls_ba* h, const dnls_solver_opts* opts, cons
   if (!h || !in || !cams || !pts || !in->obs || (h->impl.h.Q > 0 && (!in->prior_meas || !in->prior_w)))
     return DNLS_ERR_ARG;
   if (!(in->focal > 0.0)) return DNLS_ERR_ARG;
+  if (opts && opts->algo == DNLS_DOGLEG) return DNLS_ERR_UNSUPPORTED;  // pose graphs only
   dnls_status s = ba_check_opts(opts);
   if (s != DNLS_OK) return s;
   if (!workspace || ((uintptr_t)workspace & 255) || (int64_t)workspace_bytes < h->impl.h.ws_bytes)

@@ -25,6 +25,8 @@
 #include "dnls_cost.cuh"
 #include "dnls_graph.h"
 
+static_assert(sizeof(dnls_info) == 56, "dnls_info layout is part of the ABI");
+
 namespace dnls {
 
 constexpr double kLamMin = 1e-12, kLamMax = 1e12;
@@ -55,7 +57,7 @@ struct KArgs {
   int* counter;
   dnls_info* info;
   int algo, iters, mode, refine_max;
-  double lam0, tau, refine_tol, dlm_eps;
+  double lam0, tau, refine_tol, dlm_eps, radius0;
   int smem_bytes;       // dynamic shared memory per CTA for staging (0 = none)
 };
 
@@ -363,9 +365,10 @@ __device__ void forward_problem(const KArgs& a, int b, char* smem, double* red, 
   __syncthreads();
   const bool lm = a.algo == DNLS_LM;
   double lam = lm ? a.lam0 : 0.0, lam_fact = lam;
-  int done = 0, accepted = 0, status = DNLS_PROBLEM_OK, factor_ok = 0;
+  int done = 0, accepted = 0, status = DNLS_PROBLEM_OK, factor_ok = 0, nfact = 0;
   for (int it = 0; it < a.iters; ++it) {
     done = it + 1;
+    ++nfact;
     const bool ok = factor<KIND>(p, lam, sflag, it);
     factor_ok = ok ? 1 : 0;
     lam_fact = lam;
@@ -427,6 +430,161 @@ __device__ void forward_problem(const KArgs& a, int b, char* smem, double* red, 
       in.accepted = accepted;
       in.status = status;
       in.refine_steps = 0;
+      in.factorizations = nfact;
+      in.reserved = 0;
+    }
+  }
+  __syncthreads();
+}
+
+// ----------------------------------------------------------------------------- dogleg
+// x . y over the problem's n = N * D tangent coordinates (fixed-order block reduction)
+template <int KIND>
+__device__ double dotn(const Prob<KIND>& p, const double* x, const double* y, double* red) {
+  double acc = 0.0;
+  for (int k = threadIdx.x; k < p.N * Group<KIND>::DOF; k += blockDim.x) acc = fma(x[k], y[k], acc);
+  return block_sum(acc, red);
+}
+
+// x^T (J^T J) x = sum over costs of ||J_i x_i + J_j x_j||^2 from the stored per-cost Jacobians
+// (x in elimination-position order)
+template <int KIND, class P>
+__device__ double quad_J(const Prob<KIND>& p, const double* x, double* red) {
+  constexpr int D = Group<KIND>::DOF, BS = D * D, JW = Prob<KIND>::JW;
+  const P* Jb = (const P*)p.J;
+  double acc = 0.0;
+  for (int e = threadIdx.x; e < p.E; e += blockDim.x) {
+    const int i = p.ei[e], j = p.ej[e];
+    const P* Ji = Jb + (int64_t)e * JW + D;
+    const double* xi = x + p.iperm[i] * D;
+    const double* xj = j >= 0 ? x + p.iperm[j] * D : nullptr;
+#pragma unroll
+    for (int a2 = 0; a2 < D; ++a2) {
+      double u = 0.0;
+#pragma unroll
+      for (int b2 = 0; b2 < D; ++b2) u = fma((double)Ji[a2 * D + b2], xi[b2], u);
+      if (j >= 0)
+#pragma unroll
+        for (int b2 = 0; b2 < D; ++b2) u = fma((double)Ji[BS + a2 * D + b2], xj[b2], u);
+      acc = fma(u, u, acc);
+    }
+  }
+  return block_sum(acc, red);
+}
+
+// Dogleg trust-region forward for one problem (see DNLS_DOGLEG in dnls.h): the Gauss-Newton
+// step p_B (in bv) and the Cauchy scale are computed once per linearization; each iteration
+// picks the dogleg point for the current radius, predicts the model decrease, and updates the
+// radius from the actual / predicted ratio.
+template <int KIND, class P>
+__device__ void forward_dogleg(const KArgs& a, int b, char* smem, double* red, int* sflag) {
+  constexpr int PW = Group<KIND>::PW;
+  Prob<KIND> p;
+  p.init(a, b, smem, a.smem_bytes);
+  p.stage_in(false);
+  p.prepare_weights();
+  const int n = p.N * Group<KIND>::DOF;
+  double S = eval_S<KIND>(p, p.theta, red);
+  const double S0 = S;
+  lin_costs<KIND, P>(p, p.theta);
+  __syncthreads();
+  assemble<KIND, P>(p);
+  __syncthreads();
+  double delta = a.radius0, gg = 0.0, gBg = 0.0, nB = 0.0;
+  bool fresh = true, okB = false;
+  int done = 0, accepted = 0, factor_ok = 0, nfact = 0;
+  for (int it = 0; it < a.iters; ++it) {
+    done = it + 1;
+    if (fresh) {
+      ++nfact;
+      okB = factor<KIND>(p, 0.0, sflag, it);
+      factor_ok = okB ? 1 : 0;
+      gg = dotn<KIND>(p, p.g, p.g, red);
+      gBg = quad_J<KIND, P>(p, p.g, red);
+      if (okB) {
+        for (int k = threadIdx.x; k < n; k += blockDim.x) p.dx[k] = -p.g[k];
+        __syncthreads();
+        chol_solve<KIND>(p, p.dx);
+        for (int k = threadIdx.x; k < n; k += blockDim.x) p.bv[k] = p.dx[k];
+        __syncthreads();
+        nB = sqrt(dotn<KIND>(p, p.bv, p.bv, red));
+      }
+      fresh = false;
+    }
+    bool boundary = true;
+    if (okB && nB <= delta) {
+      boundary = false;
+      for (int k = threadIdx.x; k < n; k += blockDim.x) p.dx[k] = p.bv[k];
+    } else if (!(gg > 0.0)) {
+      boundary = false;
+      for (int k = threadIdx.x; k < n; k += blockDim.x) p.dx[k] = 0.0;
+    } else if (!okB || !(gBg > 0.0) || (gg / gBg) * sqrt(gg) >= delta) {
+      const double sc = -delta / sqrt(gg);
+      for (int k = threadIdx.x; k < n; k += blockDim.x) p.dx[k] = sc * p.g[k];
+    } else {
+      // p = p_U + s (p_B - p_U) with ||p|| = delta; p_U = -(g.g / g.Bg) g
+      const double cu = -gg / gBg;
+      double dd = 0.0, ud = 0.0;
+      for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const double u = cu * p.g[k], d = p.bv[k] - u;
+        dd = fma(d, d, dd);
+        ud = fma(u, d, ud);
+      }
+      const double A2 = block_sum(dd, red);
+      const double B2 = 2.0 * block_sum(ud, red);
+      const double C2 = cu * cu * gg - delta * delta;
+      const double s = (-B2 + sqrt(B2 * B2 - 4.0 * A2 * C2)) / (2.0 * A2);
+      for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const double u = cu * p.g[k];
+        p.dx[k] = u + s * (p.bv[k] - u);
+      }
+    }
+    __syncthreads();
+    const double pred = -(dotn<KIND>(p, p.g, p.dx, red) + 0.5 * quad_J<KIND, P>(p, p.dx, red));
+    retract<KIND>(p, p.theta, p.dx, p.thc);
+    __syncthreads();
+    const double Sc = eval_S<KIND>(p, p.thc, red);
+    const bool ok = isfinite(Sc);
+    const double rho = (ok && pred > 0.0) ? (S - Sc) / pred : -1.0;
+    if (rho < 0.25)
+      delta *= 0.25;
+    else if (rho > 0.75 && boundary)
+      delta *= 2.0;
+    delta = fmin(fmax(delta, kLamMin), kLamMax);
+    const bool accept = ok && Sc <= S;
+    const bool frozen = ok && a.tau > 0.0 && fabs(S - Sc) <= a.tau * S;
+    if (accept) {
+      for (int k = threadIdx.x; k < p.N * PW; k += blockDim.x) p.theta[k] = p.thc[k];
+      __syncthreads();
+      ++accepted;
+      S = Sc;
+      if (!frozen && it + 1 < a.iters) {
+        lin_costs<KIND, P>(p, p.theta);
+        __syncthreads();
+        assemble<KIND, P>(p);
+        __syncthreads();
+        fresh = true;
+      }
+    }
+    if (frozen) break;
+  }
+  if (factor_ok) p.stage_out_factor();  // undamped factor of the last linearization
+  if (threadIdx.x == 0) {
+    p.st->lambda_fact = 0.0;
+    p.st->S = S;
+    p.st->factor_ok = factor_ok;
+    if (a.info) {
+      dnls_info& in = a.info[b];
+      in.S_init = S0;
+      in.S_final = S;
+      in.lambda = delta;
+      in.refine_resid = 0.0;
+      in.iterations = done;
+      in.accepted = accepted;
+      in.status = DNLS_PROBLEM_OK;
+      in.refine_steps = 0;
+      in.factorizations = nfact;
+      in.reserved = 0;
     }
   }
   __syncthreads();
@@ -453,6 +611,21 @@ __global__ void __launch_bounds__(256) k_forward(KArgs a) {
     if (threadIdx.x == 0) sflag = -1;
     __syncthreads();
     forward_problem<KIND, P>(a, b, a.smem_bytes ? dyn_smem : nullptr, red, &sflag);
+  }
+}
+
+// the dogleg forward as its own kernel, so that the GN/LM kernel's register allocation is not
+// shaped by the trust-region code
+template <int KIND, class P>
+__global__ void __launch_bounds__(256) k_forward_dogleg(KArgs a) {
+  __shared__ double red[256];
+  __shared__ int sflag, slot;
+  for (;;) {
+    const int b = next_problem(a, &slot);
+    if (b < 0) break;
+    if (threadIdx.x == 0) sflag = -1;
+    __syncthreads();
+    forward_dogleg<KIND, P>(a, b, a.smem_bytes ? dyn_smem : nullptr, red, &sflag);
   }
 }
 
@@ -873,7 +1046,8 @@ dnls_status upload(T** dst, const std::vector<T>& src) {
 
 dnls_status check_opts(const dnls_solver_opts* o) {
   if (!o) return DNLS_ERR_ARG;
-  if (o->algo != DNLS_GN && o->algo != DNLS_LM) return DNLS_ERR_ARG;
+  if (o->algo != DNLS_GN && o->algo != DNLS_LM && o->algo != DNLS_DOGLEG) return DNLS_ERR_ARG;
+  if (o->algo == DNLS_DOGLEG && !(o->radius0 > 0.0 && std::isfinite(o->radius0))) return DNLS_ERR_ARG;
   if (o->iters < 0 || o->iters > 100000) return DNLS_ERR_ARG;
   if (o->precision != DNLS_FP64 && o->precision != DNLS_MIXED_FP32) return DNLS_ERR_ARG;
   if (o->backward_mode != DNLS_IMPLICIT_EXACT && o->backward_mode != DNLS_IMPLICIT_GN &&
@@ -929,6 +1103,24 @@ dnls_status launch_persistent(K kernel, const dnls_graph* g, const dnls_solver_o
   if (cudaMemsetAsync(a.counter, 0, sizeof(int), st) != cudaSuccess) return DNLS_ERR_CUDA;
   kernel<<<grid, threads, smem, st>>>(a);
   return cuda_status(cudaGetLastError());
+}
+
+// the forward kernel for the problem kind, precision and algorithm
+dnls_status launch_forward(const dnls_graph* g, const dnls_solver_opts* opts, KArgs& a, cudaStream_t st) {
+  const bool mixed = opts->precision == DNLS_MIXED_FP32;
+  const bool se3 = g->impl.h.kind == DNLS_SE3;
+  if (opts->algo == DNLS_DOGLEG) {
+    if (se3)
+      return mixed ? launch_persistent(k_forward_dogleg<3, float>, g, opts, a, st)
+                   : launch_persistent(k_forward_dogleg<3, double>, g, opts, a, st);
+    return mixed ? launch_persistent(k_forward_dogleg<2, float>, g, opts, a, st)
+                 : launch_persistent(k_forward_dogleg<2, double>, g, opts, a, st);
+  }
+  if (se3)
+    return mixed ? launch_persistent(k_forward<3, float>, g, opts, a, st)
+                 : launch_persistent(k_forward<3, double>, g, opts, a, st);
+  return mixed ? launch_persistent(k_forward<2, float>, g, opts, a, st)
+               : launch_persistent(k_forward<2, double>, g, opts, a, st);
 }
 
 }  // namespace
@@ -996,13 +1188,8 @@ dnls_status dnls_graph_forward(const dnls_graph* g, const dnls_solver_opts* opts
   a.iters = opts->iters;
   a.lam0 = opts->lambda0;
   a.tau = opts->tau;
-  cudaStream_t st = (cudaStream_t)stream;
-  const bool mixed = opts->precision == DNLS_MIXED_FP32;
-  if (g->impl.h.kind == DNLS_SE3)
-    return mixed ? launch_persistent(k_forward<3, float>, g, opts, a, st, true)
-                 : launch_persistent(k_forward<3, double>, g, opts, a, st, true);
-  return mixed ? launch_persistent(k_forward<2, float>, g, opts, a, st, true)
-               : launch_persistent(k_forward<2, double>, g, opts, a, st, true);
+  a.radius0 = opts->radius0;
+  return launch_forward(g, opts, a, (cudaStream_t)stream);
 }
 
 dnls_status dnls_graph_backward(const dnls_graph* g, const dnls_solver_opts* opts,
@@ -1051,6 +1238,13 @@ dnls_status dnls_graph_linearize(const dnls_graph* g, const dnls_solver_opts* op
   else
     k_linearize<2><<<g->impl.h.B, threads, 0, st>>>(a);
   return cuda_status(cudaGetLastError());
+}
+
+dnls_status dnls_graph_get_problem_flops(const dnls_graph* g, double* flops) {
+  if (!g || !flops) return DNLS_ERR_ARG;
+  const GraphHost& h = g->impl.h;
+  for (int b = 0; b < h.B; ++b) flops[b] = h.prob_flops[b];
+  return DNLS_OK;
 }
 
 dnls_status dnls_graph_get_stats(const dnls_graph* g, dnls_graph_stats* out) {
@@ -1119,11 +1313,6 @@ extern "C" dnls_status dnls_graph_forward_noalloc(const dnls_graph* g, const dnl
   a.iters = opts->iters;
   a.lam0 = opts->lambda0;
   a.tau = opts->tau;
-  cudaStream_t st = (cudaStream_t)stream;
-  const bool mixed = opts->precision == DNLS_MIXED_FP32;
-  if (g->impl.h.kind == DNLS_SE3)
-    return mixed ? launch_persistent(k_forward<3, float>, g, opts, a, st, true)
-                 : launch_persistent(k_forward<3, double>, g, opts, a, st, true);
-  return mixed ? launch_persistent(k_forward<2, float>, g, opts, a, st, true)
-               : launch_persistent(k_forward<2, double>, g, opts, a, st, true);
+  a.radius0 = opts->radius0;
+  return launch_forward(g, opts, a, (cudaStream_t)stream);
 }

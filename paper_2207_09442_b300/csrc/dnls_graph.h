@@ -61,6 +61,7 @@ struct GraphHost {
   int32_t max_L_bytes, max_nlev, max_arena_bytes;
   int64_t n_blocks_L, n_upd;
   double factor_flops, dense_flops;
+  std::vector<double> prob_flops;  // FP64 flops of one numeric factorization, per problem
 };
 
 // Workspace header (first bytes of the workspace): the persistent launches' work counters.

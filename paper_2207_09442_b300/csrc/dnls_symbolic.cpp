@@ -425,6 +425,7 @@ int build_graph_host(int kind, int B, const int64_t* pose_offsets, const int64_t
     const double D3 = (double)D * D * D;
     const double ff = 2.0 * n_upd * D3 + (double)nnzL * D * D * (D + 1) + N * (2.0 * D3 / 3.0);
     G.factor_flops += ff;
+    G.prob_flops.push_back(ff);
     G.dense_flops += (double)n * n * n / 3.0;
     cost[b] = ff + 200.0 * E;
   }

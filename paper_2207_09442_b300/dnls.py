@@ -20,7 +20,7 @@ c_int32, c_int64, c_double, c_void_p, c_size_t = (ctypes.c_int32, ctypes.c_int64
 OK, ERR_ARG, ERR_CUDA, ERR_WORKSPACE, ERR_TIMEOUT, ERR_UNSUPPORTED = range(6)
 PROBLEM_OK, PROBLEM_NOT_CONVERGED, PROBLEM_NOT_SPD, PROBLEM_NAN = range(4)
 SE2, SE3 = 2, 3
-GN, LM = 0, 1
+GN, LM, DOGLEG = 0, 1, 2
 FP64, MIXED_FP32 = 0, 1
 IMPLICIT_EXACT, IMPLICIT_GN, BACKWARD_DLM = 0, 1, 2
 ORDER_MIN_DEGREE, ORDER_NATURAL = 0, 1
@@ -30,7 +30,7 @@ class SolverOpts(ctypes.Structure):
     _fields_ = [("algo", c_int32), ("iters", c_int32), ("precision", c_int32),
                 ("backward_mode", c_int32), ("refine_max", c_int32), ("threads", c_int32),
                 ("ctas_per_sm", c_int32), ("smem_factor", c_int32), ("lambda0", c_double),
-                ("tau", c_double), ("refine_tol", c_double), ("dlm_eps", c_double)]
+                ("tau", c_double), ("refine_tol", c_double), ("dlm_eps", c_double), ("radius0", c_double)]
 
 
 class GraphDesc(ctypes.Structure):
@@ -60,7 +60,7 @@ class BAInputs(ctypes.Structure):
                 ("focal", c_double), ("huber_delta", c_double)]
 
 
-INFO_BYTES = 48  # dnls_info: 4 doubles + 4 int32
+INFO_BYTES = 56  # dnls_info: 4 doubles + 6 int32
 
 
 class DnlsError(RuntimeError):
@@ -86,6 +86,7 @@ _SIGS = {
     "dnls_project_grad": (c_int32, [c_int32, c_int64, c_void_p, c_void_p, c_void_p, c_void_p]),
     "dnls_lift_grad": (c_int32, [c_int32, c_int64, c_void_p, c_void_p, c_void_p, c_void_p]),
     "dnls_graph_get_stats": (c_int32, [c_void_p, ctypes.POINTER(GraphStats)]),
+    "dnls_graph_get_problem_flops": (c_int32, [c_void_p, c_void_p]),
     "dnls_status_string": (ctypes.c_char_p, [c_int32]),
     "dnls_ba_create": (c_int32, [ctypes.POINTER(BADesc), ctypes.POINTER(c_void_p)]),
     "dnls_ba_destroy": (None, [c_void_p]),

@@ -21,7 +21,7 @@ from . import dnls as _d
 @dataclasses.dataclass
 class Options:
     """Solver options (see dnls_solver_opts in include/dnls.h)."""
-    algo: str = "lm"                 # "gn" | "lm"
+    algo: str = "lm"                 # "gn" | "lm" | "dogleg"
     iters: int = 20
     precision: str = "mixed_fp32"    # "fp64" | "mixed_fp32"
     backward_mode: str = "implicit"  # "implicit" (true Hessian) | "implicit_gn" | "dlm"
@@ -33,11 +33,15 @@ class Options:
     ctas_per_sm: int = 0
     smem_factor: int = 1
     dlm_eps: float = 1e-2            # backward_mode "dlm": finite-difference scale eps
+    radius0: float = 1.0             # algo "dogleg": initial trust radius
 
     def c(self) -> _d.SolverOpts:
         fp64 = self.precision == "fp64"
         o = _d.SolverOpts()
-        o.algo = _d.GN if self.algo == "gn" else _d.LM
+        algos = {"gn": _d.GN, "lm": _d.LM, "dogleg": _d.DOGLEG}
+        if self.algo not in algos:
+            raise ValueError(f"unknown algo {self.algo!r}")
+        o.algo = algos[self.algo]
         o.iters = int(self.iters)
         o.precision = _d.FP64 if fp64 else _d.MIXED_FP32
         modes = {"implicit": _d.IMPLICIT_EXACT, "implicit_gn": _d.IMPLICIT_GN, "dlm": _d.BACKWARD_DLM}
@@ -52,6 +56,7 @@ class Options:
         o.tau = float(self.tau if self.tau is not None else (1e-14 if fp64 else 1e-10))
         o.refine_tol = float(self.refine_tol if self.refine_tol is not None else (1e-11 if fp64 else 1e-7))
         o.dlm_eps = float(self.dlm_eps)
+        o.radius0 = float(self.radius0)
         return o
 
 
@@ -94,6 +99,12 @@ class PoseGraphStructure:
         _d.check(_d.lib().dnls_graph_get_stats(self._h, ctypes.byref(s)), "dnls_graph_get_stats")
         return {f: getattr(s, f) for f, _ in s._fields_}
 
+    def factor_flops_per_problem(self) -> np.ndarray:
+        """FP64 flops of one numeric factorization of each problem."""
+        out = np.zeros(self.batch, dtype=np.float64)
+        _d.check(_d.lib().dnls_graph_get_problem_flops(self._h, out.ctypes.data), "dnls_graph_get_problem_flops")
+        return out
+
     def __del__(self):
         if getattr(self, "_h", None) is not None and _d._lib is not None:
             _d.lib().dnls_graph_destroy(self._h)
@@ -107,12 +118,12 @@ def _stream():
 def info_to_dict(info: torch.Tensor) -> dict:
     """Decode a device dnls_info array into host numpy arrays."""
     raw = info.cpu()
-    f = raw.view(torch.float64).reshape(-1, 6)
-    i = raw.view(torch.int32).reshape(-1, 12)
+    f = raw.view(torch.float64).reshape(-1, 7)
+    i = raw.view(torch.int32).reshape(-1, 14)
     return {"S_init": f[:, 0].numpy(), "S_final": f[:, 1].numpy(), "lambda": f[:, 2].numpy(),
             "refine_resid": f[:, 3].numpy(), "iterations": i[:, 8].numpy(),
             "accepted": i[:, 9].numpy(), "status": i[:, 10].numpy(),
-            "refine_steps": i[:, 11].numpy()}
+            "refine_steps": i[:, 11].numpy(), "factorizations": i[:, 12].numpy()}
 
 
 class PoseGraphSolver:

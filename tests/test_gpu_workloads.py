@@ -32,6 +32,7 @@ def test_full_se3_b256_mixed_sampled():
     sol, theta, _ = run_forward(b, opts)
     info = sol.info_dict()
     assert (info["status"] == 0).all()
+    assert (info["factorizations"] == info["iterations"]).all()  # LM factors every iteration
     for k in (0, 97, 255):
         _, ref, _ = oracle_solve(b, k, opts)
         assert rel(poses_of(b, theta, k), ref) < 1e-5, k
