@@ -19,6 +19,10 @@ What it follows:
     theta* (+) xi the "exact" mode uses the true Hessian d^2 S / d xi^2 at xi = 0; the "gn" mode
     uses sum J^T J (what a Gauss-Newton implementation differentiates).
   * Unrolled backward (Sec. 4.3 "Unrolling"): autograd through every iteration of this solver.
+  * Robust costs (Sec. 3 "robust loss functions"; Sec. 3.1 / App. D.1 learn the radius of a
+    Welsch loss for PGO): with per-cost log radii u_e, S = 1/2 sum rho_e(||r_e||^2),
+    rho(s) = c^2 (1 - exp(-s / c^2)), c = exp(u).  GN/LM/dogleg linearize by IRLS (sqrt(rho'(s))
+    scales r and J; rho'' is dropped), the exact Hessian and D_phi g keep every term.
   * Direct loss minimization (Sec. 4.3, App. G): g_DLM = (dS/dphi(theta*) - dS/dphi(theta_direct))
     / eps, theta_direct one GN step from theta* on S + ||eps xi - v/2||^2 (see nls.dlm_direct_step).
 
@@ -51,6 +55,7 @@ class Graph:
     logw: torch.Tensor        # [E]
     theta_init: torch.Tensor  # [N, pw]
     theta_gt: torch.Tensor    # [N, pw]
+    log_radius: Optional[torch.Tensor] = None  # [E] log Welsch radius (None: plain squares)
 
     @property
     def dof(self):
@@ -71,7 +76,8 @@ def graph_from_batch(batch, b: int) -> Graph:
                  torch.as_tensor(batch.edge_j[e0:e1].astype(np.int64)),
                  t(batch.meas[e0:e1]), t(batch.wdiag[e0:e1]),
                  t(batch.logw[e0:e1].astype(np.float64)), t(batch.theta_init[p0:p1]),
-                 t(batch.theta_gt[p0:p1]))
+                 t(batch.theta_gt[p0:p1]),
+                 None if batch.log_radius is None else t(batch.log_radius[e0:e1]))
 
 
 # ----------------------------------------------------------------------------- costs
@@ -122,18 +128,36 @@ def residuals(g: Graph, theta, xi=None, eps=None, logw=None):
     return w * c
 
 
-def objective(g: Graph, theta, **kw):
-    """Eq. 1: S = 1/2 sum ||r_e||^2."""
+def welsch(s, log_c):
+    """Welsch loss on the squared norm s with radius c = exp(log_c): c^2 (1 - exp(-s / c^2))
+    (tends to s as c grows; bounded by c^2)."""
+    c2 = torch.exp(2.0 * log_c)
+    return -c2 * torch.expm1(-s / c2)
+
+
+def welsch_d1(s, log_c):
+    """d rho / d s = exp(-s / c^2)."""
+    return torch.exp(-s / torch.exp(2.0 * log_c))
+
+
+def objective(g: Graph, theta, log_radius=None, **kw):
+    """Eq. 1: S = 1/2 sum ||r_e||^2, or 1/2 sum rho_e(||r_e||^2) with the graph's Welsch radii
+    (``log_radius`` replaces them)."""
     r = residuals(g, theta, **kw)
-    return 0.5 * (r * r).sum()
+    s = (r * r).sum(-1)
+    lr = g.log_radius if log_radius is None else log_radius
+    if lr is None:
+        return 0.5 * s.sum()
+    return 0.5 * welsch(s, lr).sum()
 
 
-def jacobian(g: Graph, theta, eps=None, logw=None):
+def jacobian(g: Graph, theta, eps=None, logw=None, log_radius=None):
     """Stacked residual vector r [E*dof] and Jacobian J = dr/dxi [E*dof, N*dof] at xi = 0.
 
     Each cost's local Jacobian w.r.t. the tangents of its own poses is taken by forward-mode
     autograd (vmapped over costs of one type) and placed at that cost's rows and pose columns;
-    all other entries of J are zero by definition."""
+    all other entries of J are zero by definition.  With robust costs both are scaled per cost
+    by sqrt(rho'(||r_e||^2)) (IRLS), so that J^T r is the gradient of the robust S."""
     dof, N = g.dof, g.n_poses
     E = g.ei.shape[0]
     if eps is None:
@@ -166,6 +190,11 @@ def jacobian(g: Graph, theta, eps=None, logw=None):
         Ji = vmap(jacfwd(fp, argnums=4))(theta[i], g.Z[idx], w[idx], eps[idx],
                                          zero.expand(len(idx), dof))
         J = _place(J, idx, i, Ji)
+    lr = g.log_radius if log_radius is None else log_radius
+    if lr is not None:
+        sw = torch.sqrt(welsch_d1((r * r).sum(-1), lr))
+        r = r * sw[:, None]
+        J = J * sw[:, None, None, None]
     return r.reshape(-1), J.reshape(E * dof, N * dof)
 
 
@@ -181,7 +210,7 @@ def _place(J, rows, cols, blocks):
 
 # ----------------------------------------------------------------------------- solver
 def solve(g: Graph, theta0=None, algo="lm", iters=20, lam0=1e-3, tau=1e-14,
-          eps=None, logw=None, record=False, radius0=1.0):
+          eps=None, logw=None, record=False, radius0=1.0, log_radius=None):
     """K iterations of GN (algo='gn': no damping, always accept), LM, or the dogleg trust-region
     method (algo='dogleg', initial radius ``radius0``) from theta0 (default theta_init).
     Returns (theta, nls.SolveInfo).  Differentiable w.r.t. ``eps`` / ``logw`` when they require
@@ -189,22 +218,24 @@ def solve(g: Graph, theta0=None, algo="lm", iters=20, lam0=1e-3, tau=1e-14,
     theta = g.theta_init if theta0 is None else theta0
     dof = g.dof
     if algo == "dogleg":
-        return nls.dogleg_loop(lambda th: jacobian(g, th, eps=eps, logw=logw),
-                               lambda th: objective(g, th, eps=eps, logw=logw),
+        return nls.dogleg_loop(lambda th: jacobian(g, th, eps=eps, logw=logw, log_radius=log_radius),
+                               lambda th: objective(g, th, eps=eps, logw=logw, log_radius=log_radius),
                                lambda th, d: lie.pose_retract(g.kind, th, d.reshape(-1, dof)),
                                theta, iters=iters, delta0=radius0, tau=tau, record=record)
-    return nls.lm_loop(lambda th: jacobian(g, th, eps=eps, logw=logw),
-                       lambda th: objective(g, th, eps=eps, logw=logw),
+    return nls.lm_loop(lambda th: jacobian(g, th, eps=eps, logw=logw, log_radius=log_radius),
+                       lambda th: objective(g, th, eps=eps, logw=logw, log_radius=log_radius),
                        lambda th, d: lie.pose_retract(g.kind, th, d.reshape(-1, dof)),
                        theta, algo=algo, iters=iters, lam0=lam0, tau=tau, record=record)
 
 
-def solve_to_convergence(g: Graph, theta0, eps=None, logw=None, tol=1e-14, max_iters=100):
-    """Undamped GN from a nearby point until max|delta| < tol (used to re-solve for FD checks)."""
+def solve_to_convergence(g: Graph, theta0, eps=None, logw=None, tol=1e-14, max_iters=100,
+                         log_radius=None):
+    """Undamped GN (IRLS for robust costs) from a nearby point until max|delta| < tol (used to
+    re-solve for FD checks)."""
     theta = theta0
     dof = g.dof
     for _ in range(max_iters):
-        r, J = jacobian(g, theta, eps=eps, logw=logw)
+        r, J = jacobian(g, theta, eps=eps, logw=logw, log_radius=log_radius)
         delta = -torch.linalg.solve(J.T @ J, J.T @ r)
         theta = lie.pose_retract(g.kind, theta, delta.reshape(-1, dof))
         if float(delta.abs().max()) < tol:
@@ -230,33 +261,39 @@ def tangent_grad(kind, loss_fn: Callable, theta):
 
 
 # ----------------------------------------------------------------------------- implicit backward
-def _local_objective_fns(kind, dof):
+def _local_objective_fns(kind, dof, robust):
+    """Per-cost S_e(x, phi) with phi = (measurement tangent eps (dof), log-weight, log-radius)."""
+    def loss(r, phi):
+        s = (r * r).sum()
+        return 0.5 * (welsch(s, phi[dof + 1]) if robust else s)
+
     def s_between(x, phi, Ti, Tj, Z, d):
         c = between_cost(kind, Ti, Tj, Z, x[:dof], x[dof:], phi[:dof])
-        r = torch.exp(phi[dof]) * d * c
-        return 0.5 * (r * r).sum()
+        return loss(torch.exp(phi[dof]) * d * c, phi)
 
     def s_prior(x, phi, Ti, Z, d):
         c = prior_cost(kind, Ti, Z, x, phi[:dof])
-        r = torch.exp(phi[dof]) * d * c
-        return 0.5 * (r * r).sum()
+        return loss(torch.exp(phi[dof]) * d * c, phi)
     return s_between, s_prior
 
 
 def exact_hessian_and_mixed(g: Graph, theta):
     """H = d^2 S(theta (+) xi)/d xi^2 at 0 [n, n] and, per cost e, the mixed derivative
-    M_e = d/d phi_e (d S_e / d x_e) [E, local, dof+1] with phi_e = (measurement tangent eps_e,
-    log-weight l_e) and x_e the stacked tangents of the cost's poses."""
+    M_e = d/d phi_e (d S_e / d x_e) [E, local, dof+2] with phi_e = (measurement tangent eps_e,
+    log-weight l_e, log-radius u_e) and x_e the stacked tangents of the cost's poses (the radius
+    column is zero without robust costs)."""
     dof, N, E = g.dof, g.n_poses, g.ei.shape[0]
-    s_between, s_prior = _local_objective_fns(g.kind, dof)
+    robust = g.log_radius is not None
+    s_between, s_prior = _local_objective_fns(g.kind, dof, robust)
+    lr = g.log_radius if robust else torch.zeros(E, dtype=F64)
     pri, btw = _split(g)
     H = torch.zeros(N * dof, N * dof, dtype=F64)
-    M = torch.zeros(E, 2 * dof, dof + 1, dtype=F64)
+    M = torch.zeros(E, 2 * dof, dof + 2, dtype=F64)
     if bool(btw.any()):
         idx = btw.nonzero()[:, 0]
         i, j = g.ei[idx], g.ej[idx]
         x0 = torch.zeros(len(idx), 2 * dof, dtype=F64)
-        phi0 = torch.cat([torch.zeros(len(idx), dof, dtype=F64), g.logw[idx, None]], 1)
+        phi0 = torch.cat([torch.zeros(len(idx), dof, dtype=F64), g.logw[idx, None], lr[idx, None]], 1)
         args = (theta[i], theta[j], g.Z[idx], g.d[idx])
         He = vmap(hessian(s_between, argnums=0))(x0, phi0, *args)
         Me = vmap(jacfwd(jacrev(s_between, argnums=0), argnums=1))(x0, phi0, *args)
@@ -268,7 +305,7 @@ def exact_hessian_and_mixed(g: Graph, theta):
         idx = pri.nonzero()[:, 0]
         i = g.ei[idx]
         x0 = torch.zeros(len(idx), dof, dtype=F64)
-        phi0 = torch.cat([torch.zeros(len(idx), dof, dtype=F64), g.logw[idx, None]], 1)
+        phi0 = torch.cat([torch.zeros(len(idx), dof, dtype=F64), g.logw[idx, None], lr[idx, None]], 1)
         args = (theta[i], g.Z[idx], g.d[idx])
         He = vmap(hessian(s_prior, argnums=0))(x0, phi0, *args)
         Me = vmap(jacfwd(jacrev(s_prior, argnums=0), argnums=1))(x0, phi0, *args)
@@ -297,6 +334,22 @@ def implicit_grads(g: Graph, theta_star, v, mode="exact"):
                                           x[g.ej.clamp(min=0)])], 1)
     gphi = -torch.einsum('ekp,ek->ep', M, xe)
     return gphi[:, :dof], gphi[:, dof], x
+
+
+def implicit_grad_log_radius(g: Graph, theta_star, v, mode="exact"):
+    """Eq. 3 w.r.t. the per-cost log Welsch radii: -M_e[:, radius]^T x_e [E]."""
+    dof = g.dof
+    H_exact, M = exact_hessian_and_mixed(g, theta_star)
+    if mode == "exact":
+        H = H_exact
+    else:
+        _, J = jacobian(g, theta_star)
+        H = J.T @ J
+    x = torch.linalg.solve(H, v.reshape(-1)).reshape(-1, dof)
+    pri, _ = _split(g)
+    xe = torch.cat([x[g.ei], torch.where(pri[:, None], torch.zeros_like(x[g.ei]),
+                                          x[g.ej.clamp(min=0)])], 1)
+    return -torch.einsum('ek,ek->e', M[:, :, dof + 1], xe)
 
 
 def dphi_objective(g: Graph, theta):
@@ -346,11 +399,14 @@ def fd_grads(g: Graph, loss_fn: Callable, theta_star, coords, h=1e-6):
         for sgn in (1.0, -1.0):
             eps = torch.zeros(E, dof, dtype=F64)
             logw = g.logw.clone()
+            lr = None if g.log_radius is None else g.log_radius.clone()
             if which == "meas":
                 eps[e, k] = sgn * h
+            elif which == "radius":
+                lr[e] = lr[e] + sgn * h
             else:
                 logw[e] = logw[e] + sgn * h
-            th = solve_to_convergence(g, theta_star, eps=eps, logw=logw)
+            th = solve_to_convergence(g, theta_star, eps=eps, logw=logw, log_radius=lr)
             vals.append(float(loss_fn(th)))
         out.append((vals[0] - vals[1]) / (2 * h))
     return out

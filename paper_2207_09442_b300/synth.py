@@ -51,6 +51,8 @@ class PoseGraphBatch:
     logw: np.ndarray               # float32 [E] learnable log-weight l_e (w_e = exp(l_e) d_e)
     theta_init: np.ndarray         # float64 [P, 12] or [P, 4]
     theta_gt: np.ndarray           # float64 [P, 12] or [P, 4]
+    log_radius: Optional[np.ndarray] = None  # float64 [E] log Welsch radius per cost (None: no
+                                             # robust loss)
 
     @property
     def batch(self) -> int:
@@ -72,7 +74,8 @@ class PoseGraphBatch:
             self.kind, np.array([0, p1 - p0], np.int64), np.array([0, e1 - e0], np.int64),
             self.edge_i[e0:e1].copy(), self.edge_j[e0:e1].copy(), self.meas[e0:e1].copy(),
             self.wdiag[e0:e1].copy(), self.logw[e0:e1].copy(), self.theta_init[p0:p1].copy(),
-            self.theta_gt[p0:p1].copy())
+            self.theta_gt[p0:p1].copy(),
+            None if self.log_radius is None else self.log_radius[e0:e1].copy())
 
     def subset(self, idx) -> "PoseGraphBatch":
         """A batch made of the listed problems, in the listed order."""
@@ -88,8 +91,9 @@ def concat_pose_graphs(parts) -> PoseGraphBatch:
         po[k + 1] = po[k] + (p.pose_offsets[-1] - p.pose_offsets[0])
         eo[k + 1] = eo[k] + (p.edge_offsets[-1] - p.edge_offsets[0])
     cat = lambda name: np.concatenate([getattr(p, name) for p in parts], axis=0)
+    lr = None if any(p.log_radius is None for p in parts) else cat("log_radius")
     return PoseGraphBatch(kind, po, eo, cat("edge_i"), cat("edge_j"), cat("meas"), cat("wdiag"),
-                          cat("logw"), cat("theta_init"), cat("theta_gt"))
+                          cat("logw"), cat("theta_init"), cat("theta_gt"), lr)
 
 
 # ----------------------------------------------------------------------------- rigid helpers
@@ -200,21 +204,34 @@ def pgo_se2(batch=16, n_poses=32, n_lc=8, config_id=1, first=0) -> PoseGraphBatc
 
 
 def pgo_se3(batch=256, n_poses=128, n_lc=None, config_id=2, log_weights=False,
-            n_poses_range: Optional[tuple] = None, first=0) -> PoseGraphBatch:
+            n_poses_range: Optional[tuple] = None, first=0, outlier_frac=0.0,
+            radius: Optional[float] = None) -> PoseGraphBatch:
     """SE(3) pose graphs; ``n_poses_range=(lo, hi)`` draws N_b ~ U{lo..hi} per problem;
-    problems ``first .. first+batch-1`` of the seeded sequence."""
+    problems ``first .. first+batch-1`` of the seeded sequence.  ``outlier_frac`` replaces that
+    fraction of the loop-closure measurements (drawn per closure) by random relative poses
+    (rotation vector N(0, 0.5^2 I), translation N(0, 2^2 I)); ``radius`` gives every cost a Welsch
+    robust loss of that radius (log_radius = log(radius))."""
     probs = []
     for b in range(first, first + batch):
         rng = _rng(config_id, b)
         n = int(rng.integers(n_poses_range[0], n_poses_range[1] + 1)) if n_poses_range else n_poses
         lc = (n // 4) if n_lc is None else n_lc
-        probs.append(_pose_graph_se3(rng, n, lc, 0.5, 0.05, 0.02, 0.005) + (rng,))
+        ei, ej, Z, init, gt = _pose_graph_se3(rng, n, lc, 0.5, 0.05, 0.02, 0.005)
+        if outlier_frac > 0.0:
+            for e in range(n - 1, n - 1 + lc):  # loop closures follow the n - 1 chain edges
+                if rng.uniform() < outlier_frac:
+                    R = Rotation.from_rotvec(rng.normal(0.0, 0.5, size=3)).as_matrix()
+                    Z[e] = _pack_se3(_se3_mat(R, rng.normal(0.0, 2.0, size=3)))
+        probs.append((ei, ej, Z, init, gt, rng))
     wfn = lambda r, E, d: r.uniform(0.5, 2.0, size=(E, d))
     if log_weights:
         lfn = lambda r, E: r.normal(0.0, 0.1, size=E).astype(np.float32)
     else:
         lfn = lambda r, E: np.zeros(E, np.float32)
-    return _assemble(SE3, probs, wfn, lfn)
+    out = _assemble(SE3, probs, wfn, lfn)
+    if radius is not None:
+        out.log_radius = np.full(len(out.edge_i), np.log(radius))
+    return out
 
 
 # ----------------------------------------------------------------------------- bundle adjustment

@@ -405,6 +405,73 @@ def test_dogleg_monotone_on_se3_graph():
     assert float((th - th_lm).abs().max()) < 1e-7
 
 
+# ----------------------------------------------------------------------------- robust (Welsch) costs
+def test_welsch_definition():
+    s = torch.tensor([0.0, 1e-6, 0.3, 1.0, 7.0, 50.0], dtype=F64)
+    for c in (0.2, 1.0, 3.0):
+        u = torch.tensor(math.log(c), dtype=F64)
+        rho = pgo.welsch(s, u).numpy()
+        assert abs(rho[0]) == 0.0
+        assert np.all(rho <= np.minimum(s.numpy(), c * c) + 1e-15)  # below s and below c^2
+        assert abs(float(pgo.welsch(torch.tensor(1e4, dtype=F64), u)) - c * c) < 1e-12
+        h = 1e-6
+        fd = (pgo.welsch(s + h, u) - pgo.welsch(s - h, u)).numpy()[1:] / (2 * h)
+        assert np.allclose(pgo.welsch_d1(s, u).numpy()[1:], fd, rtol=1e-7, atol=1e-10)
+    big = torch.tensor(math.log(1e6), dtype=F64)
+    assert np.allclose(pgo.welsch(s, big).numpy(), s.numpy(), rtol=1e-9, atol=0)
+
+
+def test_robust_tiny_se2_graph_against_scipy_minimize():
+    """A tiny SE(2) graph with one grossly wrong loop closure and Welsch costs: the oracle's
+    IRLS Gauss-Newton reaches the same stationary point as SciPy's BFGS on the robust objective
+    written independently in (x, y, psi) coordinates."""
+    b = synth.pgo_se2(batch=1, n_poses=5, n_lc=2, config_id=110)
+    b.meas[-2] = np.array([3.0, -2.0, math.cos(1.0), math.sin(1.0)])  # an outlier loop closure
+    g = pgo.graph_from_batch(b, 0)
+    c = 0.3
+    g.log_radius = torch.full((len(b.edge_i),), math.log(c), dtype=F64)
+    th, _ = pgo.solve(g, algo="lm", iters=40, tau=0.0)
+    th = pgo.solve_to_convergence(g, th, max_iters=300)
+    Zm = [_np_se2(z[0], z[1], math.atan2(z[3], z[2])) for z in b.meas]
+
+    def obj(q):
+        q = q.reshape(-1, 3)
+        tot = 0.0
+        for e in range(len(b.edge_i)):
+            i, j = b.edge_i[e], b.edge_j[e]
+            Ti = _np_se2(*q[i])
+            E = np.linalg.inv(Zm[e]) @ (Ti if j < 0 else np.linalg.inv(Ti) @ _np_se2(*q[j]))
+            sq = float(((b.wdiag[e] * _np_se2_log(E)) ** 2).sum())
+            tot += 0.5 * c * c * (1.0 - math.exp(-sq / (c * c)))
+        return tot
+    q0 = np.stack([[p[0], p[1], math.atan2(p[3], p[2])] for p in th.numpy()]).reshape(-1)
+    q0 = q0 + np.random.default_rng(0).normal(0.0, 1e-3, size=q0.shape)
+    sol = so.minimize(obj, q0, method="BFGS", options={"gtol": 1e-12, "maxiter": 10000})
+    assert abs(sol.fun - float(pgo.objective(g, th))) < 1e-12
+    q = sol.x.reshape(-1, 3)
+    for k in range(len(q)):
+        assert abs(q[k, 0] - float(th[k, 0])) < 1e-5 and abs(q[k, 1] - float(th[k, 1])) < 1e-5
+
+
+def test_robust_implicit_gradients_match_fd():
+    """Implicit gradients (Eq. 3) with Welsch costs w.r.t. a log radius, a log-weight and a
+    measurement, against central differences with re-solve."""
+    b = synth.pgo_se3(batch=1, n_poses=12, n_lc=6, config_id=98, outlier_frac=0.3, radius=0.03)
+    g = pgo.graph_from_batch(b, 0)
+    th, _ = pgo.solve(g, algo="lm", iters=30, tau=0.0)
+    th = pgo.solve_to_convergence(g, th)
+    loss = lambda X: pgo.pose_error_loss(3, X, g.theta_gt)
+    v = pgo.tangent_grad(3, loss, th)
+    gr = pgo.implicit_grad_log_radius(g, th, v)
+    ge, gl, _ = pgo.implicit_grads(g, th, v)
+    er = int(gr.abs().argmax())
+    el = int(gl.abs().argmax())
+    em, km = divmod(int(ge.abs().argmax()), 6)
+    fd = pgo.fd_grads(g, loss, th, [("radius", er, 0), ("logw", el, 0), ("meas", em, km)])
+    for ref, f in zip([float(gr[er]), float(gl[el]), float(ge[em, km])], fd):
+        assert abs(f - ref) < 1e-6 * abs(ref), (f, ref)
+
+
 # ----------------------------------------------------------------------------- direct loss minimization
 def test_dlm_direct_step_is_the_argmin_of_the_augmented_linear_problem():
     """On a linear least-squares problem one GN step is exact, so theta_direct must be the
