@@ -36,7 +36,7 @@ WORKLOAD = "pgo_se3_b256"
 # problems per GPU of each named workload (algorithm, iterations, precision and lambda0 come
 # from the workload table of the synthetic-data module)
 PER_GPU = {"pgo_se2_b16": 16, "pgo_se3_b256": 256, "pgo_se3_implicit_b256": 256,
-           "pgo_se3_uneven_b1024": 1024, "ba_b32": 32}
+           "pgo_se3_uneven_b1024": 1024, "pgo_se3_robust_b256": 256, "ba_b32": 32}
 METRIC = "batched LM iters/s (fwd + implicit bwd) vs plain FP64 GPU path at 1e-5"
 # DRAM bytes (read + write) per launch of the dominant kernel, from an ncu capture of the forward
 # kernel's sources as they hash here (profiles/k_forward_pgo_se3_b64_full.md: 64-problem case,
@@ -337,6 +337,7 @@ def run_pose_graphs(args, rank, world, local, dist, out):
     theta0 = t64(batch.theta_init)
     meas, wd = t64(batch.meas), t64(batch.wdiag)
     lw = torch.as_tensor(batch.logw, dtype=torch.float32, device=dev)
+    lr = None if batch.log_radius is None else t64(batch.log_radius)  # Welsch log radii
     rng = np.random.default_rng(1234)
     v = t64(rng.normal(size=(st.n_poses, dof)) * 1e-2)  # synthetic outer-loss tangent gradient
     if args.shape:
@@ -351,11 +352,13 @@ def run_pose_graphs(args, rank, world, local, dist, out):
     gl = torch.empty(st.n_costs, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream()
 
+    gr = None if lr is None else torch.empty(st.n_costs, dtype=torch.float64, device=dev)
+
     def step(mid):
         theta.copy_(theta0)
-        solver.forward(theta, meas, wd, lw, out=theta)
+        solver.forward(theta, meas, wd, lw, out=theta, log_radius=lr)
         mid.record(stream)
-        solver.backward(theta, v, meas, wd, lw, gm, gl)
+        solver.backward(theta, v, meas, wd, lw, gm, gl, log_radius=lr, grad_log_radius=gr)
 
     step(torch.cuda.Event(enable_timing=True))
     torch.cuda.synchronize()
@@ -420,13 +423,17 @@ def run_pose_graphs(args, rank, world, local, dist, out):
         p0, p1 = int(batch.pose_offsets[b_]), int(batch.pose_offsets[b_ + 1])
         e0, e1 = int(batch.edge_offsets[b_]), int(batch.edge_offsets[b_ + 1])
         g_ = pgo.graph_from_batch(batch, b_)
+        om = "gn" if bmode == "implicit_gn" else "exact"
         if bmode == "dlm":
             rm, rl, _ = pgo.dlm_grads(g_, th_cpu[p0:p1], v_cpu[p0:p1], opts.dlm_eps)
         else:
-            rm, rl, _ = pgo.implicit_grads(g_, th_cpu[p0:p1], v_cpu[p0:p1],
-                                           "gn" if bmode == "implicit_gn" else "exact")
-        gerrs.append(max(float((gm_cpu[e0:e1] - rm).norm() / rm.norm()),
-                         float((gl_cpu[e0:e1] - rl).norm() / rl.norm())))
+            rm, rl, _ = pgo.implicit_grads(g_, th_cpu[p0:p1], v_cpu[p0:p1], om)
+        errs_b = [float((gm_cpu[e0:e1] - rm).norm() / rm.norm()),
+                  float((gl_cpu[e0:e1] - rl).norm() / rl.norm())]
+        if gr is not None:
+            rr = pgo.implicit_grad_log_radius(g_, th_cpu[p0:p1], v_cpu[p0:p1], om)
+            errs_b.append(float((gr.cpu()[e0:e1] - rr).norm() / rr.norm()))
+        gerrs.append(max(errs_b))
     out["accuracy"] = {"max_rel_err_vs_oracle": max(errs), "sampled_problems": sample,
                        "tolerance": 1e-9 if precision == "fp64" else 1e-5,
                        "grad_max_rel_err_vs_oracle": max(gerrs), "grad_sampled_problems": sample[:2],
@@ -441,12 +448,13 @@ def run_pose_graphs(args, rank, world, local, dist, out):
                                                  lambda0=lam0, backward_mode=bmode), dev)
         a1 = [t64(one.theta_init), t64(one.meas), t64(one.wdiag),
               torch.as_tensor(one.logw, dtype=torch.float32, device=dev)]
+        lr1 = None if one.log_radius is None else t64(one.log_radius)
         v1 = t64(rng.normal(size=(int(one.pose_offsets[-1]), dof)) * 1e-2)
-        s1.backward(s1.forward(*a1), v1, *a1[1:])
+        s1.backward(s1.forward(*a1, log_radius=lr1), v1, *a1[1:], log_radius=lr1)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        s1.backward(s1.forward(*a1), v1, *a1[1:])
+        s1.backward(s1.forward(*a1, log_radius=lr1), v1, *a1[1:], log_radius=lr1)
         e1.record(stream)
         torch.cuda.synchronize()
         per.append(e0.elapsed_time(e1))
@@ -457,13 +465,18 @@ def run_pose_graphs(args, rank, world, local, dist, out):
     # end to end through the public API with host (pinned) buffers
     h_in = [torch.as_tensor(np.ascontiguousarray(a)).pin_memory() for a in
             (batch.theta_init, batch.meas, batch.wdiag, batch.logw)] + [v.cpu().pin_memory()]
+    if lr is not None:
+        h_in.append(lr.cpu().pin_memory())
     d_in = [torch.empty_like(x, device=dev) for x in h_in]
-    h_out = [torch.empty(x.shape, dtype=x.dtype).pin_memory() for x in (theta, gm, gl)]
+    outs = (theta, gm, gl) if lr is None else (theta, gm, gl, gr)
+    h_out = [torch.empty(x.shape, dtype=x.dtype).pin_memory() for x in outs]
 
     def run():
-        solver.forward(d_in[0], d_in[1], d_in[2], d_in[3], out=d_in[0])
-        solver.backward(d_in[0], d_in[4], d_in[1], d_in[2], d_in[3], gm, gl)
-        return d_in[0], gm, gl
+        dlr = d_in[5] if lr is not None else None
+        solver.forward(d_in[0], d_in[1], d_in[2], d_in[3], out=d_in[0], log_radius=dlr)
+        solver.backward(d_in[0], d_in[4], d_in[1], d_in[2], d_in[3], gm, gl, log_radius=dlr,
+                        grad_log_radius=gr)
+        return (d_in[0], gm, gl) if lr is None else (d_in[0], gm, gl, gr)
 
     out["e2e"] = _e2e(run, h_in, h_out, d_in, args.steps, stream, executed)
     # CPU baseline: the oracle as it stands on a bounded sample (2 problems, fwd + bwd)

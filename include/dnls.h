@@ -51,7 +51,7 @@ typedef enum {
 /* per-problem status written to dnls_info.status */
 enum {
   DNLS_PROBLEM_OK = 0,
-  DNLS_PROBLEM_NOT_CONVERGED = 1, /* backward: refinement did not reach refine_tol */
+  DNLS_PROBLEM_NOT_CONVERGED = 1, /* backward: the adjoint solve did not reach refine_tol */
   DNLS_PROBLEM_NOT_SPD = 2,       /* a Cholesky pivot was not positive (GN stops; LM raises lambda) */
   DNLS_PROBLEM_NAN = 3            /* a non-finite objective was met */
 };
@@ -84,7 +84,7 @@ typedef struct {
                               relative poses, g, the factorization and the acceptance in FP64) */
   int32_t backward_mode;   /* DNLS_IMPLICIT_EXACT (true Hessian of S), DNLS_IMPLICIT_GN or
                               DNLS_BACKWARD_DLM */
-  int32_t refine_max;      /* max refinement steps of the adjoint solve (>= 1) */
+  int32_t refine_max;      /* max (preconditioned CG) steps of the adjoint solve (>= 1) */
   int32_t threads;         /* threads per CTA: 0 = library choice, else 128 or 256 */
   int32_t ctas_per_sm;     /* resident CTAs per SM of the persistent launch: 0 = library choice */
   int32_t smem_factor;     /* 1: keep a problem's Cholesky factor in shared memory when it fits */
@@ -104,7 +104,7 @@ typedef struct {
   int32_t iterations;   /* iterations run (<= iters; fewer if the problem froze) */
   int32_t accepted;     /* accepted steps */
   int32_t status;       /* DNLS_PROBLEM_* (forward); backward overwrites on failure */
-  int32_t refine_steps; /* backward: refinement steps taken */
+  int32_t refine_steps; /* backward: adjoint-solve steps taken */
   int32_t factorizations; /* forward: numeric Cholesky factorizations run (GN/LM: one per
                              iteration; dogleg: one per linearization) */
   int32_t reserved;     /* zero */
@@ -131,6 +131,12 @@ typedef struct {
   const double* meas;   /* device [E, 12] (SE3) or [E, 4] (SE2): measurements Z_e */
   const double* wdiag;  /* device [E, dof]: fixed square-root-information diagonal d_e */
   const float* logw;    /* device [E] learnable log-weights l_e, or NULL (all zero) */
+  const double* log_radius; /* device [E] log radii u_e of a Welsch robust loss on every cost,
+                               or NULL (plain squares).  With them S = 1/2 sum rho_e(||r_e||^2),
+                               rho(s) = c^2 (1 - exp(-s/c^2)), c = exp(u_e) (Sec. 3 robust
+                               losses; Sec. 3.1 learns this radius for PGO).  GN/LM/dogleg use
+                               IRLS: r and J scaled by sqrt(rho'(s)); the implicit backward's
+                               exact Hessian keeps rho''. */
 } dnls_graph_inputs;
 
 /* Build the handle: validates indices, computes a fill-reducing block ordering, the symbolic
@@ -156,10 +162,11 @@ dnls_status dnls_graph_forward(const dnls_graph* g, const dnls_solver_opts* opts
 
 /* Implicit backward (Eq. 3 / Prop. 1, App. G.3) at theta* from the preceding forward on the
  * same workspace.  Solves H x = v with H the true Hessian of S (DNLS_IMPLICIT_EXACT) or the
- * Gauss-Newton matrix (DNLS_IMPLICIT_GN) by refinement preconditioned with the forward's cached
+ * Gauss-Newton matrix (DNLS_IMPLICIT_GN) by conjugate gradients preconditioned with the forward's cached
  * factor (Sec. 4.2 "backward for custom linear solvers"), then writes
  *   grad_meas[e] = -(D_{eps_e} g)^T x   (tangent of Z_e (+) eps = Z_e Exp(eps)), device [E, dof]
  *   grad_logw[e] = -(D_{l_e} g)^T x,                                              device [E]
+ *   grad_log_radius[e] = -(D_{u_e} g)^T x  (only with in->log_radius),            device [E]
  * v: device [P, dof] tangent gradient dL/dxi of the outer loss at theta*.
  * Either output may be NULL.  info (device [B], may be NULL) receives refine_resid,
  * refine_steps and DNLS_PROBLEM_NOT_CONVERGED where the tolerance was not reached. */
@@ -172,12 +179,13 @@ dnls_status dnls_graph_forward(const dnls_graph* g, const dnls_solver_opts* opts
  *   grad_logw[e] = (dS/d l_e (theta*)   - dS/d l_e (theta_direct))   / eps
  * with eps = opts->dlm_eps.  It needs no cached factor (the workspace's factor is overwritten
  * and marked stale, so a later implicit backward refactors); refine_* are unused and info gets
- * refine_steps = 1.  A non-SPD shifted matrix gives zero gradients and DNLS_PROBLEM_NOT_SPD. */
+ * refine_steps = 1.  A non-SPD shifted matrix gives zero gradients and DNLS_PROBLEM_NOT_SPD.
+ * DLM with robust costs (in->log_radius != NULL) is not implemented: DNLS_ERR_UNSUPPORTED. */
 dnls_status dnls_graph_backward(const dnls_graph* g, const dnls_solver_opts* opts,
                                 const dnls_graph_inputs* in, const double* theta_star,
                                 const double* v, double* grad_meas, double* grad_logw,
-                                void* workspace, size_t workspace_bytes, void* stream,
-                                dnls_info* info);
+                                double* grad_log_radius, void* workspace, size_t workspace_bytes,
+                                void* stream, dnls_info* info);
 
 /* Forward without any device allocation, for callers that are not allowed to allocate device
  * memory when they solve: for example a host application whose memory manager has reserved the

@@ -46,10 +46,12 @@ struct KArgs {
   const double* meas;
   const double* wdiag;
   const float* logw;
+  const double* log_radius;  // per-cost log Welsch radius, or null
   double* theta;        // forward: in/out poses; backward/linearize: theta (read)
   const double* v;      // backward: tangent gradient [P, dof]
   double* grad_meas;    // backward outputs
   double* grad_logw;
+  double* grad_log_radius;
   double* H_dense;      // linearize outputs
   double* grad;
   double* S_out;
@@ -70,6 +72,7 @@ struct Prob {
   const int32_t *ei, *ej;
   const double *meas, *wdiag;
   const float* logw;
+  const double* logrc;  // per-cost log Welsch radius (null: plain squares)
   double* theta;
   double *H, *L, *Lg, *Linv, *g, *dx, *tmp, *thc, *bx, *bv, *br, *bhx, *ebuf, *W;
   void* J;
@@ -96,6 +99,7 @@ struct Prob {
     meas = a.meas + m->edge_off * PW;
     wdiag = a.wdiag + m->edge_off * D;
     logw = a.logw ? a.logw + m->edge_off : nullptr;
+    logrc = a.log_radius ? a.log_radius + m->edge_off : nullptr;
     theta = a.theta + m->pose_off * PW;
     char* w = a.ws + m->ws;
     H = (double*)(w + m->w_H);
@@ -241,7 +245,23 @@ __device__ void lin_costs(Prob<KIND>& p, const double* poses) {
       for (int k = 0; k < PW; ++k) Ep[k] = (P)Em[k];
       prior_lin<KIND, P>(Ep, wp, out, out + D);
     }
+    if (p.logrc) {  // IRLS: r, J scaled by sqrt(rho'(s)), rho'(s) = exp(-s / c^2)
+      P s2 = P(0);
+#pragma unroll
+      for (int a = 0; a < D; ++a) s2 += out[a] * out[a];
+      const P sw = (P)sqrt(exp(-(double)s2 * exp(-2.0 * p.logrc[e])));
+      const int nw = D + (j >= 0 ? 2 : 1) * BS;
+      for (int k = 0; k < nw; ++k) out[k] *= sw;
+    }
   }
+}
+
+// 1/2 rho(s) of one cost: s/2, or c^2 (1 - exp(-s/c^2)) / 2 for a Welsch cost
+template <int KIND>
+__device__ __forceinline__ double half_rho(const Prob<KIND>& p, int e, double s) {
+  if (!p.logrc) return 0.5 * s;
+  const double c2 = exp(2.0 * p.logrc[e]);
+  return -0.5 * c2 * expm1(-s / c2);
 }
 
 // S = 1/2 sum ||w c||^2 in FP64 (the acceptance test always runs in FP64).
@@ -264,11 +284,13 @@ __device__ double eval_S(Prob<KIND>& p, const double* poses, double* red) {
       G::invmul(Z, Ti, Em);
     }
     G::log(Em, c);
+    double s = 0.0;
 #pragma unroll
     for (int a = 0; a < D; ++a) {
       const double r = w[a] * c[a];
-      acc += 0.5 * r * r;
+      s += r * r;
     }
+    acc += half_rho<KIND>(p, e, s);
   }
   return block_sum(acc, red);
 }
@@ -630,6 +652,15 @@ __global__ void __launch_bounds__(256) k_forward_dogleg(KArgs a) {
 }
 
 // ----------------------------------------------------------------------------- backward
+// rho'(s) = exp(-s / c^2) of a Welsch cost at s = ||r||^2, as a dual number
+template <int D>
+__device__ __forceinline__ Dual<double> welsch_d1(const Dual<double>* r, double log_c) {
+  Dual<double> s = r[0] * r[0];
+#pragma unroll
+  for (int k = 1; k < D; ++k) s = s + r[k] * r[k];
+  return m_exp(s * Dual<double>(-exp(-2.0 * log_c)));
+}
+
 // Exact-Hessian product at theta* for one problem: per cost, forward-mode (dual number in t)
 // evaluation of the local gradient at (T_i Exp(t x_i), T_j Exp(t x_j)), gathered per pose;
 // the chart term -1/2 ad(x_k)^T g_k turns the point-wise derivative into the derivative in the
@@ -660,6 +691,14 @@ __device__ void hvp_exact(Prob<KIND>& p, const double* x, double* hx) {
       between_lin<KIND, Dd>(Ai, Em, wd, r, Ji, Jj);
       jt_r<D>(Ji, r, gi);
       jt_r<D>(Jj, r, gj);
+      if (p.logrc) {  // local gradient of 1/2 rho(||r||^2): rho'(s) J^T r
+        const Dd w1 = welsch_d1<D>(r, p.logrc[e]);
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          gi[k] = gi[k] * w1;
+          gj[k] = gj[k] * w1;
+        }
+      }
 #pragma unroll
       for (int k = 0; k < D; ++k) {
         eb[2 * D + k] = gj[k].v;
@@ -670,6 +709,11 @@ __device__ void hvp_exact(Prob<KIND>& p, const double* x, double* hx) {
       G::invmul(Zd, Ti, Em);
       prior_lin<KIND, Dd>(Em, wd, r, Ji);
       jt_r<D>(Ji, r, gi);
+      if (p.logrc) {
+        const Dd w1 = welsch_d1<D>(r, p.logrc[e]);
+#pragma unroll
+        for (int k = 0; k < D; ++k) gi[k] = gi[k] * w1;
+      }
     }
 #pragma unroll
     for (int k = 0; k < D; ++k) {
@@ -852,40 +896,63 @@ __device__ void backward_problem(const KArgs& a, int b, char* smem, double* red,
     __syncthreads();
     if (!factor<KIND>(p, 0.0, sflag, 0)) status = DNLS_PROBLEM_NOT_SPD;
   }
+  // Preconditioned conjugate gradients on H x = v (H the true Hessian, or the GN matrix, SPD
+  // at a strict minimum), preconditioner M^-1 = the cached factor's solve: one Hessian product
+  // and one triangular solve pair per step.  Vectors: x in bx, residual r in br, direction p in
+  // bv, H p in bhx, z = M^-1 r in dx.
   double vn2 = 0.0;
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
     const int pos = k / D, c = k % D;
     const double vv = a.v[(p.m->pose_off + p.perm[pos]) * D + c];
-    p.bv[k] = vv;
     p.br[k] = vv;
     p.bx[k] = 0.0;
+    p.dx[k] = vv;
     vn2 += vv * vv;
   }
   const double vnorm = sqrt(block_sum(vn2, red));
   double rel = 0.0;
   int steps = 0;
   if (status == DNLS_PROBLEM_OK && vnorm > 0.0) {
+    chol_solve<KIND>(p, p.dx);  // z0
+    double rz = 0.0;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+      p.bv[k] = p.dx[k];
+      rz = fma(p.br[k], p.dx[k], rz);
+    }
+    rz = block_sum(rz, red);
+    rel = 1.0;
     for (int it = 0; it < a.refine_max; ++it) {
       steps = it + 1;
-      for (int k = threadIdx.x; k < n; k += blockDim.x) p.dx[k] = p.br[k];
-      __syncthreads();
-      chol_solve<KIND>(p, p.dx);
-      for (int k = threadIdx.x; k < n; k += blockDim.x) p.bx[k] += p.dx[k];
-      __syncthreads();
       if (need_J)
-        hvp_gn<KIND>(p, p.bx, p.bhx);
+        hvp_gn<KIND>(p, p.bv, p.bhx);
       else
-        hvp_exact<KIND>(p, p.bx, p.bhx);
+        hvp_exact<KIND>(p, p.bv, p.bhx);
+      double pq = 0.0;
+      for (int k = threadIdx.x; k < n; k += blockDim.x) pq = fma(p.bv[k], p.bhx[k], pq);
+      pq = block_sum(pq, red);
+      if (!(pq > 0.0)) break;  // not positive definite along p: stop, reported below
+      const double alpha = rz / pq;
       double r2 = 0.0;
       for (int k = threadIdx.x; k < n; k += blockDim.x) {
-        const double rr = p.bv[k] - p.bhx[k];
+        p.bx[k] = fma(alpha, p.bv[k], p.bx[k]);
+        const double rr = fma(-alpha, p.bhx[k], p.br[k]);
         p.br[k] = rr;
-        r2 += rr * rr;
+        p.dx[k] = rr;
+        r2 = fma(rr, rr, r2);
       }
       rel = sqrt(block_sum(r2, red)) / vnorm;
       if (!(rel > a.refine_tol)) break;
+      chol_solve<KIND>(p, p.dx);
+      double rz1 = 0.0;
+      for (int k = threadIdx.x; k < n; k += blockDim.x) rz1 = fma(p.br[k], p.dx[k], rz1);
+      rz1 = block_sum(rz1, red);
+      const double beta = rz1 / rz;
+      rz = rz1;
+      for (int k = threadIdx.x; k < n; k += blockDim.x) p.bv[k] = fma(beta, p.bv[k], p.dx[k]);
+      __syncthreads();
     }
     if (!(rel <= a.refine_tol)) status = DNLS_PROBLEM_NOT_CONVERGED;
+    // the local gradients in ebuf (used by the VJPs below) are independent of the direction
   } else if (status == DNLS_PROBLEM_OK) {
     // v = 0: x = 0, but the local gradients are still needed below
     if (need_J)
@@ -899,12 +966,49 @@ __device__ void backward_problem(const KArgs& a, int b, char* smem, double* red,
     const int i = p.ei[e], j = p.ej[e];
     if (status == DNLS_PROBLEM_NOT_SPD) {
       if (a.grad_logw) a.grad_logw[ge] = 0.0;
+      if (a.grad_log_radius) a.grad_log_radius[ge] = 0.0;
       if (a.grad_meas)
         for (int k = 0; k < D; ++k) a.grad_meas[ge * D + k] = 0.0;
       continue;
     }
     const double* xi = p.bx + p.iperm[i] * D;
     const double* eb = p.ebuf + (int64_t)e * 4 * D;
+    if (p.logrc) {
+      // robust cost: every parameter's VJP is -(D_phi g)^T x = -d/dt dS_e/dphi (theta (+) t x),
+      // with s = ||r||^2 and E = rho'(s) = exp(-s/c^2) as dual numbers in t:
+      //   dS/d eps = -E J_l^-1(c)^T w^2 c,  dS/dl = E s,  dS/du = c^2 (1 - E) - s E
+      double w[D];
+      p.weight(e, w);
+      Dd wd[D], Ti[PW], Zd[PW], Em[PW], c[D];
+#pragma unroll
+      for (int k = 0; k < D; ++k) wd[k] = Dd(w[k]);
+#pragma unroll
+      for (int k = 0; k < PW; ++k) Zd[k] = Dd(p.meas[(int64_t)e * PW + k]);
+      pose_dual<KIND>(p.theta + (int64_t)i * PW, xi, Ti);
+      if (j >= 0) {
+        Dd Tj[PW], A[PW];
+        pose_dual<KIND>(p.theta + (int64_t)j * PW, p.bx + p.iperm[j] * D, Tj);
+        G::invmul(Ti, Tj, A);
+        G::invmul(Zd, A, Em);
+      } else {
+        G::invmul(Zd, Ti, Em);
+      }
+      G::log(Em, c);
+      Dd sq = Dd(0.0);
+#pragma unroll
+      for (int k = 0; k < D; ++k) sq = sq + (wd[k] * c[k]) * (wd[k] * c[k]);
+      const double c2 = exp(2.0 * p.logrc[e]);
+      const Dd Ew = m_exp(sq * Dd(-1.0 / c2));
+      if (a.grad_logw) a.grad_logw[ge] = -(Ew * sq).d;
+      if (a.grad_log_radius) a.grad_log_radius[ge] = -(Dd(c2) * (Dd(1.0) - Ew) - sq * Ew).d;
+      if (a.grad_meas) {
+        Dd o[D];
+        meas_grad_neg<KIND, Dd>(Em, wd, o);
+#pragma unroll
+        for (int k = 0; k < D; ++k) a.grad_meas[ge * D + k] = (Ew * o[k]).d;
+      }
+      continue;
+    }
     if (a.grad_logw) {
       double s = 0.0;
 #pragma unroll
@@ -1079,6 +1183,7 @@ KArgs base_args(const dnls_graph* g, const dnls_graph_inputs* in, void* ws) {
   a.meas = in->meas;
   a.wdiag = in->wdiag;
   a.logw = in->logw;
+  a.log_radius = in->log_radius;
   a.ws = (char*)ws;
   a.counter = (int*)ws;
   return a;
@@ -1195,11 +1300,12 @@ dnls_status dnls_graph_forward(const dnls_graph* g, const dnls_solver_opts* opts
 dnls_status dnls_graph_backward(const dnls_graph* g, const dnls_solver_opts* opts,
                                 const dnls_graph_inputs* in, const double* theta_star,
                                 const double* v, double* grad_meas, double* grad_logw,
-                                void* workspace, size_t workspace_bytes, void* stream,
-                                dnls_info* info) {
+                                double* grad_log_radius, void* workspace, size_t workspace_bytes,
+                                void* stream, dnls_info* info) {
   if (!g || !in || !theta_star || !v || !in->meas || !in->wdiag) return DNLS_ERR_ARG;
   dnls_status s = check_opts(opts);
   if (s != DNLS_OK) return s;
+  if (opts->backward_mode == DNLS_BACKWARD_DLM && in->log_radius) return DNLS_ERR_UNSUPPORTED;
   if (opts->refine_max < 1 || !(opts->refine_tol >= 0.0)) return DNLS_ERR_ARG;
   if ((s = check_ws(g, workspace, workspace_bytes)) != DNLS_OK) return s;
   KArgs a = base_args(g, in, workspace);
@@ -1207,6 +1313,7 @@ dnls_status dnls_graph_backward(const dnls_graph* g, const dnls_solver_opts* opt
   a.v = v;
   a.grad_meas = grad_meas;
   a.grad_logw = grad_logw;
+  a.grad_log_radius = in->log_radius ? grad_log_radius : nullptr;
   a.info = info;
   a.mode = opts->backward_mode;
   a.refine_max = opts->refine_max;

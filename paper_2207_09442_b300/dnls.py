@@ -40,7 +40,7 @@ class GraphDesc(ctypes.Structure):
 
 
 class GraphInputs(ctypes.Structure):
-    _fields_ = [("meas", c_void_p), ("wdiag", c_void_p), ("logw", c_void_p)]
+    _fields_ = [("meas", c_void_p), ("wdiag", c_void_p), ("logw", c_void_p), ("log_radius", c_void_p)]
 
 
 class GraphStats(ctypes.Structure):
@@ -78,8 +78,8 @@ _SIGS = {
     "dnls_graph_forward": (c_int32, [c_void_p, ctypes.POINTER(SolverOpts), ctypes.POINTER(GraphInputs),
                                      c_void_p, c_void_p, c_size_t, c_void_p, c_void_p]),
     "dnls_graph_backward": (c_int32, [c_void_p, ctypes.POINTER(SolverOpts), ctypes.POINTER(GraphInputs),
-                                      c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t,
-                                      c_void_p, c_void_p]),
+                                      c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                      c_size_t, c_void_p, c_void_p]),
     "dnls_graph_linearize": (c_int32, [c_void_p, ctypes.POINTER(SolverOpts), ctypes.POINTER(GraphInputs),
                                        c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t,
                                        c_void_p]),

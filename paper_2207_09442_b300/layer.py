@@ -143,55 +143,68 @@ class PoseGraphSolver:
         self.workspace = torch.empty(int(nbytes.value), dtype=torch.uint8, device=self.device)
         self.info = torch.zeros(structure.batch * _d.INFO_BYTES, dtype=torch.uint8, device=self.device)
 
-    def _inputs(self, meas, wdiag, logw):
-        return _d.GraphInputs(_d.ptr(meas), _d.ptr(wdiag), _d.ptr(logw))
+    def _inputs(self, meas, wdiag, logw, log_radius=None):
+        return _d.GraphInputs(_d.ptr(meas), _d.ptr(wdiag), _d.ptr(logw), _d.ptr(log_radius))
 
-    def _check_inputs(self, meas, wdiag, logw):
+    def _check_inputs(self, meas, wdiag, logw, log_radius=None):
         s = self.s
         assert meas.dtype == torch.float64 and meas.is_contiguous() and meas.shape == (s.n_costs, s.pw)
         assert wdiag.dtype == torch.float64 and wdiag.is_contiguous() and wdiag.shape == (s.n_costs, s.dof)
         if logw is not None:
             assert logw.dtype == torch.float32 and logw.is_contiguous() and logw.shape == (s.n_costs,)
+        if log_radius is not None:
+            assert (log_radius.dtype == torch.float64 and log_radius.is_contiguous()
+                    and log_radius.shape == (s.n_costs,))
 
-    def forward(self, theta0: torch.Tensor, meas, wdiag, logw=None, out: torch.Tensor = None):
-        """Returns the optimised poses (a new tensor unless ``out`` is given)."""
-        self._check_inputs(meas, wdiag, logw)
+    def forward(self, theta0: torch.Tensor, meas, wdiag, logw=None, out: torch.Tensor = None,
+                log_radius=None):
+        """Returns the optimised poses (a new tensor unless ``out`` is given).  ``log_radius``
+        [E] FP64 gives every cost a Welsch robust loss of radius exp(log_radius)."""
+        self._check_inputs(meas, wdiag, logw, log_radius)
         assert theta0.dtype == torch.float64 and theta0.shape == (self.s.n_poses, self.s.pw)
         theta = out if out is not None else torch.empty_like(theta0)
         if theta.data_ptr() != theta0.data_ptr():
             theta.copy_(theta0)
-        inp = self._inputs(meas, wdiag, logw)
+        inp = self._inputs(meas, wdiag, logw, log_radius)
         _d.check(_d.lib().dnls_graph_forward(
             self.s.handle, ctypes.byref(self._copts), ctypes.byref(inp), theta.data_ptr(),
             self.workspace.data_ptr(), self.workspace.numel(), _stream(), self.info.data_ptr()),
             "dnls_graph_forward")
         return theta
 
-    def backward(self, theta_star, v, meas, wdiag, logw=None, grad_meas=None, grad_logw=None):
-        """Implicit gradients (tangent grad_meas [E, dof], grad_logw [E], FP64) for the tangent
-        outer-loss gradient v [P, dof] at theta*."""
-        self._check_inputs(meas, wdiag, logw)
+    def backward(self, theta_star, v, meas, wdiag, logw=None, grad_meas=None, grad_logw=None,
+                 log_radius=None, grad_log_radius=None):
+        """Implicit (or DLM) gradients (tangent grad_meas [E, dof], grad_logw [E], FP64) for the
+        tangent outer-loss gradient v [P, dof] at theta*; with robust costs (``log_radius``) also
+        the gradient w.r.t. the log radii [E], returned third."""
+        self._check_inputs(meas, wdiag, logw, log_radius)
         s = self.s
         if grad_meas is None:
             grad_meas = torch.empty(s.n_costs, s.dof, dtype=torch.float64, device=self.device)
         if grad_logw is None:
             grad_logw = torch.empty(s.n_costs, dtype=torch.float64, device=self.device)
-        inp = self._inputs(meas, wdiag, logw)
+        if log_radius is not None and grad_log_radius is None:
+            grad_log_radius = torch.empty(s.n_costs, dtype=torch.float64, device=self.device)
+        inp = self._inputs(meas, wdiag, logw, log_radius)
         _d.check(_d.lib().dnls_graph_backward(
             s.handle, ctypes.byref(self._copts), ctypes.byref(inp), theta_star.data_ptr(),
-            v.data_ptr(), grad_meas.data_ptr(), grad_logw.data_ptr(), self.workspace.data_ptr(),
-            self.workspace.numel(), _stream(), self.info.data_ptr()), "dnls_graph_backward")
+            v.data_ptr(), grad_meas.data_ptr(), grad_logw.data_ptr(), _d.ptr(grad_log_radius),
+            self.workspace.data_ptr(), self.workspace.numel(), _stream(), self.info.data_ptr()),
+            "dnls_graph_backward")
+        if log_radius is not None:
+            return grad_meas, grad_logw, grad_log_radius
         return grad_meas, grad_logw
 
-    def linearize(self, theta, meas, wdiag, logw=None):
-        """Dense H per problem (list), g [P*dof] and S [B] at theta (for inspection/tests)."""
-        self._check_inputs(meas, wdiag, logw)
+    def linearize(self, theta, meas, wdiag, logw=None, log_radius=None):
+        """Dense H per problem (list), g [P*dof] and S [B] at theta (for inspection/tests); with
+        robust costs H and g are the IRLS ones."""
+        self._check_inputs(meas, wdiag, logw, log_radius)
         s = self.s
         sizes = [(int(s.pose_offsets[b + 1] - s.pose_offsets[b]) * s.dof) for b in range(s.batch)]
         Hd = torch.empty(sum(n * n for n in sizes), dtype=torch.float64, device=self.device)
         g = torch.empty(s.n_poses * s.dof, dtype=torch.float64, device=self.device)
         S = torch.empty(s.batch, dtype=torch.float64, device=self.device)
-        inp = self._inputs(meas, wdiag, logw)
+        inp = self._inputs(meas, wdiag, logw, log_radius)
         _d.check(_d.lib().dnls_graph_linearize(
             s.handle, ctypes.byref(self._copts), ctypes.byref(inp), theta.data_ptr(),
             Hd.data_ptr(), g.data_ptr(), S.data_ptr(), self.workspace.data_ptr(),
@@ -230,35 +243,40 @@ class _SolveFn(torch.autograd.Function):
     As in the paper (Table 2), the implicit mode gives no gradient to the initial poses."""
 
     @staticmethod
-    def forward(ctx, solver: PoseGraphSolver, theta0, meas, wdiag, logw):
+    def forward(ctx, solver: PoseGraphSolver, theta0, meas, wdiag, logw, log_radius=None):
         theta = solver.forward(theta0.detach(), meas.detach(), wdiag.detach(),
-                               None if logw is None else logw.detach())
+                               None if logw is None else logw.detach(),
+                               log_radius=None if log_radius is None else log_radius.detach())
         ctx.solver = solver
-        ctx.save_for_backward(theta, meas, wdiag, logw)
+        ctx.save_for_backward(theta, meas, wdiag, logw, log_radius)
         return theta
 
     @staticmethod
     def backward(ctx, g_theta):
-        theta, meas, wdiag, logw = ctx.saved_tensors
+        theta, meas, wdiag, logw, log_radius = ctx.saved_tensors
         solver = ctx.solver
         kind = solver.s.kind
         v = project_grad(kind, theta, g_theta)
-        gm_t, gl = solver.backward(theta, v, meas, wdiag, logw)
+        out = solver.backward(theta, v, meas, wdiag, logw, log_radius=log_radius)
+        gm_t, gl = out[0], out[1]
         g_meas = lift_grad(kind, meas, gm_t) if ctx.needs_input_grad[2] else None
         g_logw = gl.to(torch.float32) if (logw is not None and ctx.needs_input_grad[4]) else None
-        return None, None, g_meas, None, g_logw
+        g_rad = out[2] if (log_radius is not None and ctx.needs_input_grad[5]) else None
+        return None, None, g_meas, None, g_logw, g_rad
 
 
 class PoseGraphLayer:
     """TheseusLayer-style wrapper (Sec. 3): ``forward(input_tensors) -> (solution, info)`` with
-    input names "theta" (initial poses), "meas", "wdiag" and optionally "logw"."""
+    input names "theta" (initial poses), "meas", "wdiag" and optionally "logw" and "log_radius"
+    (per-cost log radius of a Welsch robust loss)."""
 
     def __init__(self, structure: PoseGraphStructure, opts: Options = None):
         self.solver = PoseGraphSolver(structure, opts)
 
     def forward(self, input_tensors: dict):
         theta = _SolveFn.apply(self.solver, input_tensors["theta"], input_tensors["meas"],
-                               input_tensors["wdiag"], input_tensors.get("logw"))
+                               input_tensors["wdiag"], input_tensors.get("logw"),
+                               input_tensors.get("log_radius"))
         return {"theta": theta}, self.solver.info
 
     __call__ = forward

@@ -336,7 +336,7 @@ def ba(batch=32, n_cams=64, n_pts=4096, k_range=(4, 8), config_id=5, focal=500.0
 
 # ----------------------------------------------------------------------------- named workloads
 def workload(name: str, batch: Optional[int] = None, **kw):
-    """The five named workloads; ``batch`` shrinks a workload to its first problems (same seeds);
+    """The named synthetic workloads; ``batch`` shrinks a workload to its first problems (same seeds);
     ``first=k`` starts at problem k of the seeded sequence."""
     if name == "pgo_se2_b16":
         return pgo_se2(batch=batch or 16, **kw)
@@ -346,6 +346,9 @@ def workload(name: str, batch: Optional[int] = None, **kw):
         return pgo_se3(batch=batch or 256, n_poses=64, n_lc=16, config_id=3, log_weights=True, **kw)
     if name == "pgo_se3_uneven_b1024":
         return pgo_se3(batch=batch or 1024, n_poses_range=(16, 256), config_id=4, **kw)
+    if name == "pgo_se3_robust_b256":
+        return pgo_se3(batch=batch or 256, n_poses=64, n_lc=16, config_id=6, outlier_frac=0.2,
+                       radius=0.03, **kw)
     if name == "ba_b32":
         return ba(batch=batch or 32, **kw)
     raise KeyError(name)
@@ -357,6 +360,7 @@ WORKLOADS = {
     "pgo_se3_b256": ("lm", 20, "mixed_fp32", 1e-3),
     "pgo_se3_implicit_b256": ("lm", 20, "mixed_fp32", 1e-3),
     "pgo_se3_uneven_b1024": ("lm", 15, "mixed_fp32", 1e-3),
+    "pgo_se3_robust_b256": ("lm", 20, "mixed_fp32", 1e-3),
     "ba_b32": ("lm", 10, "mixed_fp32", 1e-3),
 }
 
