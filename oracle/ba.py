@@ -17,6 +17,7 @@ What it follows (App. D.3 and Sec. 3 "reprojection error", "robust loss function
 from __future__ import annotations
 
 import dataclasses
+import math
 
 import numpy as np
 import scipy.sparse as sp
@@ -73,7 +74,7 @@ def reproj_cost(T, p, o, f, xi_c, dp, eps_o):
 def huber(s, delta):
     d2 = delta * delta
     big = s > d2
-    s_safe = torch.where(big, s, torch.full_like(s, d2))
+    s_safe = torch.where(big, s, d2 + torch.zeros_like(s))  # delta may be a (traced) tensor
     return torch.where(big, 2.0 * delta * torch.sqrt(s_safe) - d2, s)
 
 
@@ -222,6 +223,46 @@ def implicit_grad_obs(P: BAProblem, theta, v, mode="exact"):
     x = spl.spsolve(H, v.numpy(), permc_spec="MMD_AT_PLUS_A")
     xo = torch.as_tensor(x[cols])
     return -torch.einsum('okp,ok->op', Mo, xo), torch.as_tensor(x)
+
+
+def implicit_grad_log_delta(P: BAProblem, theta, v, mode="exact"):
+    """Eq. 3 w.r.t. the Huber radius (Sec. 3.1 / App. D.3 learn this soft-kernel radius), per
+    observation: grad_o = -(d/du dS_o/dx_o)^T x_o with delta = exp(u); their sum is the gradient
+    w.r.t. a shared log radius."""
+    cams, pts = theta
+    f = P.focal
+    O, C = len(P.obs_cam), P.n_cams
+    _, x = implicit_grad_obs(P, theta, v, mode)
+
+    def s_obs(xl, u, T, p, o):
+        c = reproj_cost(T, p, o, f, xl[:6], xl[6:], torch.zeros(2, dtype=F64))
+        return 0.5 * huber((c * c).sum(), torch.exp(u))
+    x0 = torch.zeros(O, 9, dtype=F64)
+    u0 = torch.full((O,), math.log(P.delta), dtype=F64)
+    Mu = vmap(jacfwd(jacrev(s_obs, argnums=0), argnums=1))(x0, u0, cams[P.obs_cam], pts[P.obs_pt],
+                                                           P.obs_uv)
+    oc = P.obs_cam.numpy()
+    op = P.obs_pt.numpy()
+    cols = np.concatenate([oc[:, None] * 6 + np.arange(6), 6 * C + op[:, None] * 3 + np.arange(3)], 1)
+    xo = x[cols]
+    return -(Mu * xo).sum(-1)
+
+
+def fd_grad_log_delta(P: BAProblem, theta_star, h=1e-6, tol=1e-13, max_iters=50):
+    """Central difference of the camera loss w.r.t. a shared log Huber radius (re-solve by
+    undamped GN from theta*)."""
+    vals = []
+    for sgn in (1.0, -1.0):
+        Q = dataclasses.replace(P, delta=P.delta * math.exp(sgn * h))
+        th = theta_star
+        for _ in range(max_iters):
+            r, J = linearize(Q, th)
+            d, ok = nls.damped_step(J, r, 0.0, False)
+            th = retract(Q, th, d)
+            if float(np.abs(d.numpy()).max()) < tol:
+                break
+        vals.append(float(camera_loss(th[0], P.cams_gt)))
+    return (vals[0] - vals[1]) / (2 * h)
 
 
 def fd_grad_obs(P: BAProblem, theta_star, coords, h=1e-6, tol=1e-13, max_iters=50):

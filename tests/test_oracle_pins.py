@@ -571,3 +571,23 @@ def test_ba_jacobian_and_implicit_vs_fd():
     scale = float(gobs.abs().max())
     for (o, k), f in zip(coords, fd):
         assert abs(f - float(gobs[o, k])) < 1e-6 * scale
+
+
+def test_ba_implicit_gradient_wrt_huber_radius_vs_fd():
+    """The per-observation implicit gradients w.r.t. the log Huber radius sum to the central
+    difference of the outer loss w.r.t. a shared log radius (re-solve); observations inside the
+    radius contribute exactly zero."""
+    b = synth.ba(batch=1, n_cams=10, n_pts=40, config_id=401)
+    P = ba.ba_from_batch(b, 0)
+    th_s, _ = ba.solve(P, iters=60, tau=0.0)  # converged, as the re-solves of the FD are
+    v = ba.tangent_grad(P, th_s[0])
+    gd = ba.implicit_grad_log_delta(P, th_s, v)
+    # h = 1e-4: the re-solves stop at |step| < 1e-13, whose noise in the loss, divided by 2h,
+    # dominates a smaller step; the O(h^2) truncation is far below the tolerance
+    fd = ba.fd_grad_log_delta(P, th_s, h=1e-4)
+    assert abs(fd - float(gd.sum())) < 1e-6 * abs(fd)
+    cs = ba.reproj_cost(th_s[0][P.obs_cam], th_s[1][P.obs_pt], P.obs_uv, P.focal,
+                        torch.zeros(len(P.obs_cam), 6), torch.zeros(len(P.obs_cam), 3), 0)
+    inside = cs.norm(dim=-1) < P.delta
+    assert bool(inside.any()) and bool((~inside).any())
+    assert float(gd[inside].abs().max()) == 0.0
