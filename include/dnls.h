@@ -279,12 +279,16 @@ dnls_status dnls_ba_forward(const dnls_ba* h, const dnls_solver_opts* opts, cons
 /* Implicit backward (Eq. 3, true Hessian including the Huber rho'' term) w.r.t. the
  * observations at (cams, pts) from the preceding dnls_ba_forward on the same workspace:
  *   v_cams device [C, 6] and v_pts device [Pt, 3] tangent gradient of the outer loss;
- *   grad_obs device [O, 2] = -(D_obs g)^T x, x = H^-1 v (refinement preconditioned by the
- *   Schur factorization).  Only DNLS_IMPLICIT_EXACT is supported (else DNLS_ERR_UNSUPPORTED). */
+ *   grad_obs device [O, 2] = -(D_obs g)^T x, x = H^-1 v (conjugate gradients preconditioned
+ *   by the Schur factorization);
+ *   grad_log_delta device [O] or NULL: -(D_u g_o)^T x per observation for the log Huber radius
+ *   u = log(huber_delta) (Sec. 3.1 / App. D.3 learn this soft-kernel radius; zero for
+ *   observations inside the radius); their sum is the gradient w.r.t. a shared log radius.
+ * Only DNLS_IMPLICIT_EXACT is supported (else DNLS_ERR_UNSUPPORTED). */
 dnls_status dnls_ba_backward(const dnls_ba* h, const dnls_solver_opts* opts, const dnls_ba_inputs* in,
                              const double* cams, const double* pts, const double* v_cams,
-                             const double* v_pts, double* grad_obs, void* workspace,
-                             size_t workspace_bytes, void* stream, dnls_info* info);
+                             const double* v_pts, double* grad_obs, double* grad_log_delta,
+                             void* workspace, size_t workspace_bytes, void* stream, dnls_info* info);
 
 /* Sizes of the symbolic factorization (host values; for reports and tests). */
 typedef struct {

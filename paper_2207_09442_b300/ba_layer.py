@@ -77,15 +77,19 @@ class BASolver:
                  "dnls_ba_forward")
         return cams, pts
 
-    def backward(self, cams, pts, v_cams, v_pts, obs, prior_meas, prior_w, focal=500.0, huber_delta=2.0):
+    def backward(self, cams, pts, v_cams, v_pts, obs, prior_meas, prior_w, focal=500.0, huber_delta=2.0,
+                 with_log_delta=False):
+        """Implicit gradient w.r.t. the observations [O, 2]; with ``with_log_delta`` also the
+        per-observation gradient w.r.t. the log Huber radius [O] (returned second)."""
         g = torch.empty(self.s.n_obs, 2, dtype=torch.float64, device=self.device)
+        gd = torch.empty(self.s.n_obs, dtype=torch.float64, device=self.device) if with_log_delta else None
         inp = self._inputs(obs, prior_meas, prior_w, focal, huber_delta)
         _d.check(_d.lib().dnls_ba_backward(self.s.handle, ctypes.byref(self._copts), ctypes.byref(inp),
                                            cams.data_ptr(), pts.data_ptr(), v_cams.contiguous().data_ptr(),
-                                           v_pts.contiguous().data_ptr(), g.data_ptr(),
+                                           v_pts.contiguous().data_ptr(), g.data_ptr(), _d.ptr(gd),
                                            self.workspace.data_ptr(), self.workspace.numel(), _stream(),
                                            self.info.data_ptr()), "dnls_ba_backward")
-        return g
+        return (g, gd) if with_log_delta else g
 
     def info_dict(self) -> dict:
         return info_to_dict(self.info)

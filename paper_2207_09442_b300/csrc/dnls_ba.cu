@@ -81,6 +81,7 @@ struct BAArgs {
   const double* v_cams;
   const double* v_pts;
   double* grad_obs;
+  double* grad_log_delta;
   dnls_info* info;
 };
 
@@ -701,6 +702,14 @@ __global__ void k_bahvp_obs(BAArgs a, int vjp) {
   reproj<Dd>(T, p, ob, Dd(a.f), cc, Jc, Jp);
   const Dd w = huber_d1<Dd>(cc[0] * cc[0] + cc[1] * cc[1], a.delta);
   if (vjp) {
+    if (a.grad_log_delta) {
+      // dS_o/du = delta (sqrt(s) - delta) beyond the radius (u = log delta), 0 inside;
+      // the VJP is -d/dt of it along x
+      const Dd sq = cc[0] * cc[0] + cc[1] * cc[1];
+      double gd = 0.0;
+      if (a.delta > 0.0 && sq.v > a.delta * a.delta) gd = -(Dd(a.delta) * m_sqrt(sq)).d;
+      a.grad_log_delta[o] = a.st[b].status == DNLS_PROBLEM_NOT_SPD ? 0.0 : gd;
+    }
     if (a.grad_obs) {
       a.grad_obs[2 * o] = a.st[b].status == DNLS_PROBLEM_NOT_SPD ? 0.0 : (w * cc[0]).d;
       a.grad_obs[2 * o + 1] = a.st[b].status == DNLS_PROBLEM_NOT_SPD ? 0.0 : (w * cc[1]).d;
@@ -1242,7 +1251,8 @@ dnls_status dnls_ba_forward(const dnls_ba* h, const dnls_solver_opts* opts, cons
 
 dnls_status dnls_ba_backward(const dnls_ba* h, const dnls_solver_opts* opts, const dnls_ba_inputs* in,
                              const double* cams, const double* pts, const double* v_cams,
-                             const double* v_pts, double* grad_obs, void* workspace,
+                             const double* v_pts, double* grad_obs, double* grad_log_delta,
+                             void* workspace,
                              size_t workspace_bytes, void* stream, dnls_info* info) {
   if (!h || !in || !cams || !pts || !v_cams || !v_pts || !in->obs ||
       (h->impl.h.Q > 0 && (!in->prior_meas || !in->prior_w)))
@@ -1260,6 +1270,7 @@ dnls_status dnls_ba_backward(const dnls_ba* h, const dnls_solver_opts* opts, con
   a.v_cams = v_cams;
   a.v_pts = v_pts;
   a.grad_obs = grad_obs;
+  a.grad_log_delta = grad_log_delta;
   a.info = info;
   a.mixed = 0;  // the backward works in FP64
   cudaStream_t st = (cudaStream_t)stream;

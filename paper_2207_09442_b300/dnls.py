@@ -95,7 +95,7 @@ _SIGS = {
                                   c_void_p, c_void_p, c_void_p, c_size_t, c_void_p, c_void_p]),
     "dnls_ba_backward": (c_int32, [c_void_p, ctypes.POINTER(SolverOpts), ctypes.POINTER(BAInputs),
                                    c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
-                                   c_size_t, c_void_p, c_void_p]),
+                                   c_void_p, c_size_t, c_void_p, c_void_p]),
     "dnls_probe_fp64_peak": (c_int32, [c_int32, c_void_p, ctypes.POINTER(c_double)]),
 }
 

@@ -60,15 +60,18 @@ def test_small_ba_implicit_backward_fp64():
         th = (cams[c0:c1].cpu(), pts[p0:p1].cpu())  # Eq. 3 at the GPU's solution
         v = oba.tangent_grad(P, th[0])
         v_c[c0:c1] = v[:6 * (c1 - c0)].reshape(-1, 6)
-        refs.append(oba.implicit_grad_obs(P, th, v)[0])
+        refs.append((oba.implicit_grad_obs(P, th, v)[0], oba.implicit_grad_log_delta(P, th, v)))
     v_p = torch.zeros(b.pt_offsets[-1], 3, dtype=torch.float64)
-    g = sol.backward(cams, pts, v_c.to(DEV), v_p.to(DEV), *args, focal=b.focal, huber_delta=b.huber_delta)
+    g, gd = sol.backward(cams, pts, v_c.to(DEV), v_p.to(DEV), *args, focal=b.focal,
+                         huber_delta=b.huber_delta, with_log_delta=True)
     torch.cuda.synchronize()
     info = sol.info_dict()
     for k in range(b.batch):
         o0, o1 = b.obs_offsets[k], b.obs_offsets[k + 1]
-        err = rel(g[o0:o1], refs[k])
+        err = rel(g[o0:o1], refs[k][0])
         assert err < 1e-8, (k, err)
+        err_d = rel(gd[o0:o1], refs[k][1])  # log Huber radius, per observation
+        assert err_d < 1e-8, (k, err_d)
         assert info["status"][k] == 0, (k, info["refine_resid"][k], info["refine_steps"][k])
 
 
