@@ -59,12 +59,15 @@ def damped_step(J, r, lam, damped):
 
 
 def lm_loop(linearize: Callable, objective: Callable, retract: Callable, theta0,
-            algo="lm", iters=20, lam0=1e-3, tau=1e-14, record=False):
+            algo="lm", iters=20, lam0=1e-3, tau=1e-14, record=False, detach_at=None):
     """Run ``iters`` GN/LM iterations.  ``linearize(theta) -> (r, J)``, ``objective(theta) -> S``,
     ``retract(theta, delta) -> theta'``.  S is always ``objective`` (for robust costs the
     re-weighted residuals r of the linearisation give 1/2 rho'(s) s, not 1/2 rho(s)).  Branch
     decisions are taken on values; the arithmetic
-    stays on the autograd tape, so the loop can be differentiated (unrolled backward)."""
+    stays on the autograd tape, so the loop can be differentiated (unrolled backward).
+    ``detach_at = t`` cuts the tape through the poses at the start of iteration t (truncated
+    backpropagation, Sec. 4.3: only the last iters - t iterations are differentiated); the
+    linearization there is recomputed from the detached poses."""
     theta = theta0
     r, J = linearize(theta)
     # the objective itself (Eq. 1); for robust costs the re-weighted residuals of the
@@ -78,6 +81,9 @@ def lm_loop(linearize: Callable, objective: Callable, retract: Callable, theta0,
     hist = [float(S)]
     for it in range(iters):
         done = it + 1
+        if detach_at is not None and it == detach_at:
+            theta = theta.detach() if isinstance(theta, torch.Tensor) else tuple(t.detach() for t in theta)
+            r, J = linearize(theta)
         delta, ok = damped_step(J, r, lam, damped=(algo == "lm"))
         if not ok:
             if algo == "gn":

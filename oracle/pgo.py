@@ -192,7 +192,9 @@ def jacobian(g: Graph, theta, eps=None, logw=None, log_radius=None):
         J = _place(J, idx, i, Ji)
     lr = g.log_radius if log_radius is None else log_radius
     if lr is not None:
-        sw = torch.sqrt(welsch_d1((r * r).sum(-1), lr))
+        # sqrt(rho'(s)) = exp(-s / (2 c^2)), written so that its derivative stays finite where
+        # rho' underflows (the unrolled backward differentiates through these weights)
+        sw = torch.exp(-0.5 * (r * r).sum(-1) / torch.exp(2.0 * lr))
         r = r * sw[:, None]
         J = J * sw[:, None, None, None]
     return r.reshape(-1), J.reshape(E * dof, N * dof)
@@ -377,16 +379,29 @@ def dlm_grads(g: Graph, theta_star, v, eps=1e-2):
     return (ge0 - ge1) / eps, (gl0 - gl1) / eps, theta_d
 
 
-def unrolled_grads(g: Graph, loss_fn: Callable, algo="lm", iters=20, lam0=1e-3, tau=1e-14):
-    """Gradient of loss(solve(...)) w.r.t. (eps, logw) by autograd through all iterations;
-    the initial poses are treated as constants."""
+def unrolled_grads(g: Graph, loss_fn: Callable, algo="lm", iters=20, lam0=1e-3, tau=1e-14,
+                   truncate=None, with_radius=False):
+    """Gradient of loss(solve(...)) w.r.t. (eps, logw[, log_radius]) by autograd through the
+    iterations (Sec. 4.3 "Unrolling"); with ``truncate = k`` only through the last k iterations
+    ("Truncated differentiation").  The initial poses are treated as constants."""
     E, dof = g.ei.shape[0], g.dof
     eps = torch.zeros(E, dof, dtype=F64, requires_grad=True)
     logw = g.logw.clone().requires_grad_(True)
-    theta, _ = solve(g, algo=algo, iters=iters, lam0=lam0, tau=tau, eps=eps, logw=logw)
+    lr = None
+    if with_radius:
+        lr = g.log_radius.clone().requires_grad_(True)
+    theta = g.theta_init
+    detach_at = None if truncate is None or truncate >= iters else iters - truncate
+    theta, _ = nls.lm_loop(lambda th: jacobian(g, th, eps=eps, logw=logw, log_radius=lr),
+                           lambda th: objective(g, th, eps=eps, logw=logw, log_radius=lr),
+                           lambda th, d: lie.pose_retract(g.kind, th, d.reshape(-1, dof)),
+                           theta, algo=algo, iters=iters, lam0=lam0, tau=tau, detach_at=detach_at)
     L = loss_fn(theta)
-    ge, gl = torch.autograd.grad(L, (eps, logw))
-    return ge, gl
+    wrt = (eps, logw) + ((lr,) if with_radius else ())
+    if not L.requires_grad:  # every differentiated iteration was rejected: the map is constant
+        return tuple(torch.zeros_like(w) for w in wrt)
+    out = torch.autograd.grad(L, wrt, allow_unused=True)
+    return tuple(torch.zeros_like(w) if o is None else o for o, w in zip(out, wrt))
 
 
 def fd_grads(g: Graph, loss_fn: Callable, theta_star, coords, h=1e-6):

@@ -591,3 +591,35 @@ def test_ba_implicit_gradient_wrt_huber_radius_vs_fd():
     inside = cs.norm(dim=-1) < P.delta
     assert bool(inside.any()) and bool((~inside).any())
     assert float(gd[inside].abs().max()) == 0.0
+
+
+# ----------------------------------------------------------------------------- unrolled / truncated
+def test_truncated_over_all_iterations_is_the_unrolled_gradient():
+    b = synth.pgo_se3(batch=1, n_poses=10, n_lc=3, config_id=130, log_weights=True)
+    g = pgo.graph_from_batch(b, 0)
+    loss = lambda X: pgo.pose_error_loss(3, X, g.theta_gt)
+    ue, ul = pgo.unrolled_grads(g, loss, iters=4, tau=0.0)
+    te, tl = pgo.unrolled_grads(g, loss, iters=4, tau=0.0, truncate=4)
+    assert float((ue - te).abs().max()) == 0.0 and float((ul - tl).abs().max()) == 0.0
+    t2e, _ = pgo.unrolled_grads(g, loss, iters=4, tau=0.0, truncate=2)
+    assert float((ue - t2e).norm() / ue.norm()) > 1e-8  # earlier iterations do contribute here
+
+
+def test_one_truncated_gn_step_at_the_optimum_is_the_gn_implicit_gradient():
+    """From a converged theta* (detached), one Gauss-Newton step theta* (+) delta has
+    d(theta)/d(phi) = -(J^T J)^-1 d g / d phi (delta = 0 there): the implicit gradient with the
+    Gauss-Newton Hessian.  Checked with robust costs, so the IRLS weights are differentiated too."""
+    b = synth.pgo_se3(batch=1, n_poses=12, n_lc=6, config_id=98, outlier_frac=0.3, radius=0.03,
+                      log_weights=True)
+    g = pgo.graph_from_batch(b, 0)
+    th, _ = pgo.solve(g, algo="lm", iters=30, tau=0.0)
+    th = pgo.solve_to_convergence(g, th)
+    g.theta_init = th
+    loss = lambda X: pgo.pose_error_loss(3, X, g.theta_gt)
+    te, tl, tr = pgo.unrolled_grads(g, loss, algo="gn", iters=1, tau=0.0, truncate=1, with_radius=True)
+    v = pgo.tangent_grad(3, loss, th)
+    ie, il, _ = pgo.implicit_grads(g, th, v, "gn")
+    ir = pgo.implicit_grad_log_radius(g, th, v, "gn")
+    assert float((te - ie).norm() / ie.norm()) < 1e-8
+    assert float((tl - il).norm() / il.norm()) < 1e-8
+    assert float((tr - ir).norm() / ir.norm()) < 1e-8
