@@ -75,8 +75,11 @@ def _args():
                     help="which synthetic workload (default: the 256 x 128-pose SE(3) batch)")
     ap.add_argument("--algo", default="", choices=["", "gn", "lm", "dogleg"],
                     help="pose graphs: override the workload's optimizer")
-    ap.add_argument("--backward", default="implicit", choices=["implicit", "implicit_gn", "dlm"],
-                    help="pose graphs: backward mode (implicit true Hessian, implicit GN, or DLM)")
+    ap.add_argument("--backward", default="implicit", choices=["implicit", "implicit_gn", "dlm", "unroll"],
+                    help="pose graphs: backward mode (implicit true Hessian, implicit GN, DLM, or "
+                         "backpropagation through the iterations)")
+    ap.add_argument("--trunc", type=int, default=0,
+                    help="with --backward unroll: differentiate only the last k iterations (0 = all)")
     ap.add_argument("--no-extras", action="store_true", help="skip baselines (for profiling)")
     ap.add_argument("--batch", type=int, default=0,
                     help="first N problems only (profiling captures); default: the full workload")
@@ -174,7 +177,7 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- oracle samples
-def _oracle_sample(name, batch, idxs, iters, backward=True, algo=None, bmode="implicit"):
+def _oracle_sample(name, batch, idxs, iters, backward=True, algo=None, bmode="implicit", trunc=0):
     """The oracle (FP64 CPU) on the listed problems, forward (+ the backward ``bmode``):
     (seconds, executed iterations, solutions)."""
     walgo, _, _, lam0 = _setting(name)
@@ -201,6 +204,9 @@ def _oracle_sample(name, batch, idxs, iters, backward=True, algo=None, bmode="im
             v = pgo.tangent_grad(g.kind, lambda X: pgo.pose_error_loss(g.kind, X, g.theta_gt), th)
             if bmode == "dlm":
                 pgo.dlm_grads(g, th, v)
+            elif bmode == "unroll":
+                pgo.unrolled_grads(g, lambda X: pgo.pose_error_loss(g.kind, X, g.theta_gt), algo=algo,
+                                   iters=iters, lam0=lam0, tau=0.0, truncate=trunc or None)
             else:
                 pgo.implicit_grads(g, th, v, "gn" if bmode == "implicit_gn" else "exact")
     return time.perf_counter() - t0, n_it, sols
@@ -222,7 +228,7 @@ def run_reference(args):
     batch = synth.workload(name, batch=2)
     its_per = 2 if is_ba else iters
     cores = torch.get_num_threads()
-    kw = dict(backward=not is_ba, algo=algo, bmode=args.backward)
+    kw = dict(backward=not is_ba, algo=algo, bmode=args.backward, trunc=args.trunc)
     for _ in range(1 if is_ba else args.warmup):
         _oracle_sample(name, batch, [0], its_per, **kw)
     secs, its = 0.0, 0
@@ -332,7 +338,7 @@ def run_pose_graphs(args, rank, world, local, dist, out):
     st = layer.PoseGraphStructure.from_batch(batch)
     stats = st.stats()
     opts = layer.Options(algo=algo, iters=iters, precision=precision, tau=0.0,
-                         backward_mode=bmode, lambda0=lam0)
+                         backward_mode=bmode, lambda0=lam0, trunc_steps=args.trunc)
     t64 = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
     theta0 = t64(batch.theta_init)
     meas, wd = t64(batch.meas), t64(batch.wdiag)
@@ -379,7 +385,9 @@ def run_pose_graphs(args, rank, world, local, dist, out):
                    "precision": precision,
                    "backward": {"implicit": "implicit, true Hessian, cached factor + refinement",
                                 "implicit_gn": "implicit, Gauss-Newton Hessian, cached factor + refinement",
-                                "dlm": "direct loss minimization (one GN step, eps 1e-2)"}[bmode],
+                                "dlm": "direct loss minimization (one GN step, eps 1e-2)",
+                                "unroll": (f"truncated backpropagation, last {args.trunc} iterations"
+                                           if args.trunc else "backpropagation through all iterations")}[bmode],
                    "parallelism": f"{world} GPU(s), problems sharded by rank (weak)",
                    "l2": "flushed between steps"},
         "fwd_ms": fwd_ms, "bwd_ms": bwd_ms,
@@ -418,8 +426,12 @@ def run_pose_graphs(args, rank, world, local, dist, out):
     # both at the GPU's theta* (Eq. 3 is evaluated where the forward stopped)
     from oracle import pgo
     gerrs = []
+    if bmode == "unroll":
+        sample_g = []  # parity of the unrolled gradients: tests on tie-free trajectories
+    else:
+        sample_g = sample[:2]
     gm_cpu, gl_cpu, v_cpu = gm.cpu(), gl.cpu(), v.cpu()
-    for b_ in sample[:2]:
+    for b_ in sample_g:
         p0, p1 = int(batch.pose_offsets[b_]), int(batch.pose_offsets[b_ + 1])
         e0, e1 = int(batch.edge_offsets[b_]), int(batch.edge_offsets[b_ + 1])
         g_ = pgo.graph_from_batch(batch, b_)
@@ -436,7 +448,8 @@ def run_pose_graphs(args, rank, world, local, dist, out):
         gerrs.append(max(errs_b))
     out["accuracy"] = {"max_rel_err_vs_oracle": max(errs), "sampled_problems": sample,
                        "tolerance": 1e-9 if precision == "fp64" else 1e-5,
-                       "grad_max_rel_err_vs_oracle": max(gerrs), "grad_sampled_problems": sample[:2],
+                       "grad_max_rel_err_vs_oracle": max(gerrs) if gerrs else None,
+                       "grad_sampled_problems": sample_g,
                        "grad_tolerance": 1e-8 if precision == "fp64" else 1e-4}
     # plain FP64 per-problem GPU path: same kernels, FP64 everywhere, one problem per launch
     nplain = min(8, B)
@@ -445,7 +458,8 @@ def run_pose_graphs(args, rank, world, local, dist, out):
         one = batch.problem(b_)
         s1 = layer.PoseGraphSolver(layer.PoseGraphStructure.from_batch(one),
                                    layer.Options(algo=algo, iters=iters, precision="fp64", tau=0.0,
-                                                 lambda0=lam0, backward_mode=bmode), dev)
+                                                 lambda0=lam0, backward_mode=bmode,
+                                                 trunc_steps=args.trunc), dev)
         a1 = [t64(one.theta_init), t64(one.meas), t64(one.wdiag),
               torch.as_tensor(one.logw, dtype=torch.float32, device=dev)]
         lr1 = None if one.log_radius is None else t64(one.log_radius)
@@ -480,7 +494,8 @@ def run_pose_graphs(args, rank, world, local, dist, out):
 
     out["e2e"] = _e2e(run, h_in, h_out, d_in, args.steps, stream, executed)
     # CPU baseline: the oracle as it stands on a bounded sample (2 problems, fwd + bwd)
-    secs, its, _ = _oracle_sample(name, batch, list(range(min(2, B))), iters, algo=algo, bmode=bmode)
+    secs, its, _ = _oracle_sample(name, batch, list(range(min(2, B))), iters, algo=algo, bmode=bmode,
+                                  trunc=args.trunc)
     out["cpu_baseline"] = {"value": its / secs, "unit": "LM iters/s", "cores": torch.get_num_threads(),
                            "kind": "oracle",
                            "sample": f"{min(2, B)} problems x ({iters} {algo.upper()} its + {bmode} "

@@ -60,8 +60,10 @@ enum { DNLS_SE2 = 2, DNLS_SE3 = 3 };
 enum { DNLS_GN = 0, DNLS_LM = 1, DNLS_DOGLEG = 2 };
 enum { DNLS_FP64 = 0, DNLS_MIXED_FP32 = 1 };
 /* backward modes: implicit differentiation (Eq. 3 / Prop. 1) with the true Hessian or the
- * Gauss-Newton matrix, or direct loss minimization (Sec. 4.3, App. G; pose graphs only) */
-enum { DNLS_IMPLICIT_EXACT = 0, DNLS_IMPLICIT_GN = 1, DNLS_BACKWARD_DLM = 2 };
+ * Gauss-Newton matrix, direct loss minimization (Sec. 4.3, App. G), or backpropagation through
+ * the solver's iterations (Sec. 4.3 "Unrolling" / "Truncated differentiation"); the last two
+ * for pose graphs only */
+enum { DNLS_IMPLICIT_EXACT = 0, DNLS_IMPLICIT_GN = 1, DNLS_BACKWARD_DLM = 2, DNLS_BACKWARD_UNROLL = 3 };
 enum { DNLS_ORDER_MIN_DEGREE = 0, DNLS_ORDER_NATURAL = 1 };
 
 /* Solver options (paper Sec. 3: optimizer choice, max_iterations, backward_mode).  The LM
@@ -82,8 +84,8 @@ typedef struct {
   int32_t iters;           /* number of iterations K (>= 0) */
   int32_t precision;       /* DNLS_FP64, or DNLS_MIXED_FP32 (residuals, Jacobians and H in FP32;
                               relative poses, g, the factorization and the acceptance in FP64) */
-  int32_t backward_mode;   /* DNLS_IMPLICIT_EXACT (true Hessian of S), DNLS_IMPLICIT_GN or
-                              DNLS_BACKWARD_DLM */
+  int32_t backward_mode;   /* DNLS_IMPLICIT_EXACT (true Hessian of S), DNLS_IMPLICIT_GN,
+                              DNLS_BACKWARD_DLM or DNLS_BACKWARD_UNROLL */
   int32_t refine_max;      /* max (preconditioned CG) steps of the adjoint solve (>= 1) */
   int32_t threads;         /* threads per CTA: 0 = library choice, else 128 or 256 */
   int32_t ctas_per_sm;     /* resident CTAs per SM of the persistent launch: 0 = library choice */
@@ -93,6 +95,9 @@ typedef struct {
   double refine_tol;       /* adjoint solve stops once ||v - H x|| <= refine_tol * ||v|| */
   double dlm_eps;          /* DNLS_BACKWARD_DLM: the finite-difference scale eps (> 0) */
   double radius0;          /* DNLS_DOGLEG: initial trust radius (> 0) */
+  int32_t trunc_steps;     /* DNLS_BACKWARD_UNROLL: differentiate only the last trunc_steps
+                              iterations (truncated backpropagation); 0 = all (unrolling) */
+  int32_t reserved;        /* zero */
 } dnls_solver_opts;
 
 /* Per-problem report (device array of `batch` entries, written by forward/backward). */
@@ -180,7 +185,20 @@ dnls_status dnls_graph_forward(const dnls_graph* g, const dnls_solver_opts* opts
  * with eps = opts->dlm_eps.  It needs no cached factor (the workspace's factor is overwritten
  * and marked stale, so a later implicit backward refactors); refine_* are unused and info gets
  * refine_steps = 1.  A non-SPD shifted matrix gives zero gradients and DNLS_PROBLEM_NOT_SPD.
- * DLM with robust costs (in->log_radius != NULL) is not implemented: DNLS_ERR_UNSUPPORTED. */
+ * DLM with robust costs (in->log_radius != NULL) is not implemented: DNLS_ERR_UNSUPPORTED.
+ *
+ * With backward_mode = DNLS_BACKWARD_UNROLL the call backpropagates v through the GN/LM
+ * iterations the forward recorded (it must have run with the same opts, whose workspace size
+ * then includes one record per problem: poses, step and damping of every iteration):
+ * reverse over the last trunc_steps iterations (all if 0), each accepted step
+ * theta_{t+1} = theta_t Exp(delta_t), delta_t = -(H_t + lambda_t D_t)^-1 g_t contributing
+ *   xi_t = Ad(Exp(-delta_t))^T xi_{t+1} - dF/d(theta_t),   phi_bar += -dF/d(phi),
+ *   F = y^T (H_t + lambda_t D_t) delta_t + y^T g_t,  y = (H_t + lambda_t D_t)^-1 J_r(delta_t)^T xi_{t+1}
+ * with y and delta_t held fixed (D_t = diag(max(diag H_t, 1e-9)) differentiated where the floor
+ * is inactive); rejected steps pass xi unchanged.  Derivatives of F per cost are forward-mode
+ * dual numbers; everything in FP64.  Outputs as for the implicit modes (grad_log_radius with
+ * robust costs); refine_steps reports the iterations differentiated.  Dogleg forwards cannot
+ * be unrolled (DNLS_ERR_UNSUPPORTED). */
 dnls_status dnls_graph_backward(const dnls_graph* g, const dnls_solver_opts* opts,
                                 const dnls_graph_inputs* in, const double* theta_star,
                                 const double* v, double* grad_meas, double* grad_logw,

@@ -58,8 +58,11 @@ struct KArgs {
   char* ws;
   int* counter;
   dnls_info* info;
-  int algo, iters, mode, refine_max;
+  int algo, iters, mode, refine_max, trunc_steps;
   double lam0, tau, refine_tol, dlm_eps, radius0;
+  char* rec;            // unrolled backward: per-problem iteration records (null: none)
+  int64_t rec_stride;   // bytes per problem record
+  int rec_nmax;         // poses per record slot (the batch's largest problem)
   int smem_bytes;       // dynamic shared memory per CTA for staging (0 = none)
 };
 
@@ -249,7 +252,7 @@ __device__ void lin_costs(Prob<KIND>& p, const double* poses) {
       P s2 = P(0);
 #pragma unroll
       for (int a = 0; a < D; ++a) s2 += out[a] * out[a];
-      const P sw = (P)sqrt(exp(-(double)s2 * exp(-2.0 * p.logrc[e])));
+      const P sw = (P)exp(-0.5 * (double)s2 * exp(-2.0 * p.logrc[e]));
       const int nw = D + (j >= 0 ? 2 : 1) * BS;
       for (int k = 0; k < nw; ++k) out[k] *= sw;
     }
@@ -370,6 +373,39 @@ __device__ void retract(Prob<KIND>& p, const double* src, const double* delta_po
   }
 }
 
+// ----------------------------------------------------------------------------- iteration records
+// What the unrolled backward needs of every forward iteration t: the damping lambda_t, whether
+// the step was accepted, the poses theta_t at its start and its step delta_t (positions order).
+// Layout per problem: [int32 done, pad to 16][lambda: iters doubles][accepted: iters int32, padded
+// to 8 bytes][theta: iters x nmax x PW doubles][delta: iters x nmax x D doubles].
+struct RecView {
+  int32_t* done;
+  double* lam;
+  int32_t* acc;
+  double* th;
+  double* del;
+};
+
+__host__ __device__ inline int64_t rec_bytes(int iters, int nmax, int pw, int dof) {
+  const int64_t b = 16 + 8 * (int64_t)iters + ((4 * (int64_t)iters + 7) & ~7) +
+                    8 * (int64_t)iters * nmax * (pw + dof);
+  return (b + 255) & ~(int64_t)255;
+}
+
+template <int KIND>
+__device__ RecView rec_view(const KArgs& a, int b) {
+  constexpr int D = Group<KIND>::DOF, PW = Group<KIND>::PW;
+  char* r = a.rec + (int64_t)b * a.rec_stride;
+  RecView v;
+  v.done = (int32_t*)r;
+  v.lam = (double*)(r + 16);
+  v.acc = (int32_t*)(r + 16 + 8 * (int64_t)a.iters);
+  v.th = (double*)(r + 16 + 8 * (int64_t)a.iters + ((4 * (int64_t)a.iters + 7) & ~7));
+  v.del = v.th + (int64_t)a.iters * a.rec_nmax * PW;
+  (void)D;
+  return v;
+}
+
 // ----------------------------------------------------------------------------- forward
 template <int KIND, class P>
 __device__ void forward_problem(const KArgs& a, int b, char* smem, double* red, int* sflag) {
@@ -388,8 +424,18 @@ __device__ void forward_problem(const KArgs& a, int b, char* smem, double* red, 
   const bool lm = a.algo == DNLS_LM;
   double lam = lm ? a.lam0 : 0.0, lam_fact = lam;
   int done = 0, accepted = 0, status = DNLS_PROBLEM_OK, factor_ok = 0, nfact = 0;
+  RecView rv;
+  if (a.rec) rv = rec_view<KIND>(a, b);
   for (int it = 0; it < a.iters; ++it) {
     done = it + 1;
+    if (a.rec) {  // record theta_t and lambda_t for the unrolled backward
+      double* rth = rv.th + (int64_t)it * a.rec_nmax * PW;
+      for (int k = threadIdx.x; k < p.N * PW; k += blockDim.x) rth[k] = p.theta[k];
+      if (threadIdx.x == 0) {
+        rv.lam[it] = lam;
+        rv.acc[it] = 0;
+      }
+    }
     ++nfact;
     const bool ok = factor<KIND>(p, lam, sflag, it);
     factor_ok = ok ? 1 : 0;
@@ -405,6 +451,10 @@ __device__ void forward_problem(const KArgs& a, int b, char* smem, double* red, 
     for (int k = threadIdx.x; k < n; k += blockDim.x) p.dx[k] = -p.g[k];
     __syncthreads();
     chol_solve<KIND>(p, p.dx);
+    if (a.rec) {
+      double* rdel = rv.del + (int64_t)it * a.rec_nmax * D;
+      for (int k = threadIdx.x; k < n; k += blockDim.x) rdel[k] = p.dx[k];
+    }
     retract<KIND>(p, p.theta, p.dx, p.thc);
     __syncthreads();
     const double Sc = eval_S<KIND>(p, p.thc, red);
@@ -422,6 +472,7 @@ __device__ void forward_problem(const KArgs& a, int b, char* smem, double* red, 
     const bool frozen = a.tau > 0.0 && fabs(S - Sc) <= a.tau * S;
     if (accept) {
       for (int k = threadIdx.x; k < p.N * PW; k += blockDim.x) p.theta[k] = p.thc[k];
+      if (a.rec && threadIdx.x == 0) rv.acc[it] = 1;
       __syncthreads();
       ++accepted;
       S = Sc;
@@ -439,6 +490,7 @@ __device__ void forward_problem(const KArgs& a, int b, char* smem, double* red, 
   }
   if (factor_ok) p.stage_out_factor();  // keep the factor for the backward
   if (threadIdx.x == 0) {
+    if (a.rec) *rv.done = done;
     p.st->lambda_fact = lam_fact;
     p.st->S = S;
     p.st->factor_ok = factor_ok;
@@ -1050,6 +1102,250 @@ __device__ void backward_problem(const KArgs& a, int b, char* smem, double* red,
   __syncthreads();
 }
 
+// ----------------------------------------------------------------------------- unrolled backward
+// d/d(direction) of F_e = (Jt_e y)^T (Jt_e delta + rt_e) + lambda sum_k [H_kk > floor] y_k delta_k
+// |Jt_e[:, k]|^2 at theta_t, as one dual-number evaluation of cost e.  Directions: 0..D-1 the
+// tangent of pose i, D..2D-1 of pose j, 2D..3D-1 the measurement tangent, 3D the log-weight,
+// 3D+1 the log radius.  (Jt, rt: the IRLS-weighted Jacobian and residual.)  y, delta are in
+// elimination positions.
+template <int KIND>
+__device__ double unroll_dF(const Prob<KIND>& p, int e, int dir, const double* th, const double* y,
+                            const double* del, double lam) {
+  typedef Group<KIND> G;
+  constexpr int D = G::DOF, PW = G::PW, BS = D * D;
+  typedef Dual<double> Dd;
+  const int i = p.ei[e], j = p.ej[e];
+  double unit[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) unit[k] = (dir % D == k) ? 1.0 : 0.0;
+  Dd Ti[PW], Tj[PW], Zd[PW], wd[D];
+  if (dir < D) {
+    pose_dual<KIND>(th + (int64_t)i * PW, unit, Ti);
+  } else {
+#pragma unroll
+    for (int k = 0; k < PW; ++k) Ti[k] = Dd(th[(int64_t)i * PW + k]);
+  }
+  if (j >= 0) {
+    if (dir >= D && dir < 2 * D) {
+      pose_dual<KIND>(th + (int64_t)j * PW, unit, Tj);
+    } else {
+#pragma unroll
+      for (int k = 0; k < PW; ++k) Tj[k] = Dd(th[(int64_t)j * PW + k]);
+    }
+  }
+  if (dir >= 2 * D && dir < 3 * D) {
+    pose_dual<KIND>(p.meas + (int64_t)e * PW, unit, Zd);
+  } else {
+#pragma unroll
+    for (int k = 0; k < PW; ++k) Zd[k] = Dd(p.meas[(int64_t)e * PW + k]);
+  }
+  double w[D];
+  p.weight(e, w);
+#pragma unroll
+  for (int k = 0; k < D; ++k) wd[k] = dir == 3 * D ? Dd(w[k], w[k]) : Dd(w[k]);  // w = e^l d
+  Dd r[D], Ji[BS], Jj[BS];
+  if (j >= 0) {
+    Dd A[PW], Ai[PW], Em[PW];
+    G::invmul(Ti, Tj, A);
+    G::invmul(Tj, Ti, Ai);
+    G::invmul(Zd, A, Em);
+    between_lin<KIND, Dd>(Ai, Em, wd, r, Ji, Jj);
+  } else {
+    Dd Em[PW];
+    G::invmul(Zd, Ti, Em);
+    prior_lin<KIND, Dd>(Em, wd, r, Ji);
+  }
+  if (p.logrc) {  // IRLS weight exp(-s / (2 c^2)), c = exp(u)
+    const Dd u = dir == 3 * D + 1 ? Dd(p.logrc[e], 1.0) : Dd(p.logrc[e]);
+    Dd s2 = r[0] * r[0];
+#pragma unroll
+    for (int k = 1; k < D; ++k) s2 = s2 + r[k] * r[k];
+    const Dd sw = m_exp(Dd(-0.5) * s2 * m_exp(Dd(-2.0) * u));
+#pragma unroll
+    for (int k = 0; k < D; ++k) r[k] = r[k] * sw;
+#pragma unroll
+    for (int k = 0; k < BS; ++k) {
+      Ji[k] = Ji[k] * sw;
+      if (j >= 0) Jj[k] = Jj[k] * sw;
+    }
+  }
+  const int pi = p.iperm[i], pj = j >= 0 ? p.iperm[j] : 0;
+  const double *yi = y + pi * D, *yj = y + pj * D, *di = del + pi * D, *dj = del + pj * D;
+  Dd F = Dd(0.0);
+#pragma unroll
+  for (int a2 = 0; a2 < D; ++a2) {
+    Dd Jy = Dd(0.0), Jd = Dd(0.0);
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      Jy = Jy + Ji[a2 * D + k] * Dd(yi[k]);
+      Jd = Jd + Ji[a2 * D + k] * Dd(di[k]);
+      if (j >= 0) {
+        Jy = Jy + Jj[a2 * D + k] * Dd(yj[k]);
+        Jd = Jd + Jj[a2 * D + k] * Dd(dj[k]);
+      }
+    }
+    F = F + Jy * (Jd + r[a2]);
+  }
+  if (lam > 0.0) {  // the damping diag(max(diag H, floor)) where the floor is inactive
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      if (p.H[(int64_t)pi * BS + k * D + k] > kDiagFloor) {
+        Dd c2 = Dd(0.0);
+#pragma unroll
+        for (int a2 = 0; a2 < D; ++a2) c2 = c2 + Ji[a2 * D + k] * Ji[a2 * D + k];
+        F = F + Dd(lam * yi[k] * di[k]) * c2;
+      }
+      if (j >= 0 && p.H[(int64_t)pj * BS + k * D + k] > kDiagFloor) {
+        Dd c2 = Dd(0.0);
+#pragma unroll
+        for (int a2 = 0; a2 < D; ++a2) c2 = c2 + Jj[a2 * D + k] * Jj[a2 * D + k];
+        F = F + Dd(lam * yj[k] * dj[k]) * c2;
+      }
+    }
+  }
+  return F.d;
+}
+
+// Backpropagation through the recorded iterations of one problem (see DNLS_BACKWARD_UNROLL).
+template <int KIND>
+__device__ void unroll_problem(const KArgs& a, int b, char* smem, double* red, int* sflag) {
+  typedef Group<KIND> G;
+  constexpr int D = G::DOF, PW = G::PW;
+  typedef Dual<double> Dd;
+  Prob<KIND> p;
+  p.init(a, b, smem, a.smem_bytes);
+  p.stage_in(false);
+  p.prepare_weights();
+  const int n = p.N * D;
+  const RecView rv = rec_view<KIND>(a, b);
+  int status = DNLS_PROBLEM_OK;
+  const int done = *rv.done;
+  const bool rec_ok = done >= 0 && done <= a.iters;
+  const int t0 = a.trunc_steps > 0 ? max(0, done - a.trunc_steps) : 0;
+  const bool robust = p.logrc != nullptr;
+  for (int e = threadIdx.x; e < p.E; e += blockDim.x) {
+    const int64_t ge = p.m->edge_off + e;
+    if (a.grad_logw) a.grad_logw[ge] = 0.0;
+    if (a.grad_log_radius) a.grad_log_radius[ge] = 0.0;
+    if (a.grad_meas)
+      for (int k = 0; k < D; ++k) a.grad_meas[ge * D + k] = 0.0;
+  }
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const int pos = k / D, c = k % D;
+    p.br[k] = a.v[(p.m->pose_off + p.perm[pos]) * D + c];  // xi_bar at theta_done
+  }
+  __syncthreads();
+  int steps = 0;
+  for (int t = rec_ok ? done - 1 : -1; t >= t0; --t) {
+    if (!rv.acc[t]) continue;  // a rejected step leaves theta, and xi_bar, unchanged
+    ++steps;
+    const double* th = rv.th + (int64_t)t * a.rec_nmax * PW;
+    const double* del = rv.del + (int64_t)t * a.rec_nmax * D;
+    const double lam = rv.lam[t];
+    lin_costs<KIND, double>(p, th);
+    __syncthreads();
+    assemble<KIND, double>(p);
+    __syncthreads();
+    if (!factor<KIND>(p, lam, sflag, t + 1)) {
+      status = DNLS_PROBLEM_NOT_SPD;
+      break;
+    }
+    // per pose: delta_bar = J_r(delta)^T xi_bar (into dx), Ad(Exp(-delta))^T xi_bar (into bx)
+    for (int it = threadIdx.x; it < n; it += blockDim.x) {
+      const int k = it / D, c = it % D;
+      const double* dk = del + k * D;
+      const double* xb = p.br + k * D;
+      double md[D], E0i[PW], Ad[D * D];
+#pragma unroll
+      for (int q = 0; q < D; ++q) md[q] = -dk[q];
+      G::exp(md, E0i);
+      G::adjoint(E0i, Ad);
+      Dd xd[D], Ed[PW], E0d[PW], M[PW], lg[D];
+#pragma unroll
+      for (int q = 0; q < D; ++q) xd[q] = Dd(dk[q], q == c ? 1.0 : 0.0);
+      G::exp(xd, Ed);
+#pragma unroll
+      for (int q = 0; q < PW; ++q) E0d[q] = Dd(E0i[q]);
+      G::mul(E0d, Ed, M);
+      G::log(M, lg);  // Log(Exp(-delta) Exp(delta + t e_c)) = t J_r(delta) e_c + O(t^2)
+      double sj = 0.0, sa = 0.0;
+#pragma unroll
+      for (int q = 0; q < D; ++q) {
+        sj = fma(xb[q], lg[q].d, sj);
+        sa = fma(Ad[q * D + c], xb[q], sa);
+      }
+      p.dx[it] = sj;
+      p.bx[it] = sa;
+    }
+    __syncthreads();
+    chol_solve<KIND>(p, p.dx);  // y = (H_t + lambda_t D_t)^-1 delta_bar
+    const int ndir = 3 * D + 1 + (robust ? 1 : 0);
+    for (int it = threadIdx.x; it < p.E * ndir; it += blockDim.x) {
+      const int e = it / ndir, dir = it % ndir;
+      if (dir >= D && dir < 2 * D && p.ej[e] < 0) continue;  // a prior has no second pose
+      const double dF = unroll_dF<KIND>(p, e, dir, th, p.dx, del, lam);
+      const int64_t ge = p.m->edge_off + e;
+      double* eb = p.ebuf + (int64_t)e * 4 * D;
+      if (dir < D)
+        eb[dir] = dF;
+      else if (dir < 2 * D)
+        eb[2 * D + dir - D] = dF;
+      else if (dir < 3 * D) {
+        if (a.grad_meas) a.grad_meas[ge * D + dir - 2 * D] -= dF;
+      } else if (dir == 3 * D) {
+        if (a.grad_logw) a.grad_logw[ge] -= dF;
+      } else if (a.grad_log_radius) {
+        a.grad_log_radius[ge] -= dF;
+      }
+    }
+    __syncthreads();
+    // xi_bar_t = Ad(Exp(-delta))^T xi_bar_{t+1} - dF/d(theta_t), gathered per pose
+    for (int it = threadIdx.x; it < n; it += blockDim.x) {
+      const int k = it / D, c = it % D;
+      double sacc = p.bx[it];
+      for (int q = p.incptr[k]; q < p.incptr[k + 1]; ++q) {
+        const int tq = p.inc[q];
+        sacc -= p.ebuf[(int64_t)(tq >> 1) * 4 * D + (tq & 1) * 2 * D + c];
+      }
+      p.br[it] = sacc;
+    }
+    __syncthreads();
+  }
+  if (!rec_ok) status = DNLS_PROBLEM_NAN;
+  if (status != DNLS_PROBLEM_OK) {
+    for (int e = threadIdx.x; e < p.E; e += blockDim.x) {
+      const int64_t ge = p.m->edge_off + e;
+      if (a.grad_logw) a.grad_logw[ge] = 0.0;
+      if (a.grad_log_radius) a.grad_log_radius[ge] = 0.0;
+      if (a.grad_meas)
+        for (int k = 0; k < D; ++k) a.grad_meas[ge * D + k] = 0.0;
+    }
+  }
+  if (threadIdx.x == 0) {
+    p.st->factor_ok = 0;  // L now holds an iteration's damped factor, not the forward's last
+    if (a.info) {
+      a.info[b].refine_resid = 0.0;
+      a.info[b].refine_steps = steps;
+      if (status != DNLS_PROBLEM_OK) a.info[b].status = status;
+    }
+  }
+  __syncthreads();
+}
+
+// the unrolled backward as its own kernel (its dual-number evaluations need many registers)
+template <int KIND>
+__global__ void __launch_bounds__(256) k_unroll(KArgs a) {
+  __shared__ double red[256];
+  __shared__ int sflag, slot;
+  for (;;) {
+    const int b = next_problem(a, &slot);
+    if (b < 0) break;
+    if (threadIdx.x == 0) sflag = -1;
+    __syncthreads();
+    unroll_problem<KIND>(a, b, a.smem_bytes ? dyn_smem : nullptr, red, &sflag);
+  }
+}
+
 template <int KIND>
 __global__ void __launch_bounds__(256) k_backward(KArgs a) {
   __shared__ double red[256];
@@ -1120,6 +1416,7 @@ struct GraphHandle {
   int32_t* d_order = nullptr;
   int sm_count = 0;
   int smem_optin = 0;
+  int nmax = 0;  // poses of the largest problem
 };
 
 }  // namespace dnls
@@ -1155,8 +1452,9 @@ dnls_status check_opts(const dnls_solver_opts* o) {
   if (o->iters < 0 || o->iters > 100000) return DNLS_ERR_ARG;
   if (o->precision != DNLS_FP64 && o->precision != DNLS_MIXED_FP32) return DNLS_ERR_ARG;
   if (o->backward_mode != DNLS_IMPLICIT_EXACT && o->backward_mode != DNLS_IMPLICIT_GN &&
-      o->backward_mode != DNLS_BACKWARD_DLM)
+      o->backward_mode != DNLS_BACKWARD_DLM && o->backward_mode != DNLS_BACKWARD_UNROLL)
     return DNLS_ERR_ARG;
+  if (o->trunc_steps < 0) return DNLS_ERR_ARG;
   if (o->backward_mode == DNLS_BACKWARD_DLM && !(o->dlm_eps > 0.0 && std::isfinite(o->dlm_eps)))
     return DNLS_ERR_ARG;
   if (o->threads != 0 && o->threads != 128 && o->threads != 256) return DNLS_ERR_ARG;
@@ -1165,9 +1463,22 @@ dnls_status check_opts(const dnls_solver_opts* o) {
   return DNLS_OK;
 }
 
-dnls_status check_ws(const dnls_graph* g, void* ws, size_t bytes) {
+// workspace layout with iteration records (DNLS_BACKWARD_UNROLL): the solver workspace, then one
+// record per problem
+int64_t rec_offset(const dnls_graph* g) { return (g->impl.h.ws_bytes + 255) & ~(int64_t)255; }
+int64_t rec_stride(const dnls_graph* g, int iters) {
+  const GraphHost& h = g->impl.h;
+  return rec_bytes(iters, g->impl.nmax, h.kind == DNLS_SE3 ? 12 : 4, h.dof);
+}
+int64_t workspace_need(const dnls_graph* g, const dnls_solver_opts* o) {
+  if (o && o->backward_mode == DNLS_BACKWARD_UNROLL)
+    return rec_offset(g) + (int64_t)g->impl.h.B * rec_stride(g, o->iters);
+  return g->impl.h.ws_bytes;
+}
+
+dnls_status check_ws(const dnls_graph* g, void* ws, size_t bytes, const dnls_solver_opts* o = nullptr) {
   if (!ws || ((uintptr_t)ws & 255)) return DNLS_ERR_WORKSPACE;
-  if ((int64_t)bytes < g->impl.h.ws_bytes) return DNLS_ERR_WORKSPACE;
+  if ((int64_t)bytes < workspace_need(g, o)) return DNLS_ERR_WORKSPACE;
   return DNLS_OK;
 }
 
@@ -1248,6 +1559,7 @@ dnls_status dnls_graph_create(const dnls_graph_desc* desc, dnls_graph** out) {
   if (s == DNLS_OK) s = cuda_status(cudaDeviceGetAttribute(&G.sm_count, cudaDevAttrMultiProcessorCount, G.device));
   if (s == DNLS_OK)
     s = cuda_status(cudaDeviceGetAttribute(&G.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, G.device));
+  for (const ProbMeta& m : G.h.meta) G.nmax = std::max(G.nmax, (int)m.N);
   if (s == DNLS_OK) s = upload(&G.d_meta, G.h.meta);
   if (s == DNLS_OK) s = upload(&G.d_sym, G.h.sym);
   if (s == DNLS_OK) s = upload(&G.d_ei, G.h.ei);
@@ -1275,7 +1587,7 @@ void dnls_graph_destroy(dnls_graph* g) {
 dnls_status dnls_graph_workspace_size(const dnls_graph* g, const dnls_solver_opts* opts, size_t* bytes) {
   if (!g || !bytes) return DNLS_ERR_ARG;
   if (opts && check_opts(opts) != DNLS_OK) return DNLS_ERR_ARG;
-  *bytes = (size_t)g->impl.h.ws_bytes;
+  *bytes = (size_t)workspace_need(g, opts);
   return DNLS_OK;
 }
 
@@ -1285,7 +1597,7 @@ dnls_status dnls_graph_forward(const dnls_graph* g, const dnls_solver_opts* opts
   if (!g || !in || !theta || !in->meas || !in->wdiag) return DNLS_ERR_ARG;
   dnls_status s = check_opts(opts);
   if (s != DNLS_OK) return s;
-  if ((s = check_ws(g, workspace, workspace_bytes)) != DNLS_OK) return s;
+  if ((s = check_ws(g, workspace, workspace_bytes, opts)) != DNLS_OK) return s;
   KArgs a = base_args(g, in, workspace);
   a.theta = theta;
   a.info = info;
@@ -1294,6 +1606,11 @@ dnls_status dnls_graph_forward(const dnls_graph* g, const dnls_solver_opts* opts
   a.lam0 = opts->lambda0;
   a.tau = opts->tau;
   a.radius0 = opts->radius0;
+  if (opts->backward_mode == DNLS_BACKWARD_UNROLL && opts->algo != DNLS_DOGLEG) {
+    a.rec = (char*)workspace + rec_offset(g);  // record the iterations for the backward
+    a.rec_stride = rec_stride(g, opts->iters);
+    a.rec_nmax = g->impl.nmax;
+  }
   return launch_forward(g, opts, a, (cudaStream_t)stream);
 }
 
@@ -1306,8 +1623,9 @@ dnls_status dnls_graph_backward(const dnls_graph* g, const dnls_solver_opts* opt
   dnls_status s = check_opts(opts);
   if (s != DNLS_OK) return s;
   if (opts->backward_mode == DNLS_BACKWARD_DLM && in->log_radius) return DNLS_ERR_UNSUPPORTED;
+  if (opts->backward_mode == DNLS_BACKWARD_UNROLL && opts->algo == DNLS_DOGLEG) return DNLS_ERR_UNSUPPORTED;
   if (opts->refine_max < 1 || !(opts->refine_tol >= 0.0)) return DNLS_ERR_ARG;
-  if ((s = check_ws(g, workspace, workspace_bytes)) != DNLS_OK) return s;
+  if ((s = check_ws(g, workspace, workspace_bytes, opts)) != DNLS_OK) return s;
   KArgs a = base_args(g, in, workspace);
   a.theta = const_cast<double*>(theta_star);
   a.v = v;
@@ -1321,6 +1639,15 @@ dnls_status dnls_graph_backward(const dnls_graph* g, const dnls_solver_opts* opt
   a.dlm_eps = opts->dlm_eps;
   a.counter = (int*)workspace + 1;
   cudaStream_t st = (cudaStream_t)stream;
+  if (opts->backward_mode == DNLS_BACKWARD_UNROLL) {
+    a.iters = opts->iters;
+    a.trunc_steps = opts->trunc_steps;
+    a.rec = (char*)workspace + rec_offset(g);
+    a.rec_stride = rec_stride(g, opts->iters);
+    a.rec_nmax = g->impl.nmax;
+    if (g->impl.h.kind == DNLS_SE3) return launch_persistent(k_unroll<3>, g, opts, a, st, false);
+    return launch_persistent(k_unroll<2>, g, opts, a, st, false);
+  }
   if (g->impl.h.kind == DNLS_SE3) return launch_persistent(k_backward<3>, g, opts, a, st, false);
   return launch_persistent(k_backward<2>, g, opts, a, st, false);
 }

@@ -22,7 +22,7 @@ PROBLEM_OK, PROBLEM_NOT_CONVERGED, PROBLEM_NOT_SPD, PROBLEM_NAN = range(4)
 SE2, SE3 = 2, 3
 GN, LM, DOGLEG = 0, 1, 2
 FP64, MIXED_FP32 = 0, 1
-IMPLICIT_EXACT, IMPLICIT_GN, BACKWARD_DLM = 0, 1, 2
+IMPLICIT_EXACT, IMPLICIT_GN, BACKWARD_DLM, BACKWARD_UNROLL = 0, 1, 2, 3
 ORDER_MIN_DEGREE, ORDER_NATURAL = 0, 1
 
 
@@ -30,7 +30,8 @@ class SolverOpts(ctypes.Structure):
     _fields_ = [("algo", c_int32), ("iters", c_int32), ("precision", c_int32),
                 ("backward_mode", c_int32), ("refine_max", c_int32), ("threads", c_int32),
                 ("ctas_per_sm", c_int32), ("smem_factor", c_int32), ("lambda0", c_double),
-                ("tau", c_double), ("refine_tol", c_double), ("dlm_eps", c_double), ("radius0", c_double)]
+                ("tau", c_double), ("refine_tol", c_double), ("dlm_eps", c_double), ("radius0", c_double),
+                ("trunc_steps", c_int32), ("reserved", c_int32)]
 
 
 class GraphDesc(ctypes.Structure):

@@ -24,7 +24,7 @@ class Options:
     algo: str = "lm"                 # "gn" | "lm" | "dogleg"
     iters: int = 20
     precision: str = "mixed_fp32"    # "fp64" | "mixed_fp32"
-    backward_mode: str = "implicit"  # "implicit" (true Hessian) | "implicit_gn" | "dlm"
+    backward_mode: str = "implicit"  # "implicit" (true Hessian) | "implicit_gn" | "dlm" | "unroll"
     refine_max: int = 30
     lambda0: float = 1e-3
     tau: Optional[float] = None      # default: 1e-14 (fp64) / 1e-10 (mixed)
@@ -34,6 +34,7 @@ class Options:
     smem_factor: int = 1
     dlm_eps: float = 1e-2            # backward_mode "dlm": finite-difference scale eps
     radius0: float = 1.0             # algo "dogleg": initial trust radius
+    trunc_steps: int = 0             # backward_mode "unroll": last k iterations only (0 = all)
 
     def c(self) -> _d.SolverOpts:
         fp64 = self.precision == "fp64"
@@ -44,7 +45,8 @@ class Options:
         o.algo = algos[self.algo]
         o.iters = int(self.iters)
         o.precision = _d.FP64 if fp64 else _d.MIXED_FP32
-        modes = {"implicit": _d.IMPLICIT_EXACT, "implicit_gn": _d.IMPLICIT_GN, "dlm": _d.BACKWARD_DLM}
+        modes = {"implicit": _d.IMPLICIT_EXACT, "implicit_gn": _d.IMPLICIT_GN, "dlm": _d.BACKWARD_DLM,
+                 "unroll": _d.BACKWARD_UNROLL}
         if self.backward_mode not in modes:
             raise ValueError(f"unknown backward_mode {self.backward_mode!r}")
         o.backward_mode = modes[self.backward_mode]
@@ -57,6 +59,7 @@ class Options:
         o.refine_tol = float(self.refine_tol if self.refine_tol is not None else (1e-11 if fp64 else 1e-7))
         o.dlm_eps = float(self.dlm_eps)
         o.radius0 = float(self.radius0)
+        o.trunc_steps = int(self.trunc_steps)
         return o
 
 
