@@ -89,7 +89,7 @@ struct BAArgs {
 struct RedView {
   int N, nnzL, nlev;
   const int32_t *perm, *iperm, *colptr, *rows, *rowptr, *rowent, *lvlptr, *lvlcols, *tgtptr, *tgt,
-      *gptr, *gsrc, *panptr, *pan, *lsrc, *glanes, *slanes;
+      *gptr, *gsrc, *panptr, *pan, *lsrc, *glanes, *slanes, *gsplit;
   double *H, *L, *Linv, *dx, *tmp;
   __device__ void init(const BAArgs& a, int b) {
     const ProbMeta* m = a.d.rmeta + b;
@@ -113,6 +113,7 @@ struct RedView {
     pan = s + m->o_pan;
     lsrc = s + m->o_lsrc;
     glanes = s + m->o_glanes;
+    gsplit = s + m->o_gsplit;
     slanes = s + m->o_slanes;
     char* w = a.ws + m->ws;
     H = (double*)(w + m->w_H);

@@ -145,6 +145,41 @@ __device__ __forceinline__ void diag_rows(F& p, double* L, int c0, int c1, int* 
   }
 }
 
+// Subtracts from each target block of level lv the products of its source pairs: mode 0 all
+// pairs, 1 the early ones (gptr .. gsplit), 2 the late ones (gsplit .. next gptr).  Each output
+// element is summed by LN = glanes[lv] adjacent lanes and combined by a fixed-order shuffle
+// reduction.  Runs on threads tid0 .. blockDim-1 (tid0 a multiple of 32, so every warp taking
+// part is whole).
+template <int D, class F>
+__device__ __forceinline__ void gather_level(F& p, double* L, int lv, int mode, int tid0) {
+  constexpr int BS = D * D;
+  const int t0 = p.tgtptr[lv], t1 = p.tgtptr[lv + 1];
+  const int LN = p.glanes[lv];
+  const int n1 = (t1 - t0) * BS * LN;
+  const int nthr = blockDim.x - tid0, tid = threadIdx.x - tid0;
+  for (int base = 0; base < n1; base += nthr) {
+    const int it = base + tid;
+    double acc = 0.0;
+    int q = 0, el = 0, s0 = 0, s1 = 0;
+    if (it < n1) {
+      const int e2 = it / LN, lane = it % LN;
+      q = t0 + e2 / BS;
+      el = e2 % BS;
+      const int a = el / D, b = el % D;
+      s0 = mode == 2 ? p.gsplit[q] : p.gptr[q];
+      s1 = mode == 1 ? p.gsplit[q] : p.gptr[q + 1];
+      for (int s = s0 + lane; s < s1; s += LN) {
+        const double* X = L + (int64_t)p.gsrc[2 * s] * BS + a * D;
+        const double* Y = L + (int64_t)p.gsrc[2 * s + 1] * BS + b * D;
+#pragma unroll
+        for (int mm = 0; mm < D; ++mm) acc = fma(X[mm], Y[mm], acc);
+      }
+    }
+    if (LN > 1) acc = lane_sum(acc, LN);
+    if (it < n1 && (it % LN) == 0 && s1 > s0) L[(int64_t)p.tgt[q] * BS + el] -= acc;
+  }
+}
+
 // L <- H + lam * diag(max(diag H, floor)) + shift * I, then left-looking block Cholesky level
 // by level.
 // Returns false (uniformly across the CTA) if a pivot is not positive or not finite.  A failing
@@ -168,46 +203,24 @@ __device__ bool block_factor(F& p, double lam, int* sflag, int gen, double shift
     L[(int64_t)t * BS + el] = v;
   }
   __syncthreads();
+  // Level by level: (1) gather, (2) diagonal factors, (3) panels.  On a narrow level (at most
+  // 32/D columns) warp 0 alone factors the diagonal blocks, and the other warps meanwhile
+  // subtract the next level's "early" source pairs (columns two or more levels below, already
+  // final); that level's gather then only adds the pairs from the level just factored.
+  bool early_done = false;
   for (int lv = 0; lv < p.nlev; ++lv) {
-    // (1) subtract the products of already-factored descendant columns; each output element
-    //     is summed by `LN` adjacent lanes (every LN-th source pair; LN chosen per level by the
-    //     symbolic analysis) and combined by a fixed-order shuffle reduction
-    const int t0 = p.tgtptr[lv], t1 = p.tgtptr[lv + 1];
-    const int LN = p.glanes[lv];
-    const int n1 = (t1 - t0) * BS * LN;
-    for (int base = 0; base < n1; base += blockDim.x) {
-      const int it = base + threadIdx.x;
-      double acc = 0.0;
-      int q = 0, el = 0, s0 = 0, s1 = 0;
-      if (it < n1) {
-        const int e2 = it / LN, lane = it % LN;
-        q = t0 + e2 / BS;
-        el = e2 % BS;
-        const int a = el / D, b = el % D;
-        s0 = p.gptr[q];
-        s1 = p.gptr[q + 1];
-        for (int s = s0 + lane; s < s1; s += LN) {
-          const double* X = L + (int64_t)p.gsrc[2 * s] * BS + a * D;
-          const double* Y = L + (int64_t)p.gsrc[2 * s + 1] * BS + b * D;
-#pragma unroll
-          for (int mm = 0; mm < D; ++mm) acc = fma(X[mm], Y[mm], acc);
-        }
-      }
-      if (LN > 1) acc = lane_sum(acc, LN);
-      if (it < n1 && (it % LN) == 0 && s1 > s0) L[(int64_t)p.tgt[q] * BS + el] -= acc;
-    }
+    gather_level<D>(p, L, lv, early_done ? 2 : 0, 0);
     __syncthreads();
-    // (2) dense Cholesky of each diagonal block of the level and the inverse of its factor.
-    //     A warp issues one FP64 instruction per several dozen cycles whatever its active-lane
-    //     count, so narrow levels (at most 32/D columns, the upper part of the elimination tree)
-    //     run with D lanes per column in warp 0 (row-parallel, right-looking, pivots shared by
-    //     shuffles), which cuts the instructions on that warp's critical path; wider levels
-    //     take one thread per column.
     const int c0 = p.lvlptr[lv], c1 = p.lvlptr[lv + 1];
-    if (c1 - c0 <= 32 / D) {
-      if (threadIdx.x < 32) diag_rows<D>(p, L, c0, c1, sflag, gen);
+    if (c1 - c0 <= 32 / D && blockDim.x >= 64) {
+      if (threadIdx.x < 32)
+        diag_rows<D>(p, L, c0, c1, sflag, gen);
+      else if (lv + 1 < p.nlev)
+        gather_level<D>(p, L, lv + 1, 1, 32);
+      early_done = lv + 1 < p.nlev;
     } else {
       for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) diag_thread<D>(p, L, p.lvlcols[c], sflag, gen);
+      early_done = false;
     }
     __syncthreads();
     if (*sflag == gen) return false;

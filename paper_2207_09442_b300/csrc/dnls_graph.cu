@@ -71,7 +71,7 @@ struct Prob {
   static constexpr int D = Group<KIND>::DOF, PW = Group<KIND>::PW, BS = D * D, JW = 2 * BS + D;
   int N, E, npair, nnzL, nlev;
   const int32_t *perm, *iperm, *colptr, *rows, *rowptr, *rowent, *lvlptr, *lvlcols, *tgtptr, *tgt,
-      *gptr, *gsrc, *panptr, *pan, *incptr, *inc, *pairptr, *pairs, *pairtgt, *lsrc, *glanes, *slanes;
+      *gptr, *gsrc, *panptr, *pan, *incptr, *inc, *pairptr, *pairs, *pairtgt, *lsrc, *glanes, *slanes, *gsplit;
   const int32_t *ei, *ej;
   const double *meas, *wdiag;
   const float* logw;
@@ -165,6 +165,7 @@ struct Prob {
     pairtgt = s + m->o_pairtgt;
     lsrc = s + m->o_lsrc;
     glanes = s + m->o_glanes;
+    gsplit = s + m->o_gsplit;
     slanes = s + m->o_slanes;
   }
 
@@ -676,7 +677,7 @@ __device__ __forceinline__ int next_problem(const KArgs& a, int* slot) {
 }
 
 template <int KIND, class P>
-__global__ void __launch_bounds__(256) k_forward(KArgs a) {
+__global__ void __launch_bounds__(256, 2) k_forward(KArgs a) {
   __shared__ double red[256];
   __shared__ int sflag, slot;
   for (;;) {
@@ -691,7 +692,7 @@ __global__ void __launch_bounds__(256) k_forward(KArgs a) {
 // the dogleg forward as its own kernel, so that the GN/LM kernel's register allocation is not
 // shaped by the trust-region code
 template <int KIND, class P>
-__global__ void __launch_bounds__(256) k_forward_dogleg(KArgs a) {
+__global__ void __launch_bounds__(256, 2) k_forward_dogleg(KArgs a) {
   __shared__ double red[256];
   __shared__ int sflag, slot;
   for (;;) {
@@ -1347,7 +1348,7 @@ __global__ void __launch_bounds__(256) k_unroll(KArgs a) {
 }
 
 template <int KIND>
-__global__ void __launch_bounds__(256) k_backward(KArgs a) {
+__global__ void __launch_bounds__(256, 2) k_backward(KArgs a) {
   __shared__ double red[256];
   __shared__ int sflag, slot;
   for (;;) {

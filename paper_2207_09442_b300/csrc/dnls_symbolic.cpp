@@ -169,9 +169,11 @@ int build_graph_host(int kind, int B, const int64_t* pose_offsets, const int64_t
     for (int k = 0; k < N; ++k) bylev[lev[k]].push_back(k);
     // gather lists: per target block of column k, the (L(r,j), L(k,j)) pairs, j in rowl[k]
     std::vector<std::vector<std::vector<int>>> gl(N);  // gl[k][t] flat pairs, t=0 diag, 1+a off
+    std::vector<std::vector<std::vector<int>>> glv(N);  // level of each pair's source column
     int64_t n_upd = 0;
     for (int k = 0; k < N; ++k) {
       gl[k].assign(1 + rows[k].size(), {});
+      glv[k].assign(1 + rows[k].size(), {});
       for (auto& pr : rowl[k]) {
         const int bkj = pr.first, j = pr.second;
         auto it = std::lower_bound(rows[j].begin(), rows[j].end(), k);
@@ -188,6 +190,7 @@ int build_graph_host(int kind, int B, const int64_t* pose_offsets, const int64_t
           }
           gl[k][t].push_back(a_src);
           gl[k][t].push_back(bkj);
+          glv[k][t].push_back(lev[j]);
           ++n_upd;
         }
       }
@@ -271,7 +274,7 @@ int build_graph_host(int kind, int B, const int64_t* pose_offsets, const int64_t
     m.o_lvlcols = mark();
     for (int l = 0; l < nlev; ++l) blob.insert(blob.end(), bylev[l].begin(), bylev[l].end());
     // targets by level with their gather ranges
-    std::vector<int> tgt, gptr, gsrc, tgtptr, pan, panptr;
+    std::vector<int> tgt, gptr, gsrc, tgtptr, pan, panptr, gsplit;
     for (int l = 0; l < nlev; ++l) {
       tgtptr.push_back((int)tgt.size());
       panptr.push_back((int)pan.size() / 2);
@@ -290,7 +293,19 @@ int build_graph_host(int kind, int B, const int64_t* pose_offsets, const int64_t
       for (const LT& e : lt) {
         tgt.push_back(e.target);
         gptr.push_back((int)gsrc.size() / 2);
-        gsrc.insert(gsrc.end(), gl[e.k][e.t].begin(), gl[e.k][e.t].end());
+        // "early" pairs first (source column two or more levels below, final once the level
+        // below this one has started), then the pairs from the level just below; the order of
+        // pairs within each part is kept
+        const std::vector<int>& pr = gl[e.k][e.t];
+        const std::vector<int>& pl = glv[e.k][e.t];
+        for (int late = 0; late < 2; ++late) {
+          for (int q = 0; q < (int)pl.size(); ++q)
+            if ((pl[q] >= l - 1) == (late == 1)) {
+              gsrc.push_back(pr[2 * q]);
+              gsrc.push_back(pr[2 * q + 1]);
+            }
+          if (late == 0) gsplit.push_back((int)gsrc.size() / 2);
+        }
       }
       for (int k : bylev[l]) {
         for (int a = 0; a < (int)rows[k].size(); ++a) {
@@ -310,6 +325,8 @@ int build_graph_host(int kind, int B, const int64_t* pose_offsets, const int64_t
     blob.insert(blob.end(), gptr.begin(), gptr.end());
     m.o_gsrc = mark();
     blob.insert(blob.end(), gsrc.begin(), gsrc.end());
+    m.o_gsplit = mark();
+    blob.insert(blob.end(), gsplit.begin(), gsplit.end());
     m.o_panptr = mark();
     blob.insert(blob.end(), panptr.begin(), panptr.end());
     m.o_pan = mark();
