@@ -41,7 +41,7 @@ struct BAState {
   double lam, S, Sc, lam_fact, rel, vnorm, rz;
   int32_t active, need_lin, bad, accepted_last;
   int32_t iters, accepted, status, factor_ok;
-  int32_t refine_steps, pad[3];
+  int32_t refine_steps, fact_flag, pad[2];  // fact_flag: failed-pivot flag of the cluster factor
 };
 
 struct BADev {
@@ -402,12 +402,32 @@ __global__ void k_ba_schur(BAArgs a, double lam_override) {
 
 // one CTA per problem: factor the reduced system (already damped) and solve for delta_c;
 // with `solve_only`, solve with the cached factor for rhs rc (backward) into dc.
+// The reduced camera system is complete (every camera pair shares points), so its factorization
+// is dense-structured work of 384^3/3 FP64 flops per problem: one CTA would run it at one SM's
+// FP64 rate while most SMs idle.  It runs on a cluster of kRedCluster CTAs per problem instead.
+constexpr int kRedCluster = 4;
+
+__global__ void __launch_bounds__(256) k_ba_reduced_factor(BAArgs a) {
+  const int b = blockIdx.x / kRedCluster, rank = blockIdx.x % kRedCluster;
+  BAState& s = a.st[b];
+  if (!s.active) return;  // the same for every CTA of the cluster
+  RedView p;
+  p.init(a, b);
+  if (rank == 0 && threadIdx.x == 0) s.fact_flag = -1;  // published by the first cluster barrier
+  const bool ok = block_factor_cluster<6>(p, 0.0, rank, kRedCluster, &s.fact_flag, 0);
+  if (rank == 0 && threadIdx.x == 0) {
+    s.factor_ok = ok ? 1 : 0;
+    if (!ok) s.bad = 1;
+  }
+}
+
 __global__ void __launch_bounds__(256) k_ba_reduced(BAArgs a, int solve_only, const double* rhs,
                                                     double* out, int accumulate) {
   __shared__ int sflag;
   const int b = blockIdx.x;
   BAState& s = a.st[b];
   if (!s.active) return;
+  if (solve_only == 2 && !s.factor_ok) return;  // right after a failed cluster factorization
   RedView p;
   p.init(a, b);
   if (threadIdx.x == 0) sflag = -1;
@@ -1133,6 +1153,24 @@ BAArgs ba_args(const dnls_ba* h, const dnls_solver_opts* o, const dnls_ba_inputs
 
 inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
 
+// the cluster factorization of every active problem's reduced system (errors surface through
+// cudaGetLastError at the end of the calling entry point)
+void launch_reduced_factor(const BAHost& H, const BAArgs& a, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(H.B * kRedCluster));
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kRedCluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k_ba_reduced_factor, a);
+}
+
 // one LM iteration's linearise -> eliminate -> factor -> solve chain; lam_override >= 0 replaces
 // lambda (the backward's undamped refactorization)
 void ba_eliminate_and_factor(const dnls_ba* h, BAArgs& a, cudaStream_t st, double lam_override) {
@@ -1144,7 +1182,8 @@ void ba_eliminate_and_factor(const dnls_ba* h, BAArgs& a, cudaStream_t st, doubl
   k_ba_points<<<nblk(H.P, 128), 128, 0, st>>>(a, lam_override);
   k_ba_cameras<<<nblk((int64_t)H.C * 32, 256), 256, 0, st>>>(a);  // one warp per camera
   k_ba_schur<<<nblk(H.red.meta.empty() ? 1 : (int64_t)H.tgt_cam.size() * 6, 128), 128, 0, st>>>(a, lam_override);
-  k_ba_reduced<<<H.B, 256, 0, st>>>(a, 0, a.bc, a.dc, 0);
+  launch_reduced_factor(H, a, st);
+  k_ba_reduced<<<H.B, 256, 0, st>>>(a, 2, a.bc, a.dc, 0);
 }
 
 }  // namespace

@@ -148,15 +148,14 @@ __device__ __forceinline__ void diag_rows(F& p, double* L, int c0, int c1, int* 
 // Subtracts from each target block of level lv the products of its source pairs: mode 0 all
 // pairs, 1 the early ones (gptr .. gsplit), 2 the late ones (gsplit .. next gptr).  Each output
 // element is summed by LN = glanes[lv] adjacent lanes and combined by a fixed-order shuffle
-// reduction.  Runs on threads tid0 .. blockDim-1 (tid0 a multiple of 32, so every warp taking
-// part is whole).
+// reduction.  Runs on the team threads tid = 0 .. nthr-1 (whole warps: tid and nthr advance
+// warp by warp, so every warp taking part is whole).
 template <int D, class F>
-__device__ __forceinline__ void gather_level(F& p, double* L, int lv, int mode, int tid0) {
+__device__ __forceinline__ void gather_level(F& p, double* L, int lv, int mode, int tid, int nthr) {
   constexpr int BS = D * D;
   const int t0 = p.tgtptr[lv], t1 = p.tgtptr[lv + 1];
   const int LN = p.glanes[lv];
   const int n1 = (t1 - t0) * BS * LN;
-  const int nthr = blockDim.x - tid0, tid = threadIdx.x - tid0;
   for (int base = 0; base < n1; base += nthr) {
     const int it = base + tid;
     double acc = 0.0;
@@ -209,14 +208,14 @@ __device__ bool block_factor(F& p, double lam, int* sflag, int gen, double shift
   // final); that level's gather then only adds the pairs from the level just factored.
   bool early_done = false;
   for (int lv = 0; lv < p.nlev; ++lv) {
-    gather_level<D>(p, L, lv, early_done ? 2 : 0, 0);
+    gather_level<D>(p, L, lv, early_done ? 2 : 0, threadIdx.x, blockDim.x);
     __syncthreads();
     const int c0 = p.lvlptr[lv], c1 = p.lvlptr[lv + 1];
     if (c1 - c0 <= 32 / D && blockDim.x >= 64) {
       if (threadIdx.x < 32)
         diag_rows<D>(p, L, c0, c1, sflag, gen);
       else if (lv + 1 < p.nlev)
-        gather_level<D>(p, L, lv + 1, 1, 32);
+        gather_level<D>(p, L, lv + 1, 1, threadIdx.x - 32, blockDim.x - 32);
       early_done = lv + 1 < p.nlev;
     } else {
       for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) diag_thread<D>(p, L, p.lvlcols[c], sflag, gen);
@@ -244,6 +243,81 @@ __device__ bool block_factor(F& p, double lam, int* sflag, int gen, double shift
       for (int jj = 0; jj < D; ++jj) X[jj] = o[jj];
     }
     __syncthreads();
+  }
+  return true;
+}
+
+// ----------------------------------------------------------------------------- cluster factor
+// Thread-block cluster barrier with release / acquire semantics at cluster scope: every write
+// (shared or global) of every thread of the cluster before it is visible to every thread after it.
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+  asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+
+// block_factor by the nranks CTAs of a thread-block cluster (rank = the CTA's rank in it), for a
+// factor too large for one SM's FP64 rate: the same level schedule and the same sums in the same
+// order, with the gather, panel and wide-level items spread over all the cluster's threads, the
+// narrow-level diagonal blocks factored by warp 0 of rank 0 while every other warp of the cluster
+// takes the next level's early gather pairs, and cluster barriers between the phases.  The
+// factor lives in global memory; `gflag` (global, one per problem, set to -1 by the caller
+// before the launch) records a failed pivot as for block_factor.  Returns the same value in
+// every thread of the cluster.
+template <int D, class F>
+__device__ bool block_factor_cluster(F& p, double lam, int rank, int nranks, int* gflag, int gen) {
+  constexpr int BS = D * D;
+  double* L = p.L;
+  const int tid = rank * blockDim.x + threadIdx.x, nthr = nranks * blockDim.x;
+  const int nb = p.N + p.nnzL;
+  for (int it = tid; it < nb * BS; it += nthr) {
+    const int t = it / BS, el = it % BS;
+    double v;
+    if (t < p.N) {
+      v = p.H[(int64_t)t * BS + el];
+      if (el / D == el % D) v += lam * fmax(v, kDiagFloor);
+    } else {
+      const int src = p.lsrc[t - p.N];
+      v = src >= 0 ? p.H[(int64_t)(p.N + src) * BS + el] : 0.0;
+    }
+    L[(int64_t)t * BS + el] = v;
+  }
+  cluster_sync_all();
+  bool early_done = false;
+  for (int lv = 0; lv < p.nlev; ++lv) {
+    gather_level<D>(p, L, lv, early_done ? 2 : 0, tid, nthr);
+    cluster_sync_all();
+    const int c0 = p.lvlptr[lv], c1 = p.lvlptr[lv + 1];
+    if (c1 - c0 <= 32 / D) {
+      if (tid < 32)
+        diag_rows<D>(p, L, c0, c1, gflag, gen);
+      else if (lv + 1 < p.nlev)
+        gather_level<D>(p, L, lv + 1, 1, tid - 32, nthr - 32);
+      early_done = lv + 1 < p.nlev;
+    } else {
+      for (int c = c0 + tid; c < c1; c += nthr) diag_thread<D>(p, L, p.lvlcols[c], gflag, gen);
+      early_done = false;
+    }
+    cluster_sync_all();
+    if (*(volatile int*)gflag == gen) return false;
+    const int q0 = p.panptr[lv], q1 = p.panptr[lv + 1];
+    for (int it = tid; it < (q1 - q0) * D; it += nthr) {
+      const int q = q0 + it / D, row = it % D;
+      double* X = L + (int64_t)p.pan[2 * q] * BS + row * D;
+      const double* Ik = p.Linv + (int64_t)p.pan[2 * q + 1] * BS;
+      double a[D], o[D];
+#pragma unroll
+      for (int mm = 0; mm < D; ++mm) a[mm] = X[mm];
+#pragma unroll
+      for (int jj = 0; jj < D; ++jj) {
+        double s2 = 0.0;
+#pragma unroll
+        for (int mm = 0; mm <= jj; ++mm) s2 = fma(a[mm], Ik[jj * D + mm], s2);
+        o[jj] = s2;
+      }
+#pragma unroll
+      for (int jj = 0; jj < D; ++jj) X[jj] = o[jj];
+    }
+    cluster_sync_all();
   }
   return true;
 }
