@@ -505,8 +505,9 @@ def run_pose_graphs(args, rank, world, local, dist, out):
 # ----------------------------------------------------------------------------- bundle adjustment
 def ba_launches(iters: int, refine_max: int) -> int:
     """Kernels one bundle-adjustment forward + backward launches (the launch sequence of the
-    library's BA entry points: 6 + 10 per iteration forward, 16 + 8 per PCG step backward)."""
-    return 6 + 10 * iters + 16 + 8 * refine_max
+    library's BA entry points: 6 + 11 per iteration forward, 17 + 8 per PCG step backward; the
+    reduced-system factorization is one cluster launch)."""
+    return 6 + 11 * iters + 17 + 8 * refine_max
 
 
 def run_ba(args, rank, world, local, dist, out):
