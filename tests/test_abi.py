@@ -57,3 +57,18 @@ def test_null_arguments(lib):
     assert lib.dnls_project_grad(dnls.SE3, 0, None, None, None, None) == dnls.OK  # empty is fine
     f = ctypes.c_double()
     assert lib.dnls_probe_fp64_peak(0, None, ctypes.byref(f)) == dnls.ERR_ARG
+
+
+def test_create_rejects_empty_batch_and_empty_problem(lib):
+    """An empty batch, or a problem with no poses, is refused by the host validation."""
+    def create(po, eo, ei, ej):
+        po, eo = np.array(po, np.int64), np.array(eo, np.int64)
+        ei, ej = np.array(ei, np.int32), np.array(ej, np.int32)
+        d = dnls.GraphDesc(dnls.SE3, len(po) - 1, po.ctypes.data, eo.ctypes.data, ei.ctypes.data,
+                           ej.ctypes.data, 0)
+        h = ctypes.c_void_p()
+        return lib.dnls_graph_create(ctypes.byref(d), ctypes.byref(h)), h
+    rc, h = create([0], [0], [0], [0])
+    assert rc == dnls.ERR_ARG and not h.value
+    rc, h = create([0, 0, 2], [0, 0, 2], [0, 0], [1, -1])
+    assert rc == dnls.ERR_ARG and not h.value
