@@ -451,6 +451,73 @@ __global__ void __launch_bounds__(256) k_ba_reduced(BAArgs a, int solve_only, co
   }
 }
 
+// Solve with the cached reduced factor when every elimination level holds one column (the
+// complete camera graphs of dense BA): right-looking, column by column, so that each step is one
+// 6x6 diagonal product followed by the parallel update of every row it touches (no row is
+// updated by two columns at once, as there is one column per step).
+//   forward  L y = b:   y_k = L_kk^-1 b_k;        b_i -= L_ik y_k   (blocks below the diagonal)
+//   backward L^T x = y: x_k = L_kk^-T y_k;        y_j -= L_kj^T x_k (blocks left of the diagonal)
+// rhs / out as for k_ba_reduced (solve_only 1: every active problem; 2: skip a failed factor).
+__global__ void __launch_bounds__(256) k_ba_solve_chain(BAArgs a, int solve_only, const double* rhs,
+                                                        double* out) {
+  __shared__ double xk[6];
+  const int b = blockIdx.x;
+  BAState& s = a.st[b];
+  if (!s.active) return;
+  if (solve_only == 2 && !s.factor_ok) return;
+  RedView p;
+  p.init(a, b);
+  const int64_t c0 = a.d.cam_off[b];
+  double* x = p.dx;
+  for (int k = threadIdx.x; k < p.N * 6; k += blockDim.x) x[k] = rhs[(c0 + p.perm[k / 6]) * 6 + k % 6];
+  __syncthreads();
+  for (int lv = 0; lv < p.nlev; ++lv) {
+    const int k = p.lvlcols[p.lvlptr[lv]];
+    if (threadIdx.x < 6) {
+      const int i = threadIdx.x;
+      const double* I = p.Linv + (int64_t)k * 36 + i * 6;
+      double acc = 0.0;
+      for (int m = 0; m <= i; ++m) acc = fma(I[m], x[k * 6 + m], acc);
+      xk[i] = acc;
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) x[k * 6 + threadIdx.x] = xk[threadIdx.x];
+    const int q0 = p.colptr[k], cnt = p.colptr[k + 1] - q0;
+    for (int it = threadIdx.x; it < cnt * 6; it += blockDim.x) {
+      const int q = it / 6, r = it % 6;
+      const double* B = p.L + (int64_t)(p.N + q0 + q) * 36 + r * 6;
+      double acc = 0.0;
+#pragma unroll
+      for (int m = 0; m < 6; ++m) acc = fma(B[m], xk[m], acc);
+      x[p.rows[q0 + q] * 6 + r] -= acc;
+    }
+    __syncthreads();
+  }
+  for (int lv = p.nlev - 1; lv >= 0; --lv) {
+    const int k = p.lvlcols[p.lvlptr[lv]];
+    if (threadIdx.x < 6) {
+      const int i = threadIdx.x;
+      const double* I = p.Linv + (int64_t)k * 36;
+      double acc = 0.0;
+      for (int m = i; m < 6; ++m) acc = fma(I[m * 6 + i], x[k * 6 + m], acc);
+      xk[i] = acc;
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) x[k * 6 + threadIdx.x] = xk[threadIdx.x];
+    const int e0 = p.rowptr[k], cnt = p.rowptr[k + 1] - e0;
+    for (int it = threadIdx.x; it < cnt * 6; it += blockDim.x) {
+      const int q = it / 6, c = it % 6;
+      const double* B = p.L + (int64_t)p.rowent[2 * (e0 + q)] * 36 + c;  // block L(k, j), column c
+      double acc = 0.0;
+#pragma unroll
+      for (int m = 0; m < 6; ++m) acc = fma(B[m * 6], xk[m], acc);
+      x[p.rowent[2 * (e0 + q) + 1] * 6 + c] -= acc;
+    }
+    __syncthreads();
+  }
+  for (int k = threadIdx.x; k < p.N * 6; k += blockDim.x) out[(c0 + p.perm[k / 6]) * 6 + k % 6] = x[k];
+}
+
 // candidate cameras T Exp(delta_c) and points p + delta_p, delta_p = -u_p - H_pp^-1 sum H_cp^T dc
 __global__ void k_ba_update(BAArgs a) {
   const int64_t it = gtid();
@@ -892,6 +959,7 @@ struct BAHost {
   int64_t w_J, w_Y, w_Hcp, w_Hppi, w_up, w_gp, w_Hcc, w_gc, w_bc, w_dc, w_ccam, w_cpt, w_cost,
       w_xc, w_xp, w_rc, w_rp, w_vc, w_vp, w_eb, w_ebq, w_st, w_solc, w_solp, w_zc, w_zp, w_hc, w_hp;
   int64_t ws_bytes = 0;
+  bool red_chain = false;  // every elimination level of every reduced system holds one column
 };
 
 struct BAHandle {
@@ -997,6 +1065,8 @@ int build_ba_host(const dnls_ba_desc* desc, BAHost& H) {
   int rc = build_graph_host(DNLS_SE3, B, H.cam_off.data(), red_edge_off.data(), red_ei.data(),
                             red_ej.data(), DNLS_ORDER_MIN_DEGREE, &H.red);
   if (rc != DNLS_OK) return rc;
+  H.red_chain = true;
+  for (const ProbMeta& m : H.red.meta) H.red_chain = H.red_chain && m.nlev == m.N;
   // Schur gather targets: diagonal block of every camera, one block per camera pair
   H.tgt_ptr.assign(1, 0);
   for (int b = 0; b < B; ++b) {
@@ -1171,6 +1241,14 @@ void launch_reduced_factor(const BAHost& H, const BAArgs& a, cudaStream_t st) {
   cudaLaunchKernelEx(&cfg, k_ba_reduced_factor, a);
 }
 
+// dc = (reduced factor)^-1 bc for every active problem
+void reduced_solve(const BAHost& H, const BAArgs& a, cudaStream_t st, int mode) {
+  if (H.red_chain)
+    k_ba_solve_chain<<<H.B, 256, 0, st>>>(a, mode, a.bc, a.dc);
+  else
+    k_ba_reduced<<<H.B, 256, 0, st>>>(a, mode, a.bc, a.dc, 0);
+}
+
 // one LM iteration's linearise -> eliminate -> factor -> solve chain; lam_override >= 0 replaces
 // lambda (the backward's undamped refactorization)
 void ba_eliminate_and_factor(const dnls_ba* h, BAArgs& a, cudaStream_t st, double lam_override) {
@@ -1183,7 +1261,7 @@ void ba_eliminate_and_factor(const dnls_ba* h, BAArgs& a, cudaStream_t st, doubl
   k_ba_cameras<<<nblk((int64_t)H.C * 32, 256), 256, 0, st>>>(a);  // one warp per camera
   k_ba_schur<<<nblk(H.red.meta.empty() ? 1 : (int64_t)H.tgt_cam.size() * 6, 128), 128, 0, st>>>(a, lam_override);
   launch_reduced_factor(H, a, st);
-  k_ba_reduced<<<H.B, 256, 0, st>>>(a, 2, a.bc, a.dc, 0);
+  reduced_solve(H, a, st, 2);
 }
 
 }  // namespace
@@ -1323,7 +1401,7 @@ dnls_status dnls_ba_backward(const dnls_ba* h, const dnls_solver_opts* opts, con
   // z = M^-1 r (block elimination with the cached Schur factorization): camera side into dc
   auto precondition = [&]() {
     k_bap_cams<<<nblk((int64_t)H.C * 32, 256), 256, 0, st>>>(a);
-    k_ba_reduced<<<H.B, 256, 0, st>>>(a, 1, a.bc, a.dc, 0);
+    reduced_solve(H, a, st, 1);
     k_bap_pts<<<nblk(H.P, 128), 128, 0, st>>>(a);
   };
   precondition();
