@@ -391,9 +391,10 @@ __global__ void k_ba_schur(BAArgs a, double lam_override) {
     const int64_t o1 = a.d.tgt_pairs[2 * q], o2 = a.d.tgt_pairs[2 * q + 1];
     const double* Yr = a.Y + o1 * 18 + 3 * i;
     const double* Hc = a.Hcp + o2 * 18;
-    const double y0 = Yr[0], y1 = Yr[1], y2 = Yr[2];
+    const double y0 = -Yr[0], y1 = -Yr[1], y2 = -Yr[2];
 #pragma unroll
-    for (int j = 0; j < 6; ++j) acc[j] -= y0 * Hc[3 * j] + y1 * Hc[3 * j + 1] + y2 * Hc[3 * j + 2];
+    for (int j = 0; j < 6; ++j)
+      acc[j] = fma(y2, Hc[3 * j + 2], fma(y1, Hc[3 * j + 1], fma(y0, Hc[3 * j], acc[j])));
   }
   double* out = (double*)(a.ws + a.d.tgt_off[t]) + 6 * i;
 #pragma unroll
@@ -1107,6 +1108,33 @@ int build_ba_host(const dnls_ba_desc* desc, BAHost& H) {
       H.tgt_pairs.insert(H.tgt_pairs.end(), l.begin(), l.end());
       H.tgt_ptr.push_back((int32_t)(H.tgt_pairs.size() / 2));
     }
+  }
+  // targets with the most pairs first (over the whole batch), so that the threads of a warp
+  // run gather loops of similar length (a camera's diagonal block gathers every pair of its
+  // points' observations, an off-diagonal block only the points the two cameras share); each
+  // target's list and output block are unchanged
+  {
+    const int64_t T = (int64_t)H.tgt_cam.size();
+    std::vector<int64_t> ord(T);
+    for (int64_t t = 0; t < T; ++t) ord[t] = t;
+    std::stable_sort(ord.begin(), ord.end(), [&](int64_t x, int64_t y) {
+      return H.tgt_ptr[x + 1] - H.tgt_ptr[x] > H.tgt_ptr[y + 1] - H.tgt_ptr[y];
+    });
+    std::vector<int32_t> ptr(1, 0), pairs, cam, prob;
+    std::vector<int64_t> toff;
+    for (int64_t t : ord) {
+      pairs.insert(pairs.end(), H.tgt_pairs.begin() + 2 * (int64_t)H.tgt_ptr[t],
+                   H.tgt_pairs.begin() + 2 * (int64_t)H.tgt_ptr[t + 1]);
+      ptr.push_back((int32_t)(pairs.size() / 2));
+      cam.push_back(H.tgt_cam[t]);
+      prob.push_back(H.tgt_prob[t]);
+      toff.push_back(H.tgt_off[t]);
+    }
+    H.tgt_ptr.swap(ptr);
+    H.tgt_pairs.swap(pairs);
+    H.tgt_cam.swap(cam);
+    H.tgt_prob.swap(prob);
+    H.tgt_off.swap(toff);
   }
   // workspace: the reduced systems' regions, then the global BA arrays
   int64_t off = (H.red.ws_bytes + 255) & ~(int64_t)255;
