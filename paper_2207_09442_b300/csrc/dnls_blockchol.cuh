@@ -87,13 +87,14 @@ __device__ __forceinline__ void diag_thread(F& p, double* L, int k, int* sflag, 
 }
 
 // The same for the diagonal blocks of level columns c0..c1-1 (c1 - c0 <= 32 / D) by the 32
-// lanes of one warp: lane r of group g holds row r of column lvlcols[c0 + g]; step j shares the
-// pivot row's entries by shuffles and updates the trailing rows (the same subtractions in the
-// same order as the one-thread version); then lane r computes column r of the factor's inverse.
-// All 32 lanes must call (lanes beyond the last group work on an identity block and store
-// nothing).
+// lanes of one warp, in two parts.  diag_rows_factor: lane r of group g holds row r of column
+// lvlcols[c0 + g]; step j shares the pivot row's entries by shuffles and updates the trailing
+// rows (the same subtractions in the same order as the one-thread version); it stores L(k,k) and
+// the reciprocal pivots (the diagonal of L(k,k)^-1).  diag_rows_inverse (after the stores are
+// visible to the warp) reloads them and lane r computes column r of L(k,k)^-1.  All 32 lanes
+// must call both (lanes beyond the last group work on an identity block and store nothing).
 template <int D, class F>
-__device__ __forceinline__ void diag_rows(F& p, double* L, int c0, int c1, int* sflag, int gen) {
+__device__ __forceinline__ void diag_rows_factor(F& p, double* L, int c0, int c1, int* sflag, int gen) {
   constexpr int BS = D * D;
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
@@ -120,6 +121,30 @@ __device__ __forceinline__ void diag_rows(F& p, double* L, int c0, int c1, int* 
       if (m <= r) A[m] = fma(-lrj, lmj, A[m]);
     }
   }
+  if (act) {
+#pragma unroll
+    for (int m = 0; m < D; ++m) Lk[r * D + m] = m <= r ? A[m] : 0.0;
+    p.Linv[(int64_t)k * BS + r * D + r] = inv[r];
+    if (!ok) *sflag = gen;
+  }
+}
+
+template <int D, class F>
+__device__ __forceinline__ void diag_rows_inverse(F& p, const double* L, int c0, int c1) {
+  constexpr int BS = D * D;
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int grp = lane / D, r = lane - grp * D, base = grp * D;
+  const bool act = grp < c1 - c0;
+  const int k = act ? p.lvlcols[c0 + grp] : 0;
+  const double* Lk = L + (int64_t)k * BS;
+  const double* Ik = p.Linv + (int64_t)k * BS;
+  double A[D], inv[D];
+#pragma unroll
+  for (int m = 0; m < D; ++m) {
+    A[m] = act ? Lk[r * D + m] : (m == r ? 1.0 : 0.0);
+    inv[m] = act ? Ik[m * D + m] : 1.0;
+  }
   // column r of L^-1: I(r, r) = 1 / L(r, r); I(i, r) = -(sum_{m=r}^{i-1} L(i, m) I(m, r)) / L(i, i)
   double I[D];
 #pragma unroll
@@ -137,11 +162,40 @@ __device__ __forceinline__ void diag_rows(F& p, double* L, int c0, int c1, int* 
   }
   if (act) {
 #pragma unroll
-    for (int m = 0; m < D; ++m) {
-      Lk[r * D + m] = m <= r ? A[m] : 0.0;
-      p.Linv[(int64_t)k * BS + m * D + r] = I[m];
+    for (int m = 0; m < D; ++m) p.Linv[(int64_t)k * BS + m * D + r] = I[m];
+  }
+}
+
+template <int D, class F>
+__device__ __forceinline__ void diag_rows(F& p, double* L, int c0, int c1, int* sflag, int gen) {
+  diag_rows_factor<D>(p, L, c0, c1, sflag, gen);
+  __syncwarp();
+  diag_rows_inverse<D>(p, L, c0, c1);
+}
+
+// Off-diagonal blocks of level lv's columns by forward substitution with L(k,k) and its
+// reciprocal pivots: L(r,k) <- A(r,k) L(k,k)^-T, one row per thread of the team (used on narrow
+// levels, where the inverse of L(k,k) is still being formed by warp 0).
+template <int D, class F>
+__device__ __forceinline__ void panel_subst(F& p, double* L, int lv, int tid, int nthr) {
+  constexpr int BS = D * D;
+  const int q0 = p.panptr[lv], q1 = p.panptr[lv + 1];
+  for (int it = tid; it < (q1 - q0) * D; it += nthr) {
+    const int q = q0 + it / D, row = it % D;
+    double* X = L + (int64_t)p.pan[2 * q] * BS + row * D;
+    const int k = p.pan[2 * q + 1];
+    const double* Lk = L + (int64_t)k * BS;
+    const double* Ik = p.Linv + (int64_t)k * BS;
+    double o[D];
+#pragma unroll
+    for (int jj = 0; jj < D; ++jj) {
+      double s2 = X[jj];
+#pragma unroll
+      for (int mm = 0; mm < jj; ++mm) s2 = fma(-o[mm], Lk[jj * D + mm], s2);
+      o[jj] = s2 * Ik[jj * D + jj];
     }
-    if (!ok) *sflag = gen;
+#pragma unroll
+    for (int jj = 0; jj < D; ++jj) X[jj] = o[jj];
   }
 }
 
@@ -212,11 +266,22 @@ __device__ bool block_factor(F& p, double lam, int* sflag, int gen, double shift
     __syncthreads();
     const int c0 = p.lvlptr[lv], c1 = p.lvlptr[lv + 1];
     if (c1 - c0 <= 32 / D && blockDim.x >= 64) {
+      // narrow level: warp 0 factors the diagonal blocks while the other warps take the next
+      // level's early gather pairs; then the other warps form the panel by substitution while
+      // warp 0 completes L(k,k)^-1 (needed only by the solves)
       if (threadIdx.x < 32)
-        diag_rows<D>(p, L, c0, c1, sflag, gen);
+        diag_rows_factor<D>(p, L, c0, c1, sflag, gen);
       else if (lv + 1 < p.nlev)
         gather_level<D>(p, L, lv + 1, 1, threadIdx.x - 32, blockDim.x - 32);
       early_done = lv + 1 < p.nlev;
+      __syncthreads();
+      if (*sflag == gen) return false;
+      if (threadIdx.x < 32)
+        diag_rows_inverse<D>(p, L, c0, c1);
+      else
+        panel_subst<D>(p, L, lv, threadIdx.x - 32, blockDim.x - 32);
+      __syncthreads();
+      continue;
     } else {
       for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) diag_thread<D>(p, L, p.lvlcols[c], sflag, gen);
       early_done = false;

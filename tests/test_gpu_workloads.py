@@ -87,9 +87,22 @@ def test_uneven_small_fp64_every_problem():
     # directions, and the 1e-9 check is meant to compare converged solutions
     opts = layer.Options(algo="lm", iters=30, precision="fp64", tau=0.0)
     sol, theta, _ = run_forward(b, opts)
+    eps = float(np.finfo(np.float64).eps)
     for k in range(b.batch):
-        _, ref, _ = oracle_solve(b, k, opts)
-        assert rel(poses_of(b, theta, k), ref) < 1e-9, k
+        g, ref, _ = oracle_solve(b, k, opts)
+        # Both loops accept a step on a comparison of S values, which carry a rounding error of
+        # ~eps S; near the optimum S - S* = 1/2 d^T H d, so the two solutions may settle anywhere
+        # within |d| ~ sqrt(2 eps S / lambda_min(H)) of the optimum without either loop seeing a
+        # difference (up to 5.7e-9 relative here, problem 6: 128 poses, lambda_min 6e-5).  The
+        # bound is that radius (at least 1e-9); in addition the oracle's S at the GPU's solution
+        # must equal its S at its own to within that rounding.
+        r, J = pgo.jacobian(g, ref)
+        lmin = float(torch.linalg.eigvalsh(J.T @ J)[0])
+        S_ref = float(pgo.objective(g, ref))
+        tol = max(1e-9, 2.0 * (2.0 * eps * S_ref / lmin) ** 0.5 / float(ref.norm()))
+        mine = poses_of(b, theta, k)
+        assert rel(mine, ref) < tol, (k, rel(mine, ref), tol)
+        assert float(pgo.objective(g, mine)) <= S_ref * (1.0 + 64.0 * eps), k
 
 
 def test_cuda_graph_capture_replays_forward_and_backward():
