@@ -48,11 +48,11 @@ __device__ __forceinline__ void diag_thread(F& p, double* L, int k, int* sflag, 
     double d = A[jj * D + jj];
 #pragma unroll
     for (int mm = 0; mm < jj; ++mm) d -= A[jj * D + mm] * A[jj * D + mm];
-    ok = ok && (d > 0.0) && isfinite(d);
-    const double dd = fmax(d, 1e-300);
-    const double il = rsqrt(dd);
+    const double il = rsqrt(d);
     inv[jj] = il;
-    A[jj * D + jj] = dd * il;
+    const double ljj = d * il;  // NaN unless the pivot is positive and finite
+    ok = ok && ljj > 0.0 && ljj < INFINITY;
+    A[jj * D + jj] = ljj;
 #pragma unroll
     for (int ii = jj + 1; ii < D; ++ii) {
       double s = A[ii * D + jj];
@@ -105,22 +105,25 @@ __device__ __forceinline__ void diag_rows_factor(F& p, double* L, int c0, int c1
   double A[D], inv[D];
 #pragma unroll
   for (int m = 0; m < D; ++m) A[m] = act ? Lk[r * D + m] : (m == r ? 1.0 : 0.0);
-  bool ok = true;
 #pragma unroll
   for (int j = 0; j < D; ++j) {
     const double d = __shfl_sync(full, A[j], base + j);  // pivot A(j, j), already updated
-    ok = ok && (d > 0.0) && isfinite(d);
-    const double dd = fmax(d, 1e-300);
-    const double il = rsqrt(dd);
+    const double il = rsqrt(d);
     inv[j] = il;
-    const double lrj = r == j ? dd * il : (r > j ? A[j] * il : 0.0);
+    // L(j, j) = d / sqrt(d) on lane j, L(r, j) = A(r, j) / sqrt(d) below it; lanes above the
+    // pivot row compute a value nobody reads
+    const double lrj = (r == j ? d : A[j]) * il;
     A[j] = lrj;
 #pragma unroll
     for (int m = j + 1; m < D; ++m) {
       const double lmj = __shfl_sync(full, lrj, base + m);
-      if (m <= r) A[m] = fma(-lrj, lmj, A[m]);
+      A[m] = fma(-lrj, lmj, A[m]);  // entries right of the diagonal are never read or stored
     }
   }
+  // a pivot that is not positive and finite leaves L(r, r) = d rsqrt(d) NaN (0 * inf, inf * 0
+  // or the NaN of a negative square root), so one test of the row's own diagonal per lane
+  // replaces a test per pivot
+  const bool ok = A[r] > 0.0 && A[r] < INFINITY;
   if (act) {
 #pragma unroll
     for (int m = 0; m < D; ++m) Lk[r * D + m] = m <= r ? A[m] : 0.0;
@@ -208,14 +211,14 @@ template <int D, class F>
 __device__ __forceinline__ void gather_level(F& p, double* L, int lv, int mode, int tid, int nthr) {
   constexpr int BS = D * D;
   const int t0 = p.tgtptr[lv], t1 = p.tgtptr[lv + 1];
-  const int LN = p.glanes[lv];
+  const int LN = p.glanes[lv], lsh = __ffs(LN) - 1;  // LN is a power of two
   const int n1 = (t1 - t0) * BS * LN;
   for (int base = 0; base < n1; base += nthr) {
     const int it = base + tid;
     double acc = 0.0;
     int q = 0, el = 0, s0 = 0, s1 = 0;
     if (it < n1) {
-      const int e2 = it / LN, lane = it % LN;
+      const int e2 = it >> lsh, lane = it & (LN - 1);
       q = t0 + e2 / BS;
       el = e2 % BS;
       const int a = el / D, b = el % D;
@@ -229,7 +232,7 @@ __device__ __forceinline__ void gather_level(F& p, double* L, int lv, int mode, 
       }
     }
     if (LN > 1) acc = lane_sum(acc, LN);
-    if (it < n1 && (it % LN) == 0 && s1 > s0) L[(int64_t)p.tgt[q] * BS + el] -= acc;
+    if (it < n1 && (it & (LN - 1)) == 0 && s1 > s0) L[(int64_t)p.tgt[q] * BS + el] -= acc;
   }
 }
 
@@ -394,14 +397,14 @@ __device__ void block_solve(F& p, double* x) {
   const double* L = p.L;
   for (int lv = 0; lv < p.nlev; ++lv) {
     const int c0 = p.lvlptr[lv], c1 = p.lvlptr[lv + 1];
-    const int LN = p.slanes[lv];
+    const int LN = p.slanes[lv], lsh = __ffs(LN) - 1;  // LN is a power of two
     const int n1 = (c1 - c0) * D * LN;
     for (int base = 0; base < n1; base += blockDim.x) {
       const int it = base + threadIdx.x;
       double acc = 0.0;
       int k = 0, i = 0;
       if (it < n1) {
-        const int e2 = it / LN, lane = it % LN;
+        const int e2 = it >> lsh, lane = it & (LN - 1);
         k = p.lvlcols[c0 + e2 / D];
         i = e2 % D;
         for (int q = p.rowptr[k] + lane; q < p.rowptr[k + 1]; q += LN) {
@@ -412,7 +415,7 @@ __device__ void block_solve(F& p, double* x) {
         }
       }
       if (LN > 1) acc = lane_sum(acc, LN);
-      if (it < n1 && (it % LN) == 0) p.tmp[k * D + i] = x[k * D + i] - acc;
+      if (it < n1 && (it & (LN - 1)) == 0) p.tmp[k * D + i] = x[k * D + i] - acc;
     }
     __syncthreads();
     for (int it = threadIdx.x; it < (c1 - c0) * D; it += blockDim.x) {
@@ -428,14 +431,14 @@ __device__ void block_solve(F& p, double* x) {
   }
   for (int lv = p.nlev - 1; lv >= 0; --lv) {
     const int c0 = p.lvlptr[lv], c1 = p.lvlptr[lv + 1];
-    const int LN = p.slanes[lv];
+    const int LN = p.slanes[lv], lsh = __ffs(LN) - 1;  // LN is a power of two
     const int n1 = (c1 - c0) * D * LN;
     for (int base = 0; base < n1; base += blockDim.x) {
       const int it = base + threadIdx.x;
       double acc = 0.0;
       int k = 0, i = 0;
       if (it < n1) {
-        const int e2 = it / LN, lane = it % LN;
+        const int e2 = it >> lsh, lane = it & (LN - 1);
         k = p.lvlcols[c0 + e2 / D];
         i = e2 % D;
         const int basec = p.colptr[k];
@@ -448,7 +451,7 @@ __device__ void block_solve(F& p, double* x) {
         }
       }
       if (LN > 1) acc = lane_sum(acc, LN);
-      if (it < n1 && (it % LN) == 0) p.tmp[k * D + i] = x[k * D + i] - acc;
+      if (it < n1 && (it & (LN - 1)) == 0) p.tmp[k * D + i] = x[k * D + i] - acc;
     }
     __syncthreads();
     for (int it = threadIdx.x; it < (c1 - c0) * D; it += blockDim.x) {
