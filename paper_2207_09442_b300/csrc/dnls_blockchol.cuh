@@ -132,14 +132,16 @@ __device__ __forceinline__ void diag_rows_factor(F& p, double* L, int c0, int c1
   }
 }
 
+// Columns c0..c1-1 of `cols` (null: the columns c0..c1-1 themselves).
 template <int D, class F>
-__device__ __forceinline__ void diag_rows_inverse(F& p, const double* L, int c0, int c1) {
+__device__ __forceinline__ void diag_rows_inverse(F& p, const double* L, int c0, int c1,
+                                                  const int32_t* cols) {
   constexpr int BS = D * D;
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const int grp = lane / D, r = lane - grp * D, base = grp * D;
   const bool act = grp < c1 - c0;
-  const int k = act ? p.lvlcols[c0 + grp] : 0;
+  const int k = act ? (cols ? cols[c0 + grp] : c0 + grp) : 0;
   const double* Lk = L + (int64_t)k * BS;
   const double* Ik = p.Linv + (int64_t)k * BS;
   double A[D], inv[D];
@@ -173,12 +175,12 @@ template <int D, class F>
 __device__ __forceinline__ void diag_rows(F& p, double* L, int c0, int c1, int* sflag, int gen) {
   diag_rows_factor<D>(p, L, c0, c1, sflag, gen);
   __syncwarp();
-  diag_rows_inverse<D>(p, L, c0, c1);
+  diag_rows_inverse<D>(p, L, c0, c1, p.lvlcols);
 }
 
 // Off-diagonal blocks of level lv's columns by forward substitution with L(k,k) and its
-// reciprocal pivots: L(r,k) <- A(r,k) L(k,k)^-T, one row per thread of the team (used on narrow
-// levels, where the inverse of L(k,k) is still being formed by warp 0).
+// reciprocal pivots (the diagonal of L(k,k)^-1, stored by diag_rows_factor):
+// L(r,k) <- A(r,k) L(k,k)^-T, one row per thread of the team.
 template <int D, class F>
 __device__ __forceinline__ void panel_subst(F& p, double* L, int lv, int tid, int nthr) {
   constexpr int BS = D * D;
@@ -236,82 +238,86 @@ __device__ __forceinline__ void gather_level(F& p, double* L, int lv, int mode, 
   }
 }
 
+// L <- H + lam * diag(max(diag H, floor)) + shift * I (fill-in blocks zero) by the team threads
+// tid = 0 .. nthr-1.  Each thread first fetches the source offsets of U elements, then the
+// elements, then stores them, so its loads are in flight together.
+template <int D, class F>
+__device__ __forceinline__ void load_damped(F& p, double* L, double lam, double shift, int tid,
+                                            int nthr) {
+  constexpr int BS = D * D, U = 4;
+  const int total = (p.N + p.nnzL) * BS;
+  for (int it0 = tid; it0 < total; it0 += U * nthr) {
+    int off[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int it = it0 + u * nthr, t = it / BS, el = it - t * BS;
+      int o = -1;
+      if (it < total) {
+        if (t < p.N) {
+          o = it;
+        } else {
+          const int src = p.lsrc[t - p.N];
+          o = src >= 0 ? (p.N + src) * BS + el : -1;
+        }
+      }
+      off[u] = o;
+    }
+    double v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) v[u] = off[u] >= 0 ? p.H[off[u]] : 0.0;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int it = it0 + u * nthr, t = it / BS, el = it - t * BS;
+      if (it < total) {
+        double x = v[u];
+        if (t < p.N && el / D == el % D) x += lam * fmax(x, kDiagFloor) + shift;
+        L[it] = x;
+      }
+    }
+  }
+}
+
 // L <- H + lam * diag(max(diag H, floor)) + shift * I, then left-looking block Cholesky level
-// by level.
+// by level, and finally the inverses of the diagonal blocks (used by the solves only).
 // Returns false (uniformly across the CTA) if a pivot is not positive or not finite.  A failing
 // thread writes the call's generation number `gen` into *sflag; the flag is never reset, so a
 // slow thread can never see a later call's state.
 template <int D, class F>
 __device__ bool block_factor(F& p, double lam, int* sflag, int gen, double shift = 0.0) {
-  constexpr int BS = D * D;
+  constexpr int CPW = 32 / D;  // diagonal blocks per warp in diag_rows_factor
   double* L = p.L;
-  const int nb = p.N + p.nnzL;
-  for (int it = threadIdx.x; it < nb * BS; it += blockDim.x) {
-    const int t = it / BS, el = it % BS;
-    double v;
-    if (t < p.N) {
-      v = p.H[(int64_t)t * BS + el];
-      if (el / D == el % D) v += lam * fmax(v, kDiagFloor) + shift;
-    } else {
-      const int src = p.lsrc[t - p.N];
-      v = src >= 0 ? p.H[(int64_t)(p.N + src) * BS + el] : 0.0;
-    }
-    L[(int64_t)t * BS + el] = v;
-  }
+  const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  load_damped<D>(p, L, lam, shift, threadIdx.x, blockDim.x);
   __syncthreads();
   // Level by level: (1) gather, (2) diagonal factors, (3) panels.  On a narrow level (at most
-  // 32/D columns) warp 0 alone factors the diagonal blocks, and the other warps meanwhile
+  // CPW columns) warp 0 alone factors the diagonal blocks, and the other warps meanwhile
   // subtract the next level's "early" source pairs (columns two or more levels below, already
-  // final); that level's gather then only adds the pairs from the level just factored.
+  // final); that level's gather then only adds the pairs from the level just factored.  On a
+  // wide level every warp factors CPW diagonal blocks at a time.
   bool early_done = false;
   for (int lv = 0; lv < p.nlev; ++lv) {
     gather_level<D>(p, L, lv, early_done ? 2 : 0, threadIdx.x, blockDim.x);
     __syncthreads();
     const int c0 = p.lvlptr[lv], c1 = p.lvlptr[lv + 1];
-    if (c1 - c0 <= 32 / D && blockDim.x >= 64) {
-      // narrow level: warp 0 factors the diagonal blocks while the other warps take the next
-      // level's early gather pairs; then the other warps form the panel by substitution while
-      // warp 0 completes L(k,k)^-1 (needed only by the solves)
-      if (threadIdx.x < 32)
+    if (c1 - c0 <= CPW && nwarps >= 2) {
+      if (warp == 0)
         diag_rows_factor<D>(p, L, c0, c1, sflag, gen);
       else if (lv + 1 < p.nlev)
         gather_level<D>(p, L, lv + 1, 1, threadIdx.x - 32, blockDim.x - 32);
       early_done = lv + 1 < p.nlev;
-      __syncthreads();
-      if (*sflag == gen) return false;
-      if (threadIdx.x < 32)
-        diag_rows_inverse<D>(p, L, c0, c1);
-      else
-        panel_subst<D>(p, L, lv, threadIdx.x - 32, blockDim.x - 32);
-      __syncthreads();
-      continue;
     } else {
-      for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) diag_thread<D>(p, L, p.lvlcols[c], sflag, gen);
+      for (int cc = c0 + warp * CPW; cc < c1; cc += nwarps * CPW)
+        diag_rows_factor<D>(p, L, cc, min(cc + CPW, c1), sflag, gen);
       early_done = false;
     }
     __syncthreads();
     if (*sflag == gen) return false;
-    // (3) off-diagonal blocks of the level's columns: L(r,k) <- A(r,k) L(k,k)^-T, one row each
-    const int q0 = p.panptr[lv], q1 = p.panptr[lv + 1];
-    for (int it = threadIdx.x; it < (q1 - q0) * D; it += blockDim.x) {
-      const int q = q0 + it / D, row = it % D;
-      double* X = L + (int64_t)p.pan[2 * q] * BS + row * D;
-      const double* Ik = p.Linv + (int64_t)p.pan[2 * q + 1] * BS;
-      double a[D], o[D];
-#pragma unroll
-      for (int mm = 0; mm < D; ++mm) a[mm] = X[mm];
-#pragma unroll
-      for (int jj = 0; jj < D; ++jj) {
-        double s = 0.0;
-#pragma unroll
-        for (int mm = 0; mm <= jj; ++mm) s = fma(a[mm], Ik[jj * D + mm], s);
-        o[jj] = s;
-      }
-#pragma unroll
-      for (int jj = 0; jj < D; ++jj) X[jj] = o[jj];
-    }
+    panel_subst<D>(p, L, lv, threadIdx.x, blockDim.x);
     __syncthreads();
   }
+  for (int cc = warp * CPW; cc < p.N; cc += nwarps * CPW)
+    diag_rows_inverse<D>(p, L, cc, min(cc + CPW, p.N), nullptr);
+  __syncthreads();
   return true;
 }
 
@@ -336,19 +342,7 @@ __device__ bool block_factor_cluster(F& p, double lam, int rank, int nranks, int
   constexpr int BS = D * D;
   double* L = p.L;
   const int tid = rank * blockDim.x + threadIdx.x, nthr = nranks * blockDim.x;
-  const int nb = p.N + p.nnzL;
-  for (int it = tid; it < nb * BS; it += nthr) {
-    const int t = it / BS, el = it % BS;
-    double v;
-    if (t < p.N) {
-      v = p.H[(int64_t)t * BS + el];
-      if (el / D == el % D) v += lam * fmax(v, kDiagFloor);
-    } else {
-      const int src = p.lsrc[t - p.N];
-      v = src >= 0 ? p.H[(int64_t)(p.N + src) * BS + el] : 0.0;
-    }
-    L[(int64_t)t * BS + el] = v;
-  }
+  load_damped<D>(p, L, lam, 0.0, tid, nthr);
   cluster_sync_all();
   bool early_done = false;
   for (int lv = 0; lv < p.nlev; ++lv) {
