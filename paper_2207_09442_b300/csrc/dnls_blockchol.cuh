@@ -238,12 +238,11 @@ __device__ __forceinline__ void gather_level(F& p, double* L, int lv, int mode, 
   }
 }
 
-// L <- H + lam * diag(max(diag H, floor)) + shift * I (fill-in blocks zero) by the team threads
-// tid = 0 .. nthr-1.  Each thread first fetches the source offsets of U elements, then the
-// elements, then stores them, so its loads are in flight together.
+// L <- H (fill-in blocks zero) by the team threads tid = 0 .. nthr-1.  Each thread first fetches
+// the source offsets of U elements, then the elements, then stores them, so its loads are in
+// flight together.  damp_diagonal then adds lam * max(diag H, floor) + shift to the diagonal.
 template <int D, class F>
-__device__ __forceinline__ void load_damped(F& p, double* L, double lam, double shift, int tid,
-                                            int nthr) {
+__device__ __forceinline__ void load_factor(F& p, double* L, int tid, int nthr) {
   constexpr int BS = D * D, U = 4;
   const int total = (p.N + p.nnzL) * BS;
   for (int it0 = tid; it0 < total; it0 += U * nthr) {
@@ -267,13 +266,20 @@ __device__ __forceinline__ void load_damped(F& p, double* L, double lam, double 
     for (int u = 0; u < U; ++u) v[u] = off[u] >= 0 ? p.H[off[u]] : 0.0;
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const int it = it0 + u * nthr, t = it / BS, el = it - t * BS;
-      if (it < total) {
-        double x = v[u];
-        if (t < p.N && el / D == el % D) x += lam * fmax(x, kDiagFloor) + shift;
-        L[it] = x;
-      }
+      const int it = it0 + u * nthr;
+      if (it < total) L[it] = v[u];
     }
+  }
+}
+
+// The damping that follows load_factor (after a barrier), on the N * D diagonal entries.
+template <int D, class F>
+__device__ __forceinline__ void damp_diagonal(F& p, double* L, double lam, double shift, int tid,
+                                              int nthr) {
+  for (int it = tid; it < p.N * D; it += nthr) {
+    const int t = it / D, a = it - t * D;
+    double* x = L + (int64_t)t * D * D + a * (D + 1);
+    *x += lam * fmax(*x, kDiagFloor) + shift;
   }
 }
 
@@ -287,7 +293,9 @@ __device__ bool block_factor(F& p, double lam, int* sflag, int gen, double shift
   constexpr int CPW = 32 / D;  // diagonal blocks per warp in diag_rows_factor
   double* L = p.L;
   const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  load_damped<D>(p, L, lam, shift, threadIdx.x, blockDim.x);
+  load_factor<D>(p, L, threadIdx.x, blockDim.x);
+  __syncthreads();
+  damp_diagonal<D>(p, L, lam, shift, threadIdx.x, blockDim.x);
   __syncthreads();
   // Level by level: (1) gather, (2) diagonal factors, (3) panels.  On a narrow level (at most
   // CPW columns) warp 0 alone factors the diagonal blocks, and the other warps meanwhile
@@ -342,7 +350,9 @@ __device__ bool block_factor_cluster(F& p, double lam, int rank, int nranks, int
   constexpr int BS = D * D;
   double* L = p.L;
   const int tid = rank * blockDim.x + threadIdx.x, nthr = nranks * blockDim.x;
-  load_damped<D>(p, L, lam, 0.0, tid, nthr);
+  load_factor<D>(p, L, tid, nthr);
+  cluster_sync_all();
+  damp_diagonal<D>(p, L, lam, 0.0, tid, nthr);
   cluster_sync_all();
   bool early_done = false;
   for (int lv = 0; lv < p.nlev; ++lv) {

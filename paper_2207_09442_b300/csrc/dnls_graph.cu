@@ -230,17 +230,19 @@ __device__ void lin_costs(Prob<KIND>& p, const double* poses) {
     P* out = Jb + (int64_t)e * JW;
     if (j >= 0) {
       const double* Tj = poses + (int64_t)j * PW;
-      double A[PW], Ai[PW], Em[PW];
+      double A[PW], Em[PW];
       G::invmul(Ti, Tj, A);
-      G::invmul(Tj, Ti, Ai);
       G::invmul(Z, A, Em);
-      P Ap[PW], Ep[PW];
+      // A^-1 = T_j^-1 T_i only enters the Jacobian (through its adjoint), so it is inverted in
+      // precision P from A rounded to P
+      P Ap[PW], Ai[PW], Ep[PW];
 #pragma unroll
       for (int k = 0; k < PW; ++k) {
-        Ap[k] = (P)Ai[k];
+        Ap[k] = (P)A[k];
         Ep[k] = (P)Em[k];
       }
-      between_lin<KIND, P>(Ap, Ep, wp, out, out + D, out + D + BS);
+      G::inv(Ap, Ai);
+      between_lin<KIND, P>(Ai, Ep, wp, out, out + D, out + D + BS);
     } else {
       double Em[PW];
       G::invmul(Z, Ti, Em);
@@ -300,7 +302,8 @@ __device__ double eval_S(Prob<KIND>& p, const double* poses, double* red) {
 }
 
 // H (diagonal and pair blocks, undamped) and g = J^T r from the per-cost Jacobians.
-// H products in P (FP32 on the mixed path), g accumulated in FP64.
+// H products in P (FP32 on the mixed path); g sums each cost's J^T r term in P and adds the
+// terms of the incident costs in FP64.
 template <int KIND, class P>
 __device__ void assemble(Prob<KIND>& p) {
   constexpr int D = Group<KIND>::DOF, BS = D * D, JW = Prob<KIND>::JW;
@@ -337,8 +340,10 @@ __device__ void assemble(Prob<KIND>& p) {
         const int t = p.inc[q];
         const P* r = Jb + (int64_t)(t >> 1) * JW;
         const P* Jt = r + D + (t & 1) * BS;
+        P term = Jt[a] * r[0];
 #pragma unroll
-        for (int mm = 0; mm < D; ++mm) acc += (double)Jt[mm * D + a] * (double)r[mm];
+        for (int mm = 1; mm < D; ++mm) term = fma(Jt[mm * D + a], r[mm], term);
+        acc += (double)term;
       }
       p.g[(int64_t)k * D + a] = acc;
     }
