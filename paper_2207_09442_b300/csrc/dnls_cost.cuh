@@ -88,17 +88,51 @@ DNLS_HD void jt_r(const S* J, const S* r, S* g) {
   }
 }
 
-// pose T (+) (t x) as a dual number in t at t = 0: value T, derivative T x^
+// Between cost, local gradients only: with u = J_r^-1(c)^T (w^2 c) (= J_j^T r),
+// J_i^T r = -Ad(A^-1)^T u, since J_i = -diag(w) J_r^-1(c) Ad(A^-1) and J_j = diag(w) J_r^-1(c).
+// Also returns the weighted residual r = w c.  Ainv = A^-1 = T_j^-1 T_i.
+template <int KIND, class S>
+DNLS_HD void between_grad(const S* Ainv, const S* E, const S* w, S* r, S* gi, S* gj) {
+  typedef Group<KIND> G;
+  constexpr int D = G::DOF;
+  S c[D], Jr[D * D], Ad[D * D], w2c[D];
+  G::log(E, c);
+  G::jr_inv(c, Jr);
+  G::adjoint(Ainv, Ad);
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    r[a] = w[a] * c[a];
+    w2c[a] = w[a] * r[a];
+  }
+  jt_r<D>(Jr, w2c, gj);
+  jt_r<D>(Ad, gj, gi);
+#pragma unroll
+  for (int b = 0; b < D; ++b) gi[b] = -gi[b];
+}
+
+// pose T (+) (t x) as a dual number in t at t = 0: value T, derivative T x^ (the derivative of
+// Exp at the identity is the hat map: for SE(3) [[phi]x | rho], for SE(2) the rotation
+// derivative (0, psi) and the translation derivative rho).
 template <int KIND>
 DNLS_HD void pose_dual(const double* T, const double* x, Dual<double>* out) {
-  typedef Group<KIND> G;
-  Dual<double> xi[G::DOF], Ex[G::PW], Td[G::PW];
+  if constexpr (KIND == 3) {
+    const double *rho = x, *phi = x + 3;
 #pragma unroll
-  for (int k = 0; k < G::DOF; ++k) xi[k] = Dual<double>(0.0, x[k]);
-  G::exp(xi, Ex);
-#pragma unroll
-  for (int k = 0; k < G::PW; ++k) Td[k] = Dual<double>(T[k], 0.0);
-  G::mul(Td, Ex, out);
+    for (int r = 0; r < 3; ++r) {
+      const double R0 = T[4 * r], R1 = T[4 * r + 1], R2 = T[4 * r + 2];
+      // row r of R [phi]x: [R1 phi2 - R2 phi1, R2 phi0 - R0 phi2, R0 phi1 - R1 phi0]
+      out[4 * r] = Dual<double>(R0, R1 * phi[2] - R2 * phi[1]);
+      out[4 * r + 1] = Dual<double>(R1, R2 * phi[0] - R0 * phi[2]);
+      out[4 * r + 2] = Dual<double>(R2, R0 * phi[1] - R1 * phi[0]);
+      out[4 * r + 3] = Dual<double>(T[4 * r + 3], R0 * rho[0] + R1 * rho[1] + R2 * rho[2]);
+    }
+  } else {
+    const double c = T[2], s = T[3];
+    out[0] = Dual<double>(T[0], c * x[0] - s * x[1]);
+    out[1] = Dual<double>(T[1], s * x[0] + c * x[1]);
+    out[2] = Dual<double>(c, -s * x[2]);
+    out[3] = Dual<double>(s, c * x[2]);
+  }
 }
 
 }  // namespace dnls

@@ -741,14 +741,12 @@ __device__ void hvp_exact(Prob<KIND>& p, const double* x, double* hx) {
     pose_dual<KIND>(p.theta + (int64_t)i * PW, x + p.iperm[i] * D, Ti);
     double* eb = p.ebuf + (int64_t)e * 4 * D;
     if (j >= 0) {
-      Dd Tj[PW], A[PW], Ai[PW], Em[PW], Jj[D * D], gj[D];
+      Dd Tj[PW], A[PW], Ai[PW], Em[PW], gj[D];
       pose_dual<KIND>(p.theta + (int64_t)j * PW, x + p.iperm[j] * D, Tj);
       G::invmul(Ti, Tj, A);
-      G::invmul(Tj, Ti, Ai);
+      G::inv(A, Ai);
       G::invmul(Zd, A, Em);
-      between_lin<KIND, Dd>(Ai, Em, wd, r, Ji, Jj);
-      jt_r<D>(Ji, r, gi);
-      jt_r<D>(Jj, r, gj);
+      between_grad<KIND, Dd>(Ai, Em, wd, r, gi, gj);
       if (p.logrc) {  // local gradient of 1/2 rho(||r||^2): rho'(s) J^T r
         const Dd w1 = welsch_d1<D>(r, p.logrc[e]);
 #pragma unroll
