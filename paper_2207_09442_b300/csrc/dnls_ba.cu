@@ -782,13 +782,13 @@ __global__ void k_bahvp_obs(BAArgs a, int vjp) {
   if (!vjp && !a.st[b].active) return;
   typedef Dual<double> Dd;
   const int64_t c = a.d.obs_cam[o], q = a.d.obs_pt[o];
-  Dd T[12], p[3], ob[2], cc[2], Jc[12], Jp[6];
+  Dd T[12], p[3], ob[2], cc[2], gc[6], gp[3];
   pose_dual<3>(a.cams + c * 12, a.xc + c * 6, T);
 #pragma unroll
   for (int k = 0; k < 3; ++k) p[k] = Dd(a.pts[q * 3 + k], a.xp[q * 3 + k]);
   ob[0] = Dd(a.obs[2 * o]);
   ob[1] = Dd(a.obs[2 * o + 1]);
-  reproj<Dd>(T, p, ob, Dd(a.f), cc, Jc, Jp);
+  reproj_grad<Dd>(T, p, ob, Dd(a.f), cc, gc, gp);
   const Dd w = huber_d1<Dd>(cc[0] * cc[0] + cc[1] * cc[1], a.delta);
   if (vjp) {
     if (a.grad_log_delta) {
@@ -808,13 +808,13 @@ __global__ void k_bahvp_obs(BAArgs a, int vjp) {
   double* e = a.eb + o * 18;
 #pragma unroll
   for (int k = 0; k < 6; ++k) {
-    const Dd gk = (Jc[k] * cc[0] + Jc[6 + k] * cc[1]) * w;
+    const Dd gk = gc[k] * w;
     e[k] = gk.v;
     e[9 + k] = gk.d;
   }
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    const Dd gk = (Jp[k] * cc[0] + Jp[3 + k] * cc[1]) * w;
+    const Dd gk = gp[k] * w;
     e[6 + k] = gk.v;
     e[15 + k] = gk.d;
   }

@@ -43,6 +43,30 @@ DNLS_HD void reproj(const S* T, const S* p, const S* obs, S f, S* c, S* Jc, S* J
   }
 }
 
+// The residual c and the local gradients gc = Jc^T c (6), gp = Jp^T c (3) without forming the
+// Jacobians: with v = P^T c (P = d(u,v)/d p_c), gc = [-v; [p_c]x^T v] and gp = R v.
+template <class S>
+DNLS_HD void reproj_grad(const S* T, const S* p, const S* obs, S f, S* c, S* gc, S* gp) {
+  S d[3] = {p[0] - T[3], p[1] - T[7], p[2] - T[11]};
+  S pc[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) pc[i] = T[i] * d[0] + T[4 + i] * d[1] + T[8 + i] * d[2];
+  const S iz = DNLS_C(1.0) / pc[2];
+  const S fz = f * iz;
+  const S xu = pc[0] * iz, yv = pc[1] * iz;
+  c[0] = f * xu - obs[0];
+  c[1] = f * yv - obs[1];
+  const S v[3] = {fz * c[0], fz * c[1], -(xu * (fz * c[0]) + yv * (fz * c[1]))};
+  gc[0] = -v[0];
+  gc[1] = -v[1];
+  gc[2] = -v[2];
+  gc[3] = pc[2] * v[1] - pc[1] * v[2];
+  gc[4] = pc[0] * v[2] - pc[2] * v[0];
+  gc[5] = pc[1] * v[0] - pc[0] * v[1];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) gp[k] = T[4 * k] * v[0] + T[4 * k + 1] * v[1] + T[4 * k + 2] * v[2];
+}
+
 // Huber rho'(s) (with delta <= 0 meaning no robust loss)
 template <class S>
 DNLS_HD S huber_d1(const S& s, double delta) {
