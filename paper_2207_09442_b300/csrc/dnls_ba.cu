@@ -87,15 +87,16 @@ struct BAArgs {
 
 // view of one problem's reduced system for block_factor / block_solve
 struct RedView {
-  int N, nnzL, nlev;
+  int N, nnzL, nlev, chain_lev;
   const int32_t *perm, *iperm, *colptr, *rows, *rowptr, *rowent, *lvlptr, *lvlcols, *tgtptr, *tgt,
-      *gptr, *gsrc, *panptr, *pan, *lsrc, *glanes, *slanes, *gsplit;
+      *gptr, *gsrc, *panptr, *pan, *lsrc, *glanes, *slanes, *gsplit, *rsplit;
   double *H, *L, *Linv, *dx, *tmp;
   __device__ void init(const BAArgs& a, int b) {
     const ProbMeta* m = a.d.rmeta + b;
     N = m->N;
     nnzL = m->nnzL;
     nlev = m->nlev;
+    chain_lev = m->chain_lev;
     const int32_t* s = a.d.rsym + m->sym;
     perm = s + m->o_perm;
     iperm = s + m->o_iperm;
@@ -115,6 +116,7 @@ struct RedView {
     glanes = s + m->o_glanes;
     gsplit = s + m->o_gsplit;
     slanes = s + m->o_slanes;
+    rsplit = s + m->o_rsplit;
     char* w = a.ws + m->ws;
     H = (double*)(w + m->w_H);
     L = (double*)(w + m->w_L);

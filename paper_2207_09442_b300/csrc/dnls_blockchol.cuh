@@ -401,6 +401,34 @@ __device__ void block_solve(F& p, double* x) {
   const double* L = p.L;
   for (int lv = 0; lv < p.nlev; ++lv) {
     const int c0 = p.lvlptr[lv], c1 = p.lvlptr[lv + 1];
+    // Rows of the top chain (levels chain_lev.., one column each): their pairs from columns
+    // outside the chain, whose values are final once the levels below are done, are summed for
+    // all chain rows at once before the first chain level; each chain level then only adds the
+    // pairs from chain columns (rowent from rsplit[k] on).
+    const bool chain = lv >= p.chain_lev;
+    if (lv == p.chain_lev) {
+      const int LN = p.slanes[p.nlev], lsh = __ffs(LN) - 1;
+      const int n1 = (p.nlev - lv) * D * LN;
+      for (int base = 0; base < n1; base += blockDim.x) {
+        const int it = base + threadIdx.x;
+        double acc = 0.0;
+        int k = 0, i = 0;
+        if (it < n1) {
+          const int e2 = it >> lsh, lane = it & (LN - 1);
+          k = p.lvlcols[c0 + e2 / D];
+          i = e2 % D;
+          for (int q = p.rowptr[k] + lane; q < p.rsplit[k]; q += LN) {
+            const double* B = L + (int64_t)p.rowent[2 * q] * BS + i * D;
+            const double* y = x + p.rowent[2 * q + 1] * D;
+#pragma unroll
+            for (int mm = 0; mm < D; ++mm) acc = fma(B[mm], y[mm], acc);
+          }
+        }
+        if (LN > 1) acc = lane_sum(acc, LN);
+        if (it < n1 && (it & (LN - 1)) == 0) p.tmp[k * D + i] = x[k * D + i] - acc;
+      }
+      __syncthreads();
+    }
     const int LN = p.slanes[lv], lsh = __ffs(LN) - 1;  // LN is a power of two
     const int n1 = (c1 - c0) * D * LN;
     for (int base = 0; base < n1; base += blockDim.x) {
@@ -411,7 +439,7 @@ __device__ void block_solve(F& p, double* x) {
         const int e2 = it >> lsh, lane = it & (LN - 1);
         k = p.lvlcols[c0 + e2 / D];
         i = e2 % D;
-        for (int q = p.rowptr[k] + lane; q < p.rowptr[k + 1]; q += LN) {
+        for (int q = (chain ? p.rsplit[k] : p.rowptr[k]) + lane; q < p.rowptr[k + 1]; q += LN) {
           const double* B = L + (int64_t)p.rowent[2 * q] * BS + i * D;
           const double* y = x + p.rowent[2 * q + 1] * D;
 #pragma unroll
@@ -419,7 +447,7 @@ __device__ void block_solve(F& p, double* x) {
         }
       }
       if (LN > 1) acc = lane_sum(acc, LN);
-      if (it < n1 && (it & (LN - 1)) == 0) p.tmp[k * D + i] = x[k * D + i] - acc;
+      if (it < n1 && (it & (LN - 1)) == 0) p.tmp[k * D + i] = (chain ? p.tmp[k * D + i] : x[k * D + i]) - acc;
     }
     __syncthreads();
     for (int it = threadIdx.x; it < (c1 - c0) * D; it += blockDim.x) {

@@ -69,9 +69,9 @@ struct KArgs {
 template <int KIND>
 struct Prob {
   static constexpr int D = Group<KIND>::DOF, PW = Group<KIND>::PW, BS = D * D, JW = 2 * BS + D;
-  int N, E, npair, nnzL, nlev;
+  int N, E, npair, nnzL, nlev, chain_lev;
   const int32_t *perm, *iperm, *colptr, *rows, *rowptr, *rowent, *lvlptr, *lvlcols, *tgtptr, *tgt,
-      *gptr, *gsrc, *panptr, *pan, *incptr, *inc, *pairptr, *pairs, *pairtgt, *lsrc, *glanes, *slanes, *gsplit;
+      *gptr, *gsrc, *panptr, *pan, *incptr, *inc, *pairptr, *pairs, *pairtgt, *lsrc, *glanes, *slanes, *gsplit, *rsplit;
   const int32_t *ei, *ej;
   const double *meas, *wdiag;
   const float* logw;
@@ -96,6 +96,7 @@ struct Prob {
     npair = m->npair;
     nnzL = m->nnzL;
     nlev = m->nlev;
+    chain_lev = m->chain_lev;
     gsym = a.g.sym + m->sym;
     ei = a.g.ei + m->edge_off;
     ej = a.g.ej + m->edge_off;
@@ -167,6 +168,7 @@ struct Prob {
     glanes = s + m->o_glanes;
     gsplit = s + m->o_gsplit;
     slanes = s + m->o_slanes;
+    rsplit = s + m->o_rsplit;
   }
 
   // Copies the symbolic blob (and, with `factor`, the cached factor) into shared memory.

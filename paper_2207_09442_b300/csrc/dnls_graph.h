@@ -33,9 +33,13 @@ struct ProbMeta {
   int32_t o_incptr, o_inc;     // [N+1] by position, [incidences]: cost << 1 | slot
   int32_t o_pairptr, o_pairs;  // [npair+1], [n_between]: cost << 1 | orientation
   int32_t o_pairtgt, o_lsrc;   // [npair]: L block id of each pair; [nnzL]: pair of each L block or -1
-  int32_t o_glanes, o_slanes;  // [nlev]: lanes per output in the level's gathers / solve sweeps (1, 2, 4 or 8)
-  int32_t o_gsplit, o_pad;     // [N + nnzL] (parallel to tgt): end of the target's "early" source
-                               // pairs (columns two or more levels below), which come first
+  int32_t o_glanes, o_slanes;  // [nlev], [nlev + 1]: lanes per output in the level's gathers / solve
+                               // sweeps (1, 2, 4 or 8)
+  int32_t o_gsplit, o_rsplit;  // [N + nnzL] (parallel to tgt): end of the target's "early" source
+                               // pairs (columns two or more levels below), which come first;
+                               // [N]: start of row k's pairs from top-chain columns (rowent)
+  int32_t chain_lev, pad0;     // first level of the top chain (nlev: none); slanes[nlev] holds
+                               // the lanes of its pre-pass
   int32_t w_H, w_L, w_Linv;    // workspace byte offsets
   int32_t w_g, w_dx, w_tmp, w_thc, w_J;
   int32_t w_bx, w_bv, w_br, w_bhx, w_ebuf, w_state, w_W;

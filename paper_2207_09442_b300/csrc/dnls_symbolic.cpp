@@ -167,6 +167,12 @@ int build_graph_host(int kind, int B, const int64_t* pose_offsets, const int64_t
     for (int k = 0; k < N; ++k) nlev = std::max(nlev, lev[k] + 1);
     std::vector<std::vector<int>> bylev(nlev);
     for (int k = 0; k < N; ++k) bylev[lev[k]].push_back(k);
+    // the top chain: the longest run of one-column levels ending at the root (the columns of
+    // the separator eliminated last); its rows' sums over columns outside it are formed in one
+    // pass of the forward solve before its levels (at least two such levels, else none)
+    int chain_lev = nlev;
+    while (chain_lev > 0 && bylev[chain_lev - 1].size() == 1) --chain_lev;
+    if (nlev - chain_lev < 2) chain_lev = nlev;
     // gather lists: per target block of column k, the (L(r,j), L(k,j)) pairs, j in rowl[k]
     std::vector<std::vector<std::vector<int>>> gl(N);  // gl[k][t] flat pairs, t=0 diag, 1+a off
     std::vector<std::vector<std::vector<int>>> glv(N);  // level of each pair's source column
@@ -256,12 +262,28 @@ int build_graph_host(int kind, int B, const int64_t* pose_offsets, const int64_t
       }
       blob.push_back(acc);
     }
+    // within each row, pairs from columns outside the top chain first; rsplit[k] = where the
+    // chain columns' pairs begin (the row's end for rows outside the chain)
+    std::vector<int32_t> rsplit(N);
     m.o_rowent = mark();
-    for (int k = 0; k < N; ++k)
-      for (auto& pr : rowl[k]) {
-        blob.push_back(pr.first);
-        blob.push_back(pr.second);
+    {
+      int acc = 0;
+      for (int k = 0; k < N; ++k) {
+        int nonchain = 0;
+        for (int pass = 0; pass < 2; ++pass)
+          for (auto& pr : rowl[k]) {
+            if ((lev[pr.second] >= chain_lev) != (pass == 1)) continue;
+            blob.push_back(pr.first);
+            blob.push_back(pr.second);
+            if (pass == 0) ++nonchain;
+          }
+        rsplit[k] = acc + nonchain;
+        acc += (int)rowl[k].size();
       }
+    }
+    m.o_rsplit = mark();
+    blob.insert(blob.end(), rsplit.begin(), rsplit.end());
+    m.chain_lev = chain_lev;
     m.o_lvlptr = mark();
     {
       int acc = 0;
@@ -382,15 +404,23 @@ int build_graph_host(int kind, int B, const int64_t* pose_offsets, const int64_t
       blob.push_back(lanes_for((int64_t)(t1 - t0) * BS, avg, 1));
     }
     m.o_slanes = mark();
+    int64_t pre_terms = 0;  // terms of the top chain's pre-pass
     for (int l = 0; l < nlev; ++l) {
       int64_t fwd = 0, bwd = 0;
       for (int k : bylev[l]) {
-        fwd += (int64_t)rowl[k].size();
+        int64_t nonchain = 0;
+        for (auto& pr : rowl[k]) nonchain += lev[pr.second] < chain_lev;
+        fwd += l >= chain_lev ? (int64_t)rowl[k].size() - nonchain : (int64_t)rowl[k].size();
+        if (l >= chain_lev) pre_terms += nonchain;
         bwd += (int64_t)rows[k].size();
       }
       const int nc = (int)bylev[l].size();
       const double avg = nc ? (double)std::max(fwd, bwd) / nc : 0.0;
       blob.push_back(lanes_for((int64_t)nc * D, avg, 1));
+    }
+    {  // slanes[nlev]: lanes of the top chain's pre-pass
+      const int nc = nlev - chain_lev;
+      blob.push_back(nc ? lanes_for((int64_t)nc * D, (double)pre_terms / nc, 1) : 1);
     }
     blob.push_back(0);  // keep every section non-empty-addressable
     while (blob.size() % 4) blob.push_back(0);  // 16-byte multiple, for staging copies
