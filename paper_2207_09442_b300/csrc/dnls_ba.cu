@@ -1066,7 +1066,7 @@ int build_ba_host(const dnls_ba_desc* desc, BAHost& H) {
     red_ej.push_back(-1);
   }
   int rc = build_graph_host(DNLS_SE3, B, H.cam_off.data(), red_edge_off.data(), red_ei.data(),
-                            red_ej.data(), DNLS_ORDER_MIN_DEGREE, &H.red);
+                            red_ej.data(), DNLS_ORDER_MIN_DEGREE, &H.red, kRedCluster * 256);
   if (rc != DNLS_OK) return rc;
   H.red_chain = true;
   for (const ProbMeta& m : H.red.meta) H.red_chain = H.red_chain && m.nlev == m.N;

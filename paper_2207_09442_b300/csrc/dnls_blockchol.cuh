@@ -349,7 +349,10 @@ template <int D, class F>
 __device__ bool block_factor_cluster(F& p, double lam, int rank, int nranks, int* gflag, int gen) {
   constexpr int BS = D * D;
   double* L = p.L;
-  const int tid = rank * blockDim.x + threadIdx.x, nthr = nranks * blockDim.x;
+  // team index: consecutive warps of work go to consecutive CTAs, so that a phase with fewer
+  // items than the cluster has threads still spreads over all of the cluster's SMs
+  const int tid = ((threadIdx.x >> 5) * nranks + rank) * 32 + (threadIdx.x & 31);
+  const int nthr = nranks * blockDim.x;
   load_factor<D>(p, L, tid, nthr);
   cluster_sync_all();
   damp_diagonal<D>(p, L, lam, 0.0, tid, nthr);

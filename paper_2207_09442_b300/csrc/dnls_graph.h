@@ -74,7 +74,10 @@ struct GraphHost {
 constexpr int64_t kWsHeader = 256;
 
 // Returns 0 on success, or a DNLS_ERR_* code; fills `out`.
+// `threads` = the threads that will run one problem's factorization (0: one CTA's default),
+// used to choose the lanes per output of each level's sums.
 int build_graph_host(int kind, int B, const int64_t* pose_offsets, const int64_t* edge_offsets,
-                     const int32_t* edge_i, const int32_t* edge_j, int ordering, GraphHost* out);
+                     const int32_t* edge_i, const int32_t* edge_j, int ordering, GraphHost* out,
+                     int threads = 0);
 
 }  // namespace dnls

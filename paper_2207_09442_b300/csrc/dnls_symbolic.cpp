@@ -86,7 +86,8 @@ int64_t align256(int64_t x) { return (x + 255) & ~(int64_t)255; }
 }  // namespace
 
 int build_graph_host(int kind, int B, const int64_t* pose_offsets, const int64_t* edge_offsets,
-                     const int32_t* edge_i, const int32_t* edge_j, int ordering, GraphHost* out) {
+                     const int32_t* edge_i, const int32_t* edge_j, int ordering, GraphHost* out,
+                     int threads) {
   if (!out || !pose_offsets || !edge_offsets || !edge_i || !edge_j) return DNLS_ERR_ARG;
   if ((kind != DNLS_SE2 && kind != DNLS_SE3) || B < 1) return DNLS_ERR_ARG;
   if (ordering != DNLS_ORDER_MIN_DEGREE && ordering != DNLS_ORDER_NATURAL) return DNLS_ERR_ARG;
@@ -390,7 +391,7 @@ int build_graph_host(int kind, int B, const int64_t* pose_offsets, const int64_t
     // more lanes shortens the serial chains; on wide levels extra lanes only add instructions.
     // Rule: double the lanes (up to 8) while the level's outputs x lanes still fit in the
     // CTA's threads and each lane keeps at least one term on average.
-    const int threads_hint = D == 6 ? 256 : 128;
+    const int threads_hint = threads > 0 ? threads : (D == 6 ? 256 : 128);
     auto lanes_for = [&](int64_t outputs, double avg_terms, int min_lanes) {
       int ln = min_lanes;
       while (ln < 8 && outputs * ln * 2 <= threads_hint && avg_terms >= 2.0 * ln) ln *= 2;
