@@ -33,63 +33,10 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return r;
 }
 
-// Cholesky and factor inverse of diagonal block k by one thread; a failed pivot writes `gen`.
-template <int D, class F>
-__device__ __forceinline__ void diag_thread(F& p, double* L, int k, int* sflag, int gen) {
-  constexpr int BS = D * D;
-  double A[BS];
-  double* Lk = L + (int64_t)k * BS;
-#pragma unroll
-  for (int e = 0; e < BS; ++e) A[e] = Lk[e];
-  bool ok = true;
-  double inv[D];  // reciprocals of the pivots, reused by the inverse below
-#pragma unroll
-  for (int jj = 0; jj < D; ++jj) {
-    double d = A[jj * D + jj];
-#pragma unroll
-    for (int mm = 0; mm < jj; ++mm) d -= A[jj * D + mm] * A[jj * D + mm];
-    const double il = rsqrt(d);
-    inv[jj] = il;
-    const double ljj = d * il;  // NaN unless the pivot is positive and finite
-    ok = ok && ljj > 0.0 && ljj < INFINITY;
-    A[jj * D + jj] = ljj;
-#pragma unroll
-    for (int ii = jj + 1; ii < D; ++ii) {
-      double s = A[ii * D + jj];
-#pragma unroll
-      for (int mm = 0; mm < jj; ++mm) s -= A[ii * D + mm] * A[jj * D + mm];
-      A[ii * D + jj] = s * il;
-    }
-  }
-  // inverse of the lower-triangular factor
-  double I[BS];
-#pragma unroll
-  for (int e = 0; e < BS; ++e) I[e] = 0.0;
-#pragma unroll
-  for (int jj = 0; jj < D; ++jj) {
-    I[jj * D + jj] = inv[jj];
-#pragma unroll
-    for (int ii = jj + 1; ii < D; ++ii) {
-      double s = 0.0;
-#pragma unroll
-      for (int mm = jj; mm < ii; ++mm) s += A[ii * D + mm] * I[mm * D + jj];
-      I[ii * D + jj] = -s * inv[ii];
-    }
-  }
-#pragma unroll
-  for (int ii = 0; ii < D; ++ii)
-#pragma unroll
-    for (int jj = 0; jj < D; ++jj) {
-      Lk[ii * D + jj] = jj <= ii ? A[ii * D + jj] : 0.0;
-      p.Linv[(int64_t)k * BS + ii * D + jj] = I[ii * D + jj];
-    }
-  if (!ok) *sflag = gen;
-}
-
-// The same for the diagonal blocks of level columns c0..c1-1 (c1 - c0 <= 32 / D) by the 32
+// Cholesky factors of the diagonal blocks of level columns c0..c1-1 (c1 - c0 <= 32 / D) by the 32
 // lanes of one warp, in two parts.  diag_rows_factor: lane r of group g holds row r of column
 // lvlcols[c0 + g]; step j shares the pivot row's entries by shuffles and updates the trailing
-// rows (the same subtractions in the same order as the one-thread version); it stores L(k,k) and
+// rows (a right-looking column step per pivot); it stores L(k,k) and
 // the reciprocal pivots (the diagonal of L(k,k)^-1).  diag_rows_inverse (after the stores are
 // visible to the warp) reloads them and lane r computes column r of L(k,k)^-1.  All 32 lanes
 // must call both (lanes beyond the last group work on an identity block and store nothing).
@@ -169,13 +116,6 @@ __device__ __forceinline__ void diag_rows_inverse(F& p, const double* L, int c0,
 #pragma unroll
     for (int m = 0; m < D; ++m) p.Linv[(int64_t)k * BS + m * D + r] = I[m];
   }
-}
-
-template <int D, class F>
-__device__ __forceinline__ void diag_rows(F& p, double* L, int c0, int c1, int* sflag, int gen) {
-  diag_rows_factor<D>(p, L, c0, c1, sflag, gen);
-  __syncwarp();
-  diag_rows_inverse<D>(p, L, c0, c1, p.lvlcols);
 }
 
 // Off-diagonal blocks of level lv's columns by forward substitution with L(k,k) and its
@@ -347,7 +287,6 @@ __device__ __forceinline__ void cluster_sync_all() {
 // every thread of the cluster.
 template <int D, class F>
 __device__ bool block_factor_cluster(F& p, double lam, int rank, int nranks, int* gflag, int gen) {
-  constexpr int BS = D * D;
   double* L = p.L;
   // team index: consecutive warps of work go to consecutive CTAs, so that a phase with fewer
   // items than the cluster has threads still spreads over all of the cluster's SMs
@@ -357,43 +296,32 @@ __device__ bool block_factor_cluster(F& p, double lam, int rank, int nranks, int
   cluster_sync_all();
   damp_diagonal<D>(p, L, lam, 0.0, tid, nthr);
   cluster_sync_all();
+  constexpr int CPW = 32 / D;  // diagonal blocks per warp in diag_rows_factor
+  const int warp = tid >> 5, nwarps = nthr >> 5;
   bool early_done = false;
   for (int lv = 0; lv < p.nlev; ++lv) {
     gather_level<D>(p, L, lv, early_done ? 2 : 0, tid, nthr);
     cluster_sync_all();
     const int c0 = p.lvlptr[lv], c1 = p.lvlptr[lv + 1];
-    if (c1 - c0 <= 32 / D) {
-      if (tid < 32)
-        diag_rows<D>(p, L, c0, c1, gflag, gen);
+    if (c1 - c0 <= CPW) {
+      if (warp == 0)
+        diag_rows_factor<D>(p, L, c0, c1, gflag, gen);
       else if (lv + 1 < p.nlev)
         gather_level<D>(p, L, lv + 1, 1, tid - 32, nthr - 32);
       early_done = lv + 1 < p.nlev;
     } else {
-      for (int c = c0 + tid; c < c1; c += nthr) diag_thread<D>(p, L, p.lvlcols[c], gflag, gen);
+      for (int cc = c0 + warp * CPW; cc < c1; cc += nwarps * CPW)
+        diag_rows_factor<D>(p, L, cc, min(cc + CPW, c1), gflag, gen);
       early_done = false;
     }
     cluster_sync_all();
     if (*(volatile int*)gflag == gen) return false;
-    const int q0 = p.panptr[lv], q1 = p.panptr[lv + 1];
-    for (int it = tid; it < (q1 - q0) * D; it += nthr) {
-      const int q = q0 + it / D, row = it % D;
-      double* X = L + (int64_t)p.pan[2 * q] * BS + row * D;
-      const double* Ik = p.Linv + (int64_t)p.pan[2 * q + 1] * BS;
-      double a[D], o[D];
-#pragma unroll
-      for (int mm = 0; mm < D; ++mm) a[mm] = X[mm];
-#pragma unroll
-      for (int jj = 0; jj < D; ++jj) {
-        double s2 = 0.0;
-#pragma unroll
-        for (int mm = 0; mm <= jj; ++mm) s2 = fma(a[mm], Ik[jj * D + mm], s2);
-        o[jj] = s2;
-      }
-#pragma unroll
-      for (int jj = 0; jj < D; ++jj) X[jj] = o[jj];
-    }
+    panel_subst<D>(p, L, lv, tid, nthr);
     cluster_sync_all();
   }
+  for (int cc = warp * CPW; cc < p.N; cc += nwarps * CPW)
+    diag_rows_inverse<D>(p, L, cc, min(cc + CPW, p.N), nullptr);
+  cluster_sync_all();
   return true;
 }
 
