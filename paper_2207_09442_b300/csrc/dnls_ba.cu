@@ -460,9 +460,14 @@ __global__ void __launch_bounds__(256) k_ba_reduced(BAArgs a, int solve_only, co
 // updated by two columns at once, as there is one column per step).
 //   forward  L y = b:   y_k = L_kk^-1 b_k;        b_i -= L_ik y_k   (blocks below the diagonal)
 //   backward L^T x = y: x_k = L_kk^-T y_k;        y_j -= L_kj^T x_k (blocks left of the diagonal)
+// The vector lives in shared memory (6 N doubles, dynamic) when `smem` is set, else in the
+// workspace; each thread fetches the factor entries of its first item of the next step (and
+// threads 0-5 the next diagonal block's inverse row) before the step's closing barrier, so the
+// loads overlap the barrier and the next diagonal product.
 // rhs / out as for k_ba_reduced (solve_only 1: every active problem; 2: skip a failed factor).
 __global__ void __launch_bounds__(256) k_ba_solve_chain(BAArgs a, int solve_only, const double* rhs,
-                                                        double* out) {
+                                                        double* out, int smem) {
+  extern __shared__ double xs[];
   __shared__ double xk[6];
   const int b = blockIdx.x;
   BAState& s = a.st[b];
@@ -471,54 +476,104 @@ __global__ void __launch_bounds__(256) k_ba_solve_chain(BAArgs a, int solve_only
   RedView p;
   p.init(a, b);
   const int64_t c0 = a.d.cam_off[b];
-  double* x = p.dx;
-  for (int k = threadIdx.x; k < p.N * 6; k += blockDim.x) x[k] = rhs[(c0 + p.perm[k / 6]) * 6 + k % 6];
+  double* x = smem ? xs : p.dx;
+  const int t = threadIdx.x;
+  for (int k = t; k < p.N * 6; k += blockDim.x) x[k] = rhs[(c0 + p.perm[k / 6]) * 6 + k % 6];
+  // forward: item t of column k is row r = t % 6 of its (t / 6)-th block below the diagonal
+  auto fetch_fwd = [&](int lv, double* Bv, double* Iv) {
+    const int k = p.lvlcols[p.lvlptr[lv]];
+    const int q0 = p.colptr[k], cnt = p.colptr[k + 1] - q0;
+    if (t < cnt * 6) {
+      const double* B = p.L + (int64_t)(p.N + q0 + t / 6) * 36 + (t % 6) * 6;
+#pragma unroll
+      for (int m = 0; m < 6; ++m) Bv[m] = B[m];
+    }
+    if (t < 6) {
+      const double* I = p.Linv + (int64_t)k * 36 + t * 6;
+#pragma unroll
+      for (int m = 0; m < 6; ++m) Iv[m] = m <= t ? I[m] : 0.0;
+    }
+  };
+  double Bv[6] = {0, 0, 0, 0, 0, 0}, Iv[6] = {0, 0, 0, 0, 0, 0};
+  if (p.nlev > 0) fetch_fwd(0, Bv, Iv);
   __syncthreads();
   for (int lv = 0; lv < p.nlev; ++lv) {
     const int k = p.lvlcols[p.lvlptr[lv]];
-    if (threadIdx.x < 6) {
-      const int i = threadIdx.x;
-      const double* I = p.Linv + (int64_t)k * 36 + i * 6;
-      double acc = 0.0;
-      for (int m = 0; m <= i; ++m) acc = fma(I[m], x[k * 6 + m], acc);
-      xk[i] = acc;
-    }
-    __syncthreads();
-    if (threadIdx.x < 6) x[k * 6 + threadIdx.x] = xk[threadIdx.x];
-    const int q0 = p.colptr[k], cnt = p.colptr[k + 1] - q0;
-    for (int it = threadIdx.x; it < cnt * 6; it += blockDim.x) {
-      const int q = it / 6, r = it % 6;
-      const double* B = p.L + (int64_t)(p.N + q0 + q) * 36 + r * 6;
+    if (t < 6) {
       double acc = 0.0;
 #pragma unroll
-      for (int m = 0; m < 6; ++m) acc = fma(B[m], xk[m], acc);
+      for (int m = 0; m < 6; ++m) acc = fma(Iv[m], x[k * 6 + m], acc);
+      xk[t] = acc;
+    }
+    __syncthreads();
+    if (t < 6) x[k * 6 + t] = xk[t];
+    const int q0 = p.colptr[k], cnt = p.colptr[k + 1] - q0;
+    for (int it = t; it < cnt * 6; it += blockDim.x) {
+      const int q = it / 6, r = it % 6;
+      double Bm[6];
+      if (it == t) {
+#pragma unroll
+        for (int m = 0; m < 6; ++m) Bm[m] = Bv[m];
+      } else {
+        const double* B = p.L + (int64_t)(p.N + q0 + q) * 36 + r * 6;
+#pragma unroll
+        for (int m = 0; m < 6; ++m) Bm[m] = B[m];
+      }
+      double acc = 0.0;
+#pragma unroll
+      for (int m = 0; m < 6; ++m) acc = fma(Bm[m], xk[m], acc);
       x[p.rows[q0 + q] * 6 + r] -= acc;
     }
+    if (lv + 1 < p.nlev) fetch_fwd(lv + 1, Bv, Iv);
     __syncthreads();
   }
+  // backward: item t of row k is column c = t % 6 of its (t / 6)-th block left of the diagonal
+  auto fetch_bwd = [&](int lv, double* Bv, double* Iv) {
+    const int k = p.lvlcols[p.lvlptr[lv]];
+    const int e0 = p.rowptr[k], cnt = p.rowptr[k + 1] - e0;
+    if (t < cnt * 6) {
+      const double* B = p.L + (int64_t)p.rowent[2 * (e0 + t / 6)] * 36 + t % 6;
+#pragma unroll
+      for (int m = 0; m < 6; ++m) Bv[m] = B[m * 6];
+    }
+    if (t < 6) {
+      const double* I = p.Linv + (int64_t)k * 36 + t;
+#pragma unroll
+      for (int m = 0; m < 6; ++m) Iv[m] = m >= t ? I[m * 6] : 0.0;
+    }
+  };
+  if (p.nlev > 0) fetch_bwd(p.nlev - 1, Bv, Iv);
   for (int lv = p.nlev - 1; lv >= 0; --lv) {
     const int k = p.lvlcols[p.lvlptr[lv]];
-    if (threadIdx.x < 6) {
-      const int i = threadIdx.x;
-      const double* I = p.Linv + (int64_t)k * 36;
-      double acc = 0.0;
-      for (int m = i; m < 6; ++m) acc = fma(I[m * 6 + i], x[k * 6 + m], acc);
-      xk[i] = acc;
-    }
-    __syncthreads();
-    if (threadIdx.x < 6) x[k * 6 + threadIdx.x] = xk[threadIdx.x];
-    const int e0 = p.rowptr[k], cnt = p.rowptr[k + 1] - e0;
-    for (int it = threadIdx.x; it < cnt * 6; it += blockDim.x) {
-      const int q = it / 6, c = it % 6;
-      const double* B = p.L + (int64_t)p.rowent[2 * (e0 + q)] * 36 + c;  // block L(k, j), column c
+    if (t < 6) {
       double acc = 0.0;
 #pragma unroll
-      for (int m = 0; m < 6; ++m) acc = fma(B[m * 6], xk[m], acc);
-      x[p.rowent[2 * (e0 + q) + 1] * 6 + c] -= acc;
+      for (int m = 0; m < 6; ++m) acc = fma(Iv[m], x[k * 6 + m], acc);
+      xk[t] = acc;
     }
     __syncthreads();
+    if (t < 6) x[k * 6 + t] = xk[t];
+    const int e0 = p.rowptr[k], cnt = p.rowptr[k + 1] - e0;
+    for (int it = t; it < cnt * 6; it += blockDim.x) {
+      const int q = it / 6, c = it % 6;
+      double Bm[6];
+      if (it == t) {
+#pragma unroll
+        for (int m = 0; m < 6; ++m) Bm[m] = Bv[m];
+      } else {
+        const double* B = p.L + (int64_t)p.rowent[2 * (e0 + q)] * 36 + c;  // block L(k, j), column c
+#pragma unroll
+        for (int m = 0; m < 6; ++m) Bm[m] = B[m * 6];
+      }
+      double acc = 0.0;
+#pragma unroll
+      for (int m = 0; m < 6; ++m) acc = fma(Bm[m], xk[m], acc);
+      x[p.rowent[2 * (e0 + q) + 1] * 6 + c] -= acc;
+    }
+    if (lv > 0) fetch_bwd(lv - 1, Bv, Iv);
+    __syncthreads();
   }
-  for (int k = threadIdx.x; k < p.N * 6; k += blockDim.x) out[(c0 + p.perm[k / 6]) * 6 + k % 6] = x[k];
+  for (int k = t; k < p.N * 6; k += blockDim.x) out[(c0 + p.perm[k / 6]) * 6 + k % 6] = x[k];
 }
 
 // candidate cameras T Exp(delta_c) and points p + delta_p, delta_p = -u_p - H_pp^-1 sum H_cp^T dc
@@ -963,6 +1018,7 @@ struct BAHost {
       w_xc, w_xp, w_rc, w_rp, w_vc, w_vp, w_eb, w_ebq, w_st, w_solc, w_solp, w_zc, w_zp, w_hc, w_hp;
   int64_t ws_bytes = 0;
   bool red_chain = false;  // every elimination level of every reduced system holds one column
+  int red_max_n = 0;       // most cameras in one reduced system
 };
 
 struct BAHandle {
@@ -1069,7 +1125,10 @@ int build_ba_host(const dnls_ba_desc* desc, BAHost& H) {
                             red_ej.data(), DNLS_ORDER_MIN_DEGREE, &H.red, kRedCluster * 256);
   if (rc != DNLS_OK) return rc;
   H.red_chain = true;
-  for (const ProbMeta& m : H.red.meta) H.red_chain = H.red_chain && m.nlev == m.N;
+  for (const ProbMeta& m : H.red.meta) {
+    H.red_chain = H.red_chain && m.nlev == m.N;
+    H.red_max_n = std::max(H.red_max_n, m.N);
+  }
   // Schur gather targets: diagonal block of every camera, one block per camera pair
   H.tgt_ptr.assign(1, 0);
   for (int b = 0; b < B; ++b) {
@@ -1273,8 +1332,13 @@ void launch_reduced_factor(const BAHost& H, const BAArgs& a, cudaStream_t st) {
 
 // dc = (reduced factor)^-1 bc for every active problem
 void reduced_solve(const BAHost& H, const BAArgs& a, cudaStream_t st, int mode) {
-  if (H.red_chain)
-    k_ba_solve_chain<<<H.B, 256, 0, st>>>(a, mode, a.bc, a.dc);
+  if (H.red_chain) {
+    const size_t smem = (size_t)H.red_max_n * 6 * sizeof(double);
+    if (smem <= 48 * 1024)
+      k_ba_solve_chain<<<H.B, 256, smem, st>>>(a, mode, a.bc, a.dc, 1);
+    else
+      k_ba_solve_chain<<<H.B, 256, 0, st>>>(a, mode, a.bc, a.dc, 0);
+  }
   else
     k_ba_reduced<<<H.B, 256, 0, st>>>(a, mode, a.bc, a.dc, 0);
 }
