@@ -71,3 +71,34 @@ def test_large_single_problem():
     rm, rl, _ = pgo.implicit_grads(g, poses_of(b, theta, 0), v, "exact")
     assert rel(edges_of(b, gm, 0), rm) < 1e-6
     assert sol.info_dict()["status"][0] == 0
+
+
+def test_pure_chain_graph_every_level_one_column():
+    """Odometry chains without loop closures: the elimination tree is a path, every level holds
+    one column, and the whole factor is the top chain (its forward-solve pre-pass has no pairs
+    from outside the chain).  FP64 forward and implicit measurement gradients against the
+    oracle."""
+    b = synth.pgo_se3(batch=3, n_poses=24, n_lc=0, config_id=153, log_weights=True)
+    opts = layer.Options(algo="lm", iters=15, precision="fp64", tau=0.0)
+    sol, theta, (meas, wd, lw) = run_forward(b, opts)
+    st = layer.PoseGraphStructure.from_batch(b).stats()
+    assert st["n_levels_max"] == 24
+    info = sol.info_dict()
+    assert (info["status"] == 0).all()
+    v = torch.zeros(b.pose_offsets[-1], 6, dtype=torch.float64)
+    refs = {}
+    for k in range(b.batch):
+        g, ref, _ = oracle_solve(b, k, opts)
+        assert rel(poses_of(b, theta, k), ref) < 1e-9, k
+        th_k = poses_of(b, theta, k)
+        vk = pgo.tangent_grad(3, lambda X: pgo.pose_error_loss(3, X, g.theta_gt), th_k)
+        v[b.pose_offsets[k]:b.pose_offsets[k + 1]] = vk
+        refs[k] = pgo.implicit_grads(g, th_k, vk, "exact")
+    gm, gl = sol.backward(theta, v.to(DEV), meas, wd, lw)
+    torch.cuda.synchronize()
+    for k in range(b.batch):
+        rm, rl, _ = refs[k]
+        assert rel(edges_of(b, gm, k), rm) < 1e-8, k
+        # a tree of costs fits its measurements exactly (zero residuals at the optimum), so the
+        # optimum does not depend on the weights: both log-weight gradients vanish
+        assert float(edges_of(b, gl, k).abs().max()) < 1e-9 and float(rl.abs().max()) < 1e-9, k
