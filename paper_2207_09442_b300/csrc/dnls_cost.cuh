@@ -91,21 +91,20 @@ DNLS_HD void jt_r(const S* J, const S* r, S* g) {
 // Between cost, local gradients only: with u = J_r^-1(c)^T (w^2 c) (= J_j^T r),
 // J_i^T r = -Ad(A^-1)^T u, since J_i = -diag(w) J_r^-1(c) Ad(A^-1) and J_j = diag(w) J_r^-1(c).
 // Also returns the weighted residual r = w c.  Ainv = A^-1 = T_j^-1 T_i.
+// Both products are applied without forming the matrices (Group::jr_inv_T, Group::adjoint_T).
 template <int KIND, class S>
 DNLS_HD void between_grad(const S* Ainv, const S* E, const S* w, S* r, S* gi, S* gj) {
   typedef Group<KIND> G;
   constexpr int D = G::DOF;
-  S c[D], Jr[D * D], Ad[D * D], w2c[D];
+  S c[D], w2c[D];
   G::log(E, c);
-  G::jr_inv(c, Jr);
-  G::adjoint(Ainv, Ad);
 #pragma unroll
   for (int a = 0; a < D; ++a) {
     r[a] = w[a] * c[a];
     w2c[a] = w[a] * r[a];
   }
-  jt_r<D>(Jr, w2c, gj);
-  jt_r<D>(Ad, gj, gi);
+  G::jr_inv_T(c, w2c, gj);
+  G::adjoint_T(Ainv, gj, gi);
 #pragma unroll
   for (int b = 0; b < D; ++b) gi[b] = -gi[b];
 }

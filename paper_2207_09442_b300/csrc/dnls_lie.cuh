@@ -333,6 +333,66 @@ template <class S> DNLS_HD void se3_jr_inv(const S* xi, S* J) {
     }
 }
 
+// o = Ad(M)^T g for Ad(M) = [[R, [t]x R], [0, R]]: o_rho = R^T g_rho, o_phi = R^T (g_phi - t x g_rho)
+template <class S> DNLS_HD void se3_adjoint_T(const S* M, const S* g, S* o) {
+  const S t[3] = {M[3], M[7], M[11]};
+  S tg[3], h[3];
+  cross3(t, g, tg);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) h[k] = g[3 + k] - tg[k];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    o[c] = M[c] * g[0] + M[4 + c] * g[1] + M[8 + c] * g[2];
+    o[3 + c] = M[c] * h[0] + M[4 + c] * h[1] + M[8 + c] * h[2];
+  }
+}
+
+// u = J_r^-1(xi)^T v without forming the matrix.  With J_r^-1 = [[Ji, -Ji Q Ji], [0, Ji]] (as
+// above): u_rho = Ji^T v_rho, u_phi = Ji^T (v_phi - Q^T u_rho), where, for P = [phi]x and
+// R = [rho]x (skew, so every product's transpose is the reversed product times (-1)^factors),
+//   Ji^T y = y - 1/2 phi x y + dl phi x (phi x y),
+//   Q^T a = 1/2 R a + Cc (RP + PR + PRP) a + c2 (RPP + PPR - 3 PRP) a + c3 (PPRP + PRPP) a.
+template <class S> DNLS_HD void se3_jr_inv_T(const S* xi, const S* v, S* u) {
+  const S* rho = xi;
+  const S* phi = xi + 3;
+  S t2 = phi[0] * phi[0] + phi[1] * phi[1] + phi[2] * phi[2];
+  S Cc = coef_c(t2), c2 = coef_c2(t2), c3 = coef_c3(t2), dl = coef_dl(t2);
+  auto jit = [&](const S* y, S* o) {
+    S a[3], b[3];
+    cross3(phi, y, a);
+    cross3(phi, a, b);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) o[k] = y[k] - a[k] * DNLS_C(0.5) + dl * b[k];
+  };
+  S ur[3];
+  jit(v, ur);
+  S Pa[3], Ra[3], RPa[3], PRa[3], PRPa[3], PPa[3], RPPa[3], PPRa[3], PPRPa[3], PRPPa[3];
+  cross3(phi, ur, Pa);
+  cross3(rho, ur, Ra);
+  cross3(rho, Pa, RPa);
+  cross3(phi, Ra, PRa);
+  cross3(phi, RPa, PRPa);
+  cross3(phi, Pa, PPa);
+  cross3(rho, PPa, RPPa);
+  cross3(phi, PRa, PPRa);
+  cross3(phi, PRPa, PPRPa);
+  cross3(phi, RPPa, PRPPa);
+  S w[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const S qa = Ra[k] * DNLS_C(0.5) + Cc * (RPa[k] + PRa[k] + PRPa[k]) +
+                 c2 * (RPPa[k] + PPRa[k] - PRPa[k] * DNLS_C(3.0)) + c3 * (PPRPa[k] + PRPPa[k]);
+    w[k] = v[3 + k] - qa;
+  }
+  S uphi[3];
+  jit(w, uphi);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    u[k] = ur[k];
+    u[3 + k] = uphi[k];
+  }
+}
+
 // ad(xi)^T g for SE(3), ad(xi) = [[P, R], [0, P]] (P = [phi]x, R = [rho]x):
 //   ad^T g = (-phi x g_rho, -rho x g_rho - phi x g_phi)
 template <class S> DNLS_HD void se3_adT(const S* xi, const S* g, S* o) {
@@ -404,6 +464,27 @@ template <class S> DNLS_HD void se2_jr_inv(const S* xi, S* J) {
   J[3] = hp; J[4] = h; J[5] = -(hp * b0 + h * b1);
   J[6] = DNLS_C(0.0); J[7] = DNLS_C(0.0); J[8] = DNLS_C(1.0);
 }
+// o = Ad(P)^T g for Ad(P) = [[c, -s, y], [s, c, -x], [0, 0, 1]]
+template <class S> DNLS_HD void se2_adjoint_T(const S* P, const S* g, S* o) {
+  const S x = P[0], y = P[1], c = P[2], s = P[3];
+  const S o0 = c * g[0] + s * g[1];
+  const S o1 = c * g[1] - s * g[0];
+  const S o2 = y * g[0] - x * g[1] + g[2];
+  o[0] = o0; o[1] = o1; o[2] = o2;
+}
+// u = J_r^-1(xi)^T v for SE(2) (the transpose of se2_jr_inv applied to v)
+template <class S> DNLS_HD void se2_jr_inv_T(const S* xi, const S* v, S* u) {
+  S psi = xi[2];
+  S t2 = psi * psi;
+  S Bc = coef_b(t2), Cc = coef_c(t2);
+  S h = DNLS_C(1.0) - t2 * coef_dl(t2);
+  S hp = psi * DNLS_C(0.5);
+  S b0 = psi * Cc * xi[0] - Bc * xi[1];
+  S b1 = Bc * xi[0] + psi * Cc * xi[1];
+  u[0] = h * v[0] + hp * v[1];
+  u[1] = h * v[1] - hp * v[0];
+  u[2] = v[2] - (h * b0 - hp * b1) * v[0] - (hp * b0 + h * b1) * v[1];
+}
 // ad(xi)^T g for SE(2): ad = [[0, -psi, rho_y], [psi, 0, -rho_x], [0, 0, 0]]
 template <class S> DNLS_HD void se2_adT(const S* xi, const S* g, S* o) {
   S a0 = xi[2] * g[1];
@@ -423,6 +504,8 @@ template <> struct Group<3> {
   template <class S> DNLS_HD static void exp(const S* xi, S* a) { se3_exp(xi, a); }
   template <class S> DNLS_HD static void adjoint(const S* a, S* o) { se3_adjoint(a, o); }
   template <class S> DNLS_HD static void jr_inv(const S* xi, S* o) { se3_jr_inv(xi, o); }
+  template <class S> DNLS_HD static void jr_inv_T(const S* xi, const S* v, S* o) { se3_jr_inv_T(xi, v, o); }
+  template <class S> DNLS_HD static void adjoint_T(const S* a, const S* g, S* o) { se3_adjoint_T(a, g, o); }
   template <class S> DNLS_HD static void adT(const S* xi, const S* g, S* o) { se3_adT(xi, g, o); }
 };
 template <> struct Group<2> {
@@ -434,6 +517,8 @@ template <> struct Group<2> {
   template <class S> DNLS_HD static void exp(const S* xi, S* a) { se2_exp(xi, a); }
   template <class S> DNLS_HD static void adjoint(const S* a, S* o) { se2_adjoint(a, o); }
   template <class S> DNLS_HD static void jr_inv(const S* xi, S* o) { se2_jr_inv(xi, o); }
+  template <class S> DNLS_HD static void jr_inv_T(const S* xi, const S* v, S* o) { se2_jr_inv_T(xi, v, o); }
+  template <class S> DNLS_HD static void adjoint_T(const S* a, const S* g, S* o) { se2_adjoint_T(a, g, o); }
   template <class S> DNLS_HD static void adT(const S* xi, const S* g, S* o) { se2_adT(xi, g, o); }
 };
 
