@@ -59,21 +59,14 @@ template <int KIND, class S>
 DNLS_HD void meas_grad_neg(const S* E, const S* w, S* out) {
   typedef Group<KIND> G;
   constexpr int D = G::DOF;
-  S c[D], mc[D], Jl[D * D], wc[D];
+  S c[D], mc[D], wc[D];
   G::log(E, c);
 #pragma unroll
   for (int a = 0; a < D; ++a) {
     mc[a] = -c[a];
     wc[a] = w[a] * w[a] * c[a];
   }
-  G::jr_inv(mc, Jl);
-#pragma unroll
-  for (int b = 0; b < D; ++b) {
-    S acc = Jl[b] * wc[0];
-#pragma unroll
-    for (int a = 1; a < D; ++a) acc += Jl[D * a + b] * wc[a];
-    out[b] = acc;
-  }
+  G::jr_inv_T(mc, wc, out);
 }
 
 // local gradient of 1/2 ||r||^2 for one pose slot: J^T r

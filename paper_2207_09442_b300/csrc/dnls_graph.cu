@@ -1153,7 +1153,7 @@ __device__ double unroll_dF(const Prob<KIND>& p, int e, int dir, const double* t
   if (j >= 0) {
     Dd A[PW], Ai[PW], Em[PW];
     G::invmul(Ti, Tj, A);
-    G::invmul(Tj, Ti, Ai);
+    G::inv(A, Ai);
     G::invmul(Zd, A, Em);
     between_lin<KIND, Dd>(Ai, Em, wd, r, Ji, Jj);
   } else {
