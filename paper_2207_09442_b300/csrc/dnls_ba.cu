@@ -943,8 +943,11 @@ __global__ void k_bahvp_pts(BAArgs a) {
 // mode 0 (after z = M^-1 v):  p = z, rz = r.z
 // mode 1 (after h = H p):     alpha = rz / p.h; sol += alpha p; r -= alpha h; ||r|| test
 // mode 2 (after z = M^-1 r):  beta = r.z / rz; rz = r.z; p = z + beta p
-__global__ void __launch_bounds__(256) k_pcg(BAArgs a, const int64_t* pt_off, int mode, int step) {
-  __shared__ double red[256];
+// One CTA of kPcgThreads per problem: the vectors are ~13 k doubles per problem, so the wide CTA
+// keeps each thread's serial share (and its chain of loads and FMAs) short.
+constexpr int kPcgThreads = 1024;
+__global__ void __launch_bounds__(kPcgThreads) k_pcg(BAArgs a, const int64_t* pt_off, int mode, int step) {
+  __shared__ double red[kPcgThreads];
   __shared__ double s_alpha;
   const int b = blockIdx.x;
   BAState& s = a.st[b];
@@ -1499,14 +1502,14 @@ dnls_status dnls_ba_backward(const dnls_ba* h, const dnls_solver_opts* opts, con
     k_bap_pts<<<nblk(H.P, 128), 128, 0, st>>>(a);
   };
   precondition();
-  k_pcg<<<H.B, 256, 0, st>>>(a, h->impl.d_pt_off, 0, 0);
+  k_pcg<<<H.B, kPcgThreads, 0, st>>>(a, h->impl.d_pt_off, 0, 0);
   for (int it = 0; it < opts->refine_max; ++it) {
     k_bahvp_obs<<<nblk(H.O, 128), 128, 0, st>>>(a, 0);   // h = H p (true Hessian)
     k_bahvp_cams<<<nblk((int64_t)H.C * 32, 256), 256, 0, st>>>(a);
     k_bahvp_pts<<<nblk(H.P, 128), 128, 0, st>>>(a);
-    k_pcg<<<H.B, 256, 0, st>>>(a, h->impl.d_pt_off, 1, it);
+    k_pcg<<<H.B, kPcgThreads, 0, st>>>(a, h->impl.d_pt_off, 1, it);
     precondition();
-    k_pcg<<<H.B, 256, 0, st>>>(a, h->impl.d_pt_off, 2, it);
+    k_pcg<<<H.B, kPcgThreads, 0, st>>>(a, h->impl.d_pt_off, 2, it);
   }
   k_pcg_sol<<<nblk(H.C * 6 + H.P * 3, 256), 256, 0, st>>>(a);
   k_bab_finish<<<nb, 256, 0, st>>>(a);
