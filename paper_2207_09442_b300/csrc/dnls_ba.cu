@@ -408,7 +408,7 @@ __global__ void k_ba_schur(BAArgs a, double lam_override) {
 // The reduced camera system is complete (every camera pair shares points), so its factorization
 // is dense-structured work of 384^3/3 FP64 flops per problem: one CTA would run it at one SM's
 // FP64 rate while most SMs idle.  It runs on a cluster of kRedCluster CTAs per problem instead.
-constexpr int kRedCluster = 4;
+constexpr int kRedCluster = 8;  // measured: 4 -> 35.3, 8 -> 31.1, 16 -> 37.9 ms per BA forward
 
 __global__ void __launch_bounds__(256) k_ba_reduced_factor(BAArgs a) {
   const int b = blockIdx.x / kRedCluster, rank = blockIdx.x % kRedCluster;
