@@ -237,16 +237,42 @@ __global__ void k_ba_points(BAArgs a, double lam_override) {
   const double lam = lam_override >= 0.0 ? lam_override : s.lam;
   double H[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, g[3] = {0, 0, 0};
   const int o0 = a.d.pt_ptr[q], o1 = a.d.pt_ptr[q + 1];
+  // mixed path: H_pp and H_cp products in FP32 (the assembly precision; the Jacobians are FP32
+  // already); g, the inverse and Y = H_cp H_pp^-1 (Schur complement) in FP64
+  float hf[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
   for (int k = o0; k < o1; ++k) {
     const int64_t o = a.d.pt_obs[k];
     double r[2], Jc[12], Jp[6];
     load_obsJ(a, o, r, Jc, Jp);
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      g[i] += Jp[i] * r[0] + Jp[3 + i] * r[1];
+    for (int i = 0; i < 3; ++i) g[i] += Jp[i] * r[0] + Jp[3 + i] * r[1];
+    if (a.mixed) {
+      const float* Jf = (const float*)a.J + o * kJW + 14;
+      int t = 0;
 #pragma unroll
-      for (int j = 0; j < 3; ++j) H[3 * i + j] += Jp[i] * Jp[j] + Jp[3 + i] * Jp[3 + j];
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = i; j < 3; ++j) {
+          hf[t] = fmaf(Jf[i], Jf[j], fmaf(Jf[3 + i], Jf[3 + j], hf[t]));
+          ++t;
+        }
+    } else {
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) H[3 * i + j] += Jp[i] * Jp[j] + Jp[3 + i] * Jp[3 + j];
     }
+  }
+  if (a.mixed) {
+    int t = 0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = i; j < 3; ++j) {
+        H[3 * i + j] = (double)hf[t];
+        H[3 * j + i] = (double)hf[t];
+        ++t;
+      }
   }
 #pragma unroll
   for (int i = 0; i < 3; ++i) H[4 * i] += lam * fmax(H[4 * i], kDiagFloor);
@@ -268,10 +294,18 @@ __global__ void k_ba_points(BAArgs a, double lam_override) {
     double r[2], Jc[12], Jp[6];
     load_obsJ(a, o, r, Jc, Jp);
     double Hc[18];
+    if (a.mixed) {
+      const float* Jf = (const float*)a.J + o * kJW + 2;  // Jc (12) then Jp (6)
 #pragma unroll
-    for (int i = 0; i < 6; ++i)
+      for (int i = 0; i < 6; ++i)
 #pragma unroll
-      for (int j = 0; j < 3; ++j) Hc[3 * i + j] = Jc[i] * Jp[j] + Jc[6 + i] * Jp[3 + j];
+        for (int j = 0; j < 3; ++j) Hc[3 * i + j] = (double)fmaf(Jf[i], Jf[12 + j], Jf[6 + i] * Jf[15 + j]);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 6; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) Hc[3 * i + j] = Jc[i] * Jp[j] + Jc[6 + i] * Jp[3 + j];
+    }
 #pragma unroll
     for (int i = 0; i < 18; ++i) a.Hcp[o * 18 + i] = Hc[i];
 #pragma unroll
@@ -312,22 +346,44 @@ __global__ void k_ba_cameras(BAArgs a) {
   double v[33];  // upper triangle of H (21), g (6), sum H_cp u (6)
 #pragma unroll
   for (int k = 0; k < 33; ++k) v[k] = 0.0;
+  // mixed path: each lane sums its observations' H_cc terms in FP32 (the assembly precision of
+  // J^T J; the Jacobians are FP32 already), then converts once before the FP64 warp sum; g stays
+  // an FP64 sum
+  float hf[21];
+#pragma unroll
+  for (int k = 0; k < 21; ++k) hf[k] = 0.0f;
   for (int k = a.d.cam_ptr[c] + lane; k < a.d.cam_ptr[c + 1]; k += 32) {
     const int64_t o = a.d.cam_obs[k];
     double r[2], Jc[12], Jp[6];
     load_obsJ(a, o, r, Jc, Jp);
     int t = 0;
+    if (a.mixed) {
+      const float* Jf = (const float*)a.J + o * kJW + 2;
 #pragma unroll
-    for (int i = 0; i < 6; ++i) {
-      v[21 + i] += Jc[i] * r[0] + Jc[6 + i] * r[1];
+      for (int i = 0; i < 6; ++i) {
+        v[21 + i] += Jc[i] * r[0] + Jc[6 + i] * r[1];
 #pragma unroll
-      for (int j = i; j < 6; ++j) v[t++] += Jc[i] * Jc[j] + Jc[6 + i] * Jc[6 + j];
+        for (int j = i; j < 6; ++j) {
+          hf[t] = fmaf(Jf[i], Jf[j], fmaf(Jf[6 + i], Jf[6 + j], hf[t]));
+          ++t;
+        }
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < 6; ++i) {
+        v[21 + i] += Jc[i] * r[0] + Jc[6 + i] * r[1];
+#pragma unroll
+        for (int j = i; j < 6; ++j) v[t++] += Jc[i] * Jc[j] + Jc[6 + i] * Jc[6 + j];
+      }
     }
     const double* u = a.up + (int64_t)a.d.obs_pt[o] * 3;
     const double* Hc = a.Hcp + o * 18;
 #pragma unroll
     for (int i = 0; i < 6; ++i) v[27 + i] += Hc[3 * i] * u[0] + Hc[3 * i + 1] * u[1] + Hc[3 * i + 2] * u[2];
   }
+  if (a.mixed)
+#pragma unroll
+    for (int k = 0; k < 21; ++k) v[k] = (double)hf[k];
   warp_sum<33>(v);
   if (lane != 0) return;
   double H[36], g[6];
