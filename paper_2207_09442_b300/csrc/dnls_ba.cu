@@ -959,15 +959,14 @@ __global__ void k_bahvp_cams(BAArgs a) {
   const double* x = a.xc + c * 6;
   for (int k = a.d.cam_prior_ptr[c]; k < a.d.cam_prior_ptr[c + 1]; ++k) {
     const int64_t q = a.d.cam_prior[k];
-    Dd T[12], Z[12], E[12], w[6], r[6], J[36], g[6];
+    Dd T[12], Z[12], E[12], w[6], r[6], g[6];
     pose_dual<3>(a.cams + c * 12, x, T);
 #pragma unroll
     for (int m = 0; m < 12; ++m) Z[m] = Dd(a.prior_meas[q * 12 + m]);
 #pragma unroll
     for (int m = 0; m < 6; ++m) w[m] = Dd(a.prior_w[q * 6 + m]);
     se3_invmul(Z, T, E);
-    prior_lin<3, Dd>(E, w, r, J);
-    jt_r<6>(J, r, g);
+    prior_grad<3, Dd>(E, w, r, g);
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
       gs[i] += g[i].v;

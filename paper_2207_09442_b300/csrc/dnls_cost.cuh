@@ -102,6 +102,22 @@ DNLS_HD void between_grad(const S* Ainv, const S* E, const S* w, S* r, S* gi, S*
   for (int b = 0; b < D; ++b) gi[b] = -gi[b];
 }
 
+// Prior cost, local gradient only: J^T r = J_r^-1(c)^T (w^2 c), J = diag(w) J_r^-1(c); also
+// returns r = w c.
+template <int KIND, class S>
+DNLS_HD void prior_grad(const S* E, const S* w, S* r, S* g) {
+  typedef Group<KIND> G;
+  constexpr int D = G::DOF;
+  S c[D], w2c[D];
+  G::log(E, c);
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    r[a] = w[a] * c[a];
+    w2c[a] = w[a] * r[a];
+  }
+  G::jr_inv_T(c, w2c, g);
+}
+
 // pose T (+) (t x) as a dual number in t at t = 0: value T, derivative T x^ (the derivative of
 // Exp at the identity is the hat map: for SE(3) [[phi]x | rho], for SE(2) the rotation
 // derivative (0, psi) and the translation derivative rho).

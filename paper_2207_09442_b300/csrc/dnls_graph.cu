@@ -735,7 +735,7 @@ __device__ void hvp_exact(Prob<KIND>& p, const double* x, double* hx) {
     const int i = p.ei[e], j = p.ej[e];
     double w[D];
     p.weight(e, w);
-    Dd wd[D], Ti[PW], Zd[PW], r[D], Ji[D * D], gi[D];
+    Dd wd[D], Ti[PW], Zd[PW], r[D], gi[D];
 #pragma unroll
     for (int k = 0; k < D; ++k) wd[k] = Dd(w[k]);
 #pragma unroll
@@ -765,8 +765,7 @@ __device__ void hvp_exact(Prob<KIND>& p, const double* x, double* hx) {
     } else {
       Dd Em[PW];
       G::invmul(Zd, Ti, Em);
-      prior_lin<KIND, Dd>(Em, wd, r, Ji);
-      jt_r<D>(Ji, r, gi);
+      prior_grad<KIND, Dd>(Em, wd, r, gi);
       if (p.logrc) {
         const Dd w1 = welsch_d1<D>(r, p.logrc[e]);
 #pragma unroll
