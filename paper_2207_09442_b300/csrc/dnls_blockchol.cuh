@@ -325,9 +325,12 @@ __device__ bool block_factor_cluster(F& p, double lam, int rank, int nranks, int
   return true;
 }
 
-// In place: x <- (L L^T)^-1 x (positions order, FP64), level by level.
-template <int D, class F>
+// In place: x <- (L L^T)^-1 x (positions order, FP64), level by level.  kTopChain = false leaves
+// out the top chain's pre-pass (the same result up to summation order, less code: used where
+// registers are scarce).
+template <int D, bool kTopChain = true, class F>
 __device__ void block_solve(F& p, double* x) {
+  const int chain_lev = kTopChain ? p.chain_lev : p.nlev;
   constexpr int BS = D * D;
   const double* L = p.L;
   for (int lv = 0; lv < p.nlev; ++lv) {
@@ -336,8 +339,8 @@ __device__ void block_solve(F& p, double* x) {
     // outside the chain, whose values are final once the levels below are done, are summed for
     // all chain rows at once before the first chain level; each chain level then only adds the
     // pairs from chain columns (rowent from rsplit[k] on).
-    const bool chain = lv >= p.chain_lev;
-    if (lv == p.chain_lev) {
+    const bool chain = lv >= chain_lev;
+    if (lv == chain_lev) {
       const int LN = p.slanes[p.nlev], lsh = __ffs(LN) - 1;
       const int n1 = (p.nlev - lv) * D * LN;
       for (int base = 0; base < n1; base += blockDim.x) {

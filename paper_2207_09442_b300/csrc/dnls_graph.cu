@@ -358,9 +358,9 @@ __device__ __forceinline__ bool factor(Prob<KIND>& p, double lam, int* sflag, in
                                        double shift = 0.0) {
   return block_factor<Group<KIND>::DOF>(p, lam, sflag, gen, shift);
 }
-template <int KIND>
+template <int KIND, bool kTopChain = true>
 __device__ __forceinline__ void chol_solve(Prob<KIND>& p, double* x) {
-  block_solve<Group<KIND>::DOF>(p, x);
+  block_solve<Group<KIND>::DOF, kTopChain>(p, x);
 }
 
 template <int KIND>
@@ -1283,7 +1283,7 @@ __device__ void unroll_problem(const KArgs& a, int b, char* smem, double* red, i
       p.bx[it] = sa;
     }
     __syncthreads();
-    chol_solve<KIND>(p, p.dx);  // y = (H_t + lambda_t D_t)^-1 delta_bar
+    chol_solve<KIND, false>(p, p.dx);  // y = (H_t + lambda_t D_t)^-1 delta_bar
     const int ndir = 3 * D + 1 + (robust ? 1 : 0);
     for (int it = threadIdx.x; it < p.E * ndir; it += blockDim.x) {
       const int e = it / ndir, dir = it % ndir;

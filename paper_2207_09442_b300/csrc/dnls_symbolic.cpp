@@ -411,7 +411,8 @@ int build_graph_host(int kind, int B, const int64_t* pose_offsets, const int64_t
       for (int k : bylev[l]) {
         int64_t nonchain = 0;
         for (auto& pr : rowl[k]) nonchain += lev[pr.second] < chain_lev;
-        fwd += l >= chain_lev ? (int64_t)rowl[k].size() - nonchain : (int64_t)rowl[k].size();
+        // full row lengths: the same lanes serve solves with and without the chain's pre-pass
+        fwd += (int64_t)rowl[k].size();
         if (l >= chain_lev) pre_terms += nonchain;
         bwd += (int64_t)rows[k].size();
       }
