@@ -82,8 +82,9 @@ enum { DNLS_ORDER_MIN_DEGREE = 0, DNLS_ORDER_NATURAL = 1 };
 typedef struct {
   int32_t algo;            /* DNLS_GN, DNLS_LM or DNLS_DOGLEG (pose graphs only) */
   int32_t iters;           /* number of iterations K (>= 0) */
-  int32_t precision;       /* DNLS_FP64, or DNLS_MIXED_FP32 (residuals, Jacobians and H in FP32;
-                              relative poses, g, the factorization and the acceptance in FP64) */
+  int32_t precision;       /* DNLS_FP64, or DNLS_MIXED_FP32 (residuals, Jacobians and H in FP32,
+                              each cost's term of g in FP32; relative poses, the sum of g, the
+                              Schur complement, the factorization and the acceptance in FP64) */
   int32_t backward_mode;   /* DNLS_IMPLICIT_EXACT (true Hessian of S), DNLS_IMPLICIT_GN,
                               DNLS_BACKWARD_DLM or DNLS_BACKWARD_UNROLL */
   int32_t refine_max;      /* max (preconditioned CG) steps of the adjoint solve (>= 1) */
