@@ -1,8 +1,9 @@
 // Level-scheduled, left-looking block Cholesky of a block-sparse SPD matrix and the matching
-// triangular solves, run by one CTA (Sec. 4.2's sparse Cholesky with a symbolic factorization
-// computed once per structure).  The view type F supplies the symbolic structure and buffers
-// (fields N, nnzL, nlev, H, L, Linv, tmp, lsrc, tgtptr, tgt, gptr, gsrc, lvlptr, lvlcols,
-// panptr, pan, rowptr, rowent, colptr, rows, glanes, slanes; see ProbMeta in dnls_graph.h for their meaning).
+// triangular solves, run by one CTA or by the CTAs of a thread-block cluster (Sec. 4.2's sparse
+// Cholesky with a symbolic factorization computed once per structure).  The view type F supplies
+// the symbolic structure and buffers (fields N, nnzL, nlev, chain_lev, H, L, Linv, tmp, lsrc,
+// tgtptr, tgt, gptr, gsrc, gsplit, lvlptr, lvlcols, panptr, pan, rowptr, rowent, rsplit, colptr,
+// rows, glanes, slanes; see ProbMeta in dnls_graph.h for their meaning).
 // Every output element is produced by one thread in a fixed order: no atomics, bitwise
 // reproducible results.
 #pragma once
