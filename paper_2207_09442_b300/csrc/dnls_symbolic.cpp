@@ -177,7 +177,7 @@ int build_graph_host(int kind, int B, const int64_t* pose_offsets, const int64_t
     // gather lists: per target block of column k, the (L(r,j), L(k,j)) pairs, j in rowl[k]
     std::vector<std::vector<std::vector<int>>> gl(N);  // gl[k][t] flat pairs, t=0 diag, 1+a off
     std::vector<std::vector<std::vector<int>>> glv(N);  // level of each pair's source column
-    int64_t n_upd = 0;
+    int64_t n_upd = 0, n_upd_diag = 0;  // block updates; those into diagonal blocks
     for (int k = 0; k < N; ++k) {
       gl[k].assign(1 + rows[k].size(), {});
       glv[k].assign(1 + rows[k].size(), {});
@@ -199,6 +199,7 @@ int build_graph_host(int kind, int B, const int64_t* pose_offsets, const int64_t
           gl[k][t].push_back(bkj);
           glv[k][t].push_back(lev[j]);
           ++n_upd;
+          n_upd_diag += t == 0;
         }
       }
     }
@@ -472,7 +473,10 @@ int build_graph_host(int kind, int B, const int64_t* pose_offsets, const int64_t
     G.n_blocks_L += N + nnzL;
     G.n_upd += n_upd;
     const double D3 = (double)D * D * D;
-    const double ff = 2.0 * n_upd * D3 + (double)nnzL * D * D * (D + 1) + N * (2.0 * D3 / 3.0);
+    // algorithmic count: an update into a diagonal block needs only its lower triangle
+    // (D (D + 1) / 2 outputs; the kernel forms the full block)
+    const double ff = 2.0 * (n_upd - n_upd_diag) * D3 + (double)n_upd_diag * D * D * (D + 1) +
+                      (double)nnzL * D * D * (D + 1) + N * (2.0 * D3 / 3.0);
     G.factor_flops += ff;
     G.prob_flops.push_back(ff);
     G.dense_flops += (double)n * n * n / 3.0;
