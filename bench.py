@@ -383,8 +383,8 @@ def run_pose_graphs(args, rank, world, local, dist, out):
                              else f"{int(sizes.min())}..{int(sizes.max())}"),
                    "costs": st.n_costs, "iterations": iters, "algorithm": algo.upper(),
                    "precision": precision,
-                   "backward": {"implicit": "implicit, true Hessian, cached factor + refinement",
-                                "implicit_gn": "implicit, Gauss-Newton Hessian, cached factor + refinement",
+                   "backward": {"implicit": "implicit, true Hessian, PCG preconditioned by the cached factor",
+                                "implicit_gn": "implicit, Gauss-Newton Hessian, PCG preconditioned by the cached factor",
                                 "dlm": "direct loss minimization (one GN step, eps 1e-2)",
                                 "unroll": (f"truncated backpropagation, last {args.trunc} iterations"
                                            if args.trunc else "backpropagation through all iterations")}[bmode],
@@ -411,7 +411,7 @@ def run_pose_graphs(args, rank, world, local, dist, out):
                        "frac": achieved / peak,
                        "traffic": captured_traffic(name, B) if algo != "dogleg" else None,
                        "kernel": f"{kname}<{batch.kind},{'double' if precision == 'fp64' else 'float'}>"
-                                 " (FP64 block Cholesky flops of the factorizations run)",
+                                 " (algorithmic FP64 block Cholesky flops of the factorizations run)",
                        "peak_source": "FP64 FMA probe on this GPU (dnls_probe_fp64_peak), of measured"}
     out["factor"] = {"flops_per_factorization_batch": stats["factor_flops"],
                      "dense_equivalent_flops": stats["dense_flops"],
