@@ -425,38 +425,28 @@ __global__ void k_ba_cameras(BAArgs a) {
   }
 }
 
-// reduced system, one thread per (block, row, half row): S = damped H_cc - sum Y_o1 H_cp(o2)^T
+// reduced system, one thread per element of each target block: S = damped H_cc - sum Y_o1 H_cp(o2)^T
 __global__ void k_ba_schur(BAArgs a, double lam_override) {
   const int64_t it = gtid();
-  if (it >= a.d.ntgt * 12) return;
-  const int64_t t = it / 12;
-  const int i = (int)(it % 12) >> 1, j0 = 3 * ((int)it & 1);
+  if (it >= a.d.ntgt * 36) return;
+  const int64_t t = it / 36;
+  const int el = (int)(it % 36), i = el / 6, j = el % 6;
   const BAState& s = a.st[a.d.tgt_prob[t]];
   if (!s.active) return;
   const double lam = lam_override >= 0.0 ? lam_override : s.lam;
-  double acc[3];
+  double acc = 0.0;
   const int cam = a.d.tgt_cam[t];
   if (cam >= 0) {
-    const double* H = a.Hcc + (int64_t)cam * 36 + 6 * i + j0;
-#pragma unroll
-    for (int j = 0; j < 3; ++j) acc[j] = H[j];
-    if (i >= j0 && i < j0 + 3) acc[i - j0] += lam * fmax(H[i - j0], kDiagFloor);
-  } else {
-#pragma unroll
-    for (int j = 0; j < 3; ++j) acc[j] = 0.0;
+    acc = a.Hcc[(int64_t)cam * 36 + el];
+    if (i == j) acc += lam * fmax(acc, kDiagFloor);
   }
   for (int q = a.d.tgt_ptr[t]; q < a.d.tgt_ptr[t + 1]; ++q) {
     const int64_t o1 = a.d.tgt_pairs[2 * q], o2 = a.d.tgt_pairs[2 * q + 1];
     const double* Yr = a.Y + o1 * 18 + 3 * i;
-    const double* Hc = a.Hcp + o2 * 18 + 3 * j0;
-    const double y0 = -Yr[0], y1 = -Yr[1], y2 = -Yr[2];
-#pragma unroll
-    for (int j = 0; j < 3; ++j)
-      acc[j] = fma(y2, Hc[3 * j + 2], fma(y1, Hc[3 * j + 1], fma(y0, Hc[3 * j], acc[j])));
+    const double* Hc = a.Hcp + o2 * 18 + 3 * j;
+    acc = fma(-Yr[2], Hc[2], fma(-Yr[1], Hc[1], fma(-Yr[0], Hc[0], acc)));
   }
-  double* out = (double*)(a.ws + a.d.tgt_off[t]) + 6 * i + j0;
-#pragma unroll
-  for (int j = 0; j < 3; ++j) out[j] = acc[j];
+  ((double*)(a.ws + a.d.tgt_off[t]))[el] = acc;
 }
 
 // one CTA per problem: factor the reduced system (already damped) and solve for delta_c;
@@ -1411,7 +1401,7 @@ void ba_eliminate_and_factor(const dnls_ba* h, BAArgs& a, cudaStream_t st, doubl
     k_ba_lin<double><<<nblk(H.O, 256), 256, 0, st>>>(a);
   k_ba_points<<<nblk(H.P, 128), 128, 0, st>>>(a, lam_override);
   k_ba_cameras<<<nblk((int64_t)H.C * 32, 256), 256, 0, st>>>(a);  // one warp per camera
-  k_ba_schur<<<nblk(H.red.meta.empty() ? 1 : (int64_t)H.tgt_cam.size() * 12, 128), 128, 0, st>>>(a, lam_override);
+  k_ba_schur<<<nblk(H.red.meta.empty() ? 1 : (int64_t)H.tgt_cam.size() * 36, 128), 128, 0, st>>>(a, lam_override);
   launch_reduced_factor(H, a, st);
   reduced_solve(H, a, st, 2);
 }
