@@ -309,6 +309,33 @@ dnls_status dnls_ba_backward(const dnls_ba* h, const dnls_solver_opts* opts, con
                              const double* v_pts, double* grad_obs, double* grad_log_delta,
                              void* workspace, size_t workspace_bytes, void* stream, dnls_info* info);
 
+/* ------------------------------------------------------------------------------------------
+ * Dense batched SPD solves on the tensor cores (the dense solve of the normal equations, Sec. 2;
+ * the reduced camera systems left by the Schur complement, Sec. 4.2, are solved the same way
+ * inside dnls_ba_forward / dnls_ba_backward).  Per problem b:
+ *   1. A~ = D A_b D with D = diag(2^-floor(log2(A_ii) / 2)) (exact power-of-two scaling);
+ *   2. L~ L~^T = A~ in FP32 on the tensor cores: 32-wide right-looking panels, trailing updates
+ *      as tcgen05.mma on a three-term BF16 split of each panel with FP32 accumulation in tensor
+ *      memory (FP32-level accuracy); a failed pivot retries with A~ + sigma I, sigma = 1e-5 then
+ *      1e-3;
+ *   3. conjugate gradients in FP64 on A~ y = D rhs_b preconditioned by L~ L~^T, stopped once
+ *      ||D rhs - A~ y|| <= tol ||D rhs|| or after max_steps steps; x_b = D y.
+ *   A:   device [batch, n, n] FP64 row-major, symmetric positive definite; only the lower
+ *        triangle (j <= i) is read.
+ *   rhs: device [batch, n] FP64.   x: device [batch, n] FP64 output (NaN where the factor failed).
+ *   max_steps = 0 returns x = D (L~ L~^T)^-1 D rhs, the preconditioner alone (FP32 accuracy).
+ *   steps (device int32 [batch], may be NULL): CG steps taken; -1 when the factorization failed
+ *        at every shift, -2 on a CG breakdown (p^T A p <= 0: A not positive definite).
+ *   resid (device double [batch], may be NULL): final ||D rhs - A~ y|| / ||D rhs||.
+ *   workspace: device, 256-byte aligned, dnls_dense_spd_workspace_size bytes, owned by the caller.
+ * n <= DNLS_DENSE_MAX_N (DNLS_ERR_UNSUPPORTED beyond).  Errors: DNLS_ERR_ARG,
+ * DNLS_ERR_WORKSPACE, DNLS_ERR_UNSUPPORTED, DNLS_ERR_CUDA. */
+#define DNLS_DENSE_MAX_N 384
+dnls_status dnls_dense_spd_workspace_size(int32_t batch, int32_t n, size_t* bytes);
+dnls_status dnls_dense_spd_solve(int32_t batch, int32_t n, const double* A, const double* rhs, double* x,
+                                 int32_t max_steps, double tol, void* workspace, size_t workspace_bytes,
+                                 void* stream, int32_t* steps, double* resid);
+
 /* Sizes of the symbolic factorization (host values; for reports and tests). */
 typedef struct {
   int64_t n_poses, n_costs, n_blocks_L, n_block_updates, n_levels_max;

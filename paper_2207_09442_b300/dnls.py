@@ -61,6 +61,7 @@ class BAInputs(ctypes.Structure):
                 ("focal", c_double), ("huber_delta", c_double)]
 
 
+DENSE_MAX_N = 384
 INFO_BYTES = 56  # dnls_info: 4 doubles + 6 int32
 
 
@@ -98,6 +99,9 @@ _SIGS = {
                                    c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                    c_void_p, c_size_t, c_void_p, c_void_p]),
     "dnls_probe_fp64_peak": (c_int32, [c_int32, c_void_p, ctypes.POINTER(c_double)]),
+    "dnls_dense_spd_workspace_size": (c_int32, [c_int32, c_int32, ctypes.POINTER(c_size_t)]),
+    "dnls_dense_spd_solve": (c_int32, [c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_int32, c_double,
+                                       c_void_p, c_size_t, c_void_p, c_void_p, c_void_p]),
 }
 
 
