@@ -65,6 +65,11 @@ enum { DNLS_FP64 = 0, DNLS_MIXED_FP32 = 1 };
  * for pose graphs only */
 enum { DNLS_IMPLICIT_EXACT = 0, DNLS_IMPLICIT_GN = 1, DNLS_BACKWARD_DLM = 2, DNLS_BACKWARD_UNROLL = 3 };
 enum { DNLS_ORDER_MIN_DEGREE = 0, DNLS_ORDER_NATURAL = 1 };
+/* solver of the bundle-adjustment reduced camera system (Sec. 4.2): the tensor-core FP32 factor
+ * with FP64 conjugate gradients (as dnls_dense_spd_solve), or the FP64 block Cholesky with direct
+ * triangular solves; AUTO takes the tensor cores when every reduced system has order
+ * 6 * cameras <= DNLS_DENSE_MAX_N */
+enum { DNLS_REDUCED_AUTO = 0, DNLS_REDUCED_TC = 1, DNLS_REDUCED_FP64 = 2 };
 
 /* Solver options (paper Sec. 3: optimizer choice, max_iterations, backward_mode).  The LM
  * damping rule is not given in the paper; this library uses: damping matrix
@@ -98,7 +103,8 @@ typedef struct {
   double radius0;          /* DNLS_DOGLEG: initial trust radius (> 0) */
   int32_t trunc_steps;     /* DNLS_BACKWARD_UNROLL: differentiate only the last trunc_steps
                               iterations (truncated backpropagation); 0 = all (unrolling) */
-  int32_t reserved;        /* zero */
+  int32_t reduced_solver;  /* bundle adjustment: DNLS_REDUCED_AUTO (0), DNLS_REDUCED_TC or
+                              DNLS_REDUCED_FP64; pose graphs ignore it */
 } dnls_solver_opts;
 
 /* Per-problem report (device array of `batch` entries, written by forward/backward). */

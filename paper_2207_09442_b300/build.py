@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libdnls.so")
-SOURCES = ["dnls_graph.cu", "dnls_symbolic.cpp", "dnls_misc.cu", "dnls_ba.cu", "dnls_dense.cu"]
+SOURCES = ["dnls_graph.cu", "dnls_symbolic.cpp", "dnls_misc.cu", "dnls_ba.cu", "dnls_dense.cu", "dnls_tc.cu"]
 HEADERS = ["dnls_lie.cuh", "dnls_cost.cuh", "dnls_graph.h", "dnls_blockchol.cuh", "dnls_reproj.cuh", "dnls_tc.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

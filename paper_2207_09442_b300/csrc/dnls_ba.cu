@@ -11,7 +11,10 @@
 //   cameras  per camera: H_cc (+ priors), g_c, reduced rhs b_c = -g_c + sum H_cp u_p
 //   schur    per 6x6 block of the reduced camera system, one thread per row: damped H_cc minus
 //            sum_{o1,o2 on one point} Y_o1 H_cp(o2)^T over a fixed-order list (no atomics)
-//   reduced  one CTA per problem: level-scheduled block Cholesky + solves of the reduced system
+//   reduced  tensor cores (every reduced system of order <= 384): the damped reduced system
+//            scaled to unit-size diagonal, an FP32 factor with BF16-split trailing updates on
+//            tcgen05 (dnls_tc.cuh), FP64 conjugate gradients preconditioned by it; otherwise an
+//            8-CTA cluster block Cholesky in FP64 and a direct chained solve
 //   update   cameras T Exp(delta_c); points p - u_p - H_pp^-1 sum H_cp^T delta_c
 //   eval     FP64 objective at the candidate; accept: per-problem LM decision; commit.
 #include <cuda_runtime.h>
@@ -29,6 +32,7 @@
 #include "dnls_cost.cuh"
 #include "dnls_graph.h"
 #include "dnls_reproj.cuh"
+#include "dnls_tc.cuh"
 
 namespace dnls {
 
@@ -39,9 +43,11 @@ constexpr int kJW = 20;  // per observation: r (2), J_cam (12), J_pt (6)
 
 struct BAState {
   double lam, S, Sc, lam_fact, rel, vnorm, rz;
+  double inner_resid;  // largest final relative residual of the forward's reduced CG solves
   int32_t active, need_lin, bad, accepted_last;
   int32_t iters, accepted, status, factor_ok;
-  int32_t refine_steps, fact_flag, pad[2];  // fact_flag: failed-pivot flag of the cluster factor
+  int32_t refine_steps, fact_flag;  // fact_flag: failed-pivot flag of the cluster factor
+  int32_t inner_steps, inner_solves;  // forward: CG steps and solves of the reduced systems
 };
 
 struct BADev {
@@ -58,6 +64,12 @@ struct BADev {
   // the reduced systems (camera co-observation graphs)
   const ProbMeta* rmeta;
   const int32_t* rsym;
+  // tensor-core path: per problem the byte offset of its dense region in the workspace and its
+  // padded order; dmap[dmap_off[b] + r * N + c] = H block id of positions (r > c), or -1
+  const int64_t* tc_off;
+  const int32_t* tc_np;
+  const int32_t* dmap;
+  const int64_t* dmap_off;
 };
 
 struct BAArgs {
@@ -76,7 +88,7 @@ struct BAArgs {
   double *solc, *solp, *zc, *zp, *hc, *hp;
   BAState* st;
   // options
-  int algo, mixed, iters;
+  int algo, mixed, iters, tc;
   double lam0, tau, refine_tol;
   const double* v_cams;
   const double* v_pts;
@@ -145,6 +157,8 @@ __global__ void k_ba_init(BAArgs a) {
   s.status = DNLS_PROBLEM_OK;
   s.factor_ok = 0;
   s.refine_steps = 0;
+  s.inner_steps = s.inner_solves = 0;
+  s.inner_resid = 0.0;
 }
 
 template <class P>
@@ -448,6 +462,51 @@ __global__ void k_ba_schur(BAArgs a, double lam_override) {
   }
   ((double*)(a.ws + a.d.tgt_off[t]))[el] = acc;
 }
+
+// ---- tensor-core path of the reduced system
+// Entry (i, j), i >= j, of problem b's damped reduced system in elimination-position order
+// (row i = 6 r + a, r the position of its camera): the diagonal block of position r, or the
+// stored block of the position pair, or 0 where the co-observation graph has no edge.
+struct BASrc {
+  BADev d;
+  const char* ws;
+  __device__ int n(int b) const { return d.rmeta[b].N * 6; }
+  __device__ double val(int b, int i, int j) const {
+    const ProbMeta& m = d.rmeta[b];
+    const double* H = (const double*)(ws + m.ws + m.w_H);
+    const int r = i / 6, c = j / 6, a = i % 6, e = j % 6;
+    if (r == c) return H[(int64_t)r * 36 + a * 6 + e];
+    const int id = d.dmap[d.dmap_off[b] + (int64_t)r * m.N + c];
+    return id < 0 ? 0.0 : H[(int64_t)id * 36 + a * 6 + e];
+  }
+};
+
+// Right-hand side bc and solution dc of the reduced solves, in the caller's camera order.
+// report: forward solves record their CG steps and residual, and a CG breakdown marks the
+// LM step bad; the backward's preconditioner applications report nothing.
+struct BAIO {
+  BADev d;
+  const double* rhs;
+  double* out_v;
+  BAState* st;
+  int forward;
+  __device__ int n(int b) const { return d.rmeta[b].N * 6; }
+  __device__ int64_t gidx(int b, int i) const {
+    const ProbMeta& m = d.rmeta[b];
+    const int32_t* perm = d.rsym + m.sym + m.o_perm;
+    return (d.cam_off[b] + perm[i / 6]) * 6 + i % 6;
+  }
+  __device__ double rhs_of(int b, int i) const { return rhs[gidx(b, i)]; }
+  __device__ void out(int b, int i, double v) const { out_v[gidx(b, i)] = v; }
+  __device__ void report(int b, int steps, double resid, bool ok) const {
+    if (!forward) return;
+    BAState& s = st[b];
+    s.inner_steps += steps;
+    s.inner_solves += 1;
+    s.inner_resid = fmax(s.inner_resid, resid);
+    if (!ok) s.bad = 1;
+  }
+};
 
 // one CTA per problem: factor the reduced system (already damped) and solve for delta_c;
 // with `solve_only`, solve with the cached factor for rhs rc (backward) into dc.
@@ -771,8 +830,10 @@ __global__ void k_ba_info(BAArgs a, int backward) {
     in.iterations = s.iters;
     in.accepted = s.accepted;
     in.status = s.status;
-    in.refine_resid = 0.0;
-    in.refine_steps = 0;
+    // tensor-core path: the reduced solves' conjugate-gradient steps (total) and largest final
+    // relative residual; the direct FP64 path has none
+    in.refine_resid = s.inner_resid;
+    in.refine_steps = s.inner_steps;
     in.factorizations = s.iters;  // one reduced-system factorization per iteration
     in.reserved = 0;
   } else {
@@ -1067,6 +1128,11 @@ struct BAHost {
   int64_t ws_bytes = 0;
   bool red_chain = false;  // every elimination level of every reduced system holds one column
   int red_max_n = 0;       // most cameras in one reduced system
+  // tensor-core path (every reduced system of order 6 N <= tc::kMaxN)
+  bool tc_ok = false;
+  int tc_np_max = 0;
+  std::vector<int64_t> tc_off, dmap_off;
+  std::vector<int32_t> tc_np, dmap;
 };
 
 struct BAHandle {
@@ -1076,6 +1142,7 @@ struct BAHandle {
   BADev d;
   int64_t* d_prior_off = nullptr;
   int64_t* d_pt_off = nullptr;
+  int sms = 148;
 };
 
 }  // namespace dnls
@@ -1280,6 +1347,34 @@ int build_ba_host(const dnls_ba_desc* desc, BAHost& H) {
   H.w_zp = take(H.P * 3 * 8);
   H.w_hc = take(H.C * 6 * 8);
   H.w_hp = take(H.P * 3 * 8);
+  // tensor-core path: the map from position pairs to stored blocks (column k of the symbolic
+  // factor lists its row positions; lsrc names the pair block that holds each, -1 for fill),
+  // and one dense region per problem
+  H.tc_ok = true;
+  for (const ProbMeta& m : H.red.meta) H.tc_ok = H.tc_ok && m.N * 6 <= tc::kMaxN;
+  H.dmap_off.assign(B, 0);
+  H.tc_off.assign(B, 0);
+  H.tc_np.assign(B, 0);
+  if (H.tc_ok) {
+    for (int b = 0; b < B; ++b) {
+      const ProbMeta& m = H.red.meta[b];
+      const int32_t* sy = H.red.sym.data() + m.sym;
+      const int N = m.N;
+      H.dmap_off[b] = (int64_t)H.dmap.size();
+      H.dmap.resize(H.dmap.size() + (size_t)N * N, -1);
+      int32_t* dm = H.dmap.data() + H.dmap_off[b];
+      for (int k = 0; k < N; ++k)
+        for (int q = sy[m.o_colptr + k]; q < sy[m.o_colptr + k + 1]; ++q) {
+          const int lp = sy[m.o_lsrc + q];
+          dm[(int64_t)sy[m.o_rows + q] * N + k] = lp >= 0 ? N + lp : -1;
+        }
+      const int np = ((N * 6 + tc::kSlab - 1) / tc::kSlab) * tc::kSlab;
+      H.tc_np[b] = np;
+      H.tc_np_max = std::max(H.tc_np_max, np);
+      H.tc_off[b] = take(tc::Region::of(np).bytes);
+    }
+  }
+  if (H.dmap.empty()) H.dmap.push_back(-1);  // keep the array addressable
   H.ws_bytes = off;
   return DNLS_OK;
 }
@@ -1306,6 +1401,7 @@ dnls_status ba_check_opts(const dnls_solver_opts* o) {
   if (o->iters < 0 || o->iters > 100000) return DNLS_ERR_ARG;
   if (o->precision != DNLS_FP64 && o->precision != DNLS_MIXED_FP32) return DNLS_ERR_ARG;
   if (!(o->lambda0 >= 0.0) || !(o->tau >= 0.0)) return DNLS_ERR_ARG;
+  if (o->reduced_solver < DNLS_REDUCED_AUTO || o->reduced_solver > DNLS_REDUCED_FP64) return DNLS_ERR_ARG;
   return DNLS_OK;
 }
 
@@ -1350,6 +1446,7 @@ BAArgs ba_args(const dnls_ba* h, const dnls_solver_opts* o, const dnls_ba_inputs
   a.hc = (double*)(w + H.w_hc);
   a.hp = (double*)(w + H.w_hp);
   a.algo = o->algo;
+  a.tc = H.tc_ok && o->reduced_solver != DNLS_REDUCED_FP64;
   a.mixed = o->precision == DNLS_MIXED_FP32;
   a.iters = o->iters;
   a.lam0 = o->lambda0;
@@ -1391,8 +1488,37 @@ void reduced_solve(const BAHost& H, const BAArgs& a, cudaStream_t st, int mode) 
     k_ba_reduced<<<H.B, 256, 0, st>>>(a, mode, a.bc, a.dc, 0);
 }
 
+// the tensor-core batch over the reduced systems' dense regions: problems skipped while not
+// active; a failed factorization clears factor_ok and marks the LM step bad
+tc::Batch tc_batch(const BAHost& H, const BAArgs& a) {
+  tc::Batch tb;
+  tb.B = H.B;
+  tb.base = a.ws;
+  tb.off = a.d.tc_off;
+  tb.np = a.d.tc_np;
+  tb.active = &a.st[0].active;
+  tb.ok = &a.st[0].factor_ok;
+  tb.bad = &a.st[0].bad;
+  tb.stride = (int)(sizeof(BAState) / sizeof(int32_t));
+  return tb;
+}
+
+// CTAs per problem of the reduced CG solve: enough to cover the SMs, at least 32 rows each
+int tc_cluster(const BAHandle& G, int steps) {
+  if (steps <= 0) return 1;
+  int kc = 1;
+  while (kc < tc::kMaxCluster && (int64_t)G.h.B * kc * 2 <= G.sms && G.h.tc_np_max / (kc * 2) >= 32) kc *= 2;
+  return kc;
+}
+
+// Forward reduced solves: conjugate-gradient tolerance on the scaled system and step limit.  The
+// FP64 path solves to near the FP64 rounding of a direct solve; the mixed path, whose assembly
+// is FP32, to well below its 1e-5 solution tolerance.
+constexpr double kInnerTolFP64 = 1e-12, kInnerTolMixed = 1e-9;
+constexpr int kInnerMax = 40;
+
 // one LM iteration's linearise -> eliminate -> factor -> solve chain; lam_override >= 0 replaces
-// lambda (the backward's undamped refactorization)
+// lambda (the backward's undamped refactorization, which solves nothing)
 void ba_eliminate_and_factor(const dnls_ba* h, BAArgs& a, cudaStream_t st, double lam_override) {
   const BAHost& H = h->impl.h;
   if (a.mixed && lam_override < 0.0)
@@ -1402,6 +1528,17 @@ void ba_eliminate_and_factor(const dnls_ba* h, BAArgs& a, cudaStream_t st, doubl
   k_ba_points<<<nblk(H.P, 128), 128, 0, st>>>(a, lam_override);
   k_ba_cameras<<<nblk((int64_t)H.C * 32, 256), 256, 0, st>>>(a);  // one warp per camera
   k_ba_schur<<<nblk(H.red.meta.empty() ? 1 : (int64_t)H.tgt_cam.size() * 36, 128), 128, 0, st>>>(a, lam_override);
+  if (a.tc) {
+    const tc::Batch tb = tc_batch(H, a);
+    tc::k_tc_densify<BASrc><<<dim3((unsigned)(H.tc_np_max / tc::kNb), (unsigned)H.B), 256, 0, st>>>(tb, BASrc{a.d, a.ws});
+    tc::launch_factor(tb, st);
+    if (lam_override < 0.0) {
+      const int steps = kInnerMax;
+      tc::launch_pcg(tb, BAIO{a.d, a.bc, a.dc, a.st, 1}, steps, a.mixed ? kInnerTolMixed : kInnerTolFP64,
+                     tc_cluster(h->impl, steps), st);
+    }
+    return;
+  }
   launch_reduced_factor(H, a, st);
   reduced_solve(H, a, st, 2);
 }
@@ -1453,6 +1590,12 @@ dnls_status dnls_ba_create(const dnls_ba_desc* desc, dnls_ba** out) {
   if (s == DNLS_OK) s = up(G, (const int64_t**)&G.d_pt_off, H.pt_off);
   if (s == DNLS_OK) s = up(G, &d.rmeta, H.red.meta);
   if (s == DNLS_OK) s = up(G, &d.rsym, H.red.sym);
+  if (s == DNLS_OK) s = up(G, &d.tc_off, H.tc_off);
+  if (s == DNLS_OK) s = up(G, &d.tc_np, H.tc_np);
+  if (s == DNLS_OK) s = up(G, &d.dmap, H.dmap);
+  if (s == DNLS_OK) s = up(G, &d.dmap_off, H.dmap_off);
+  if (s == DNLS_OK && cudaDeviceGetAttribute(&G.sms, cudaDevAttrMultiProcessorCount, G.device) != cudaSuccess)
+    s = DNLS_ERR_CUDA;
   if (s != DNLS_OK) {
     dnls_ba_destroy(h);
     return s;
@@ -1483,6 +1626,7 @@ dnls_status dnls_ba_forward(const dnls_ba* h, const dnls_solver_opts* opts, cons
   if (opts && opts->algo == DNLS_DOGLEG) return DNLS_ERR_UNSUPPORTED;  // pose graphs only
   dnls_status s = ba_check_opts(opts);
   if (s != DNLS_OK) return s;
+  if (opts->reduced_solver == DNLS_REDUCED_TC && !h->impl.h.tc_ok) return DNLS_ERR_UNSUPPORTED;
   if (!workspace || ((uintptr_t)workspace & 255) || (int64_t)workspace_bytes < h->impl.h.ws_bytes)
     return DNLS_ERR_WORKSPACE;
   const BAHost& H = h->impl.h;
@@ -1520,6 +1664,7 @@ dnls_status dnls_ba_backward(const dnls_ba* h, const dnls_solver_opts* opts, con
   dnls_status s = ba_check_opts(opts);
   if (s != DNLS_OK) return s;
   if (opts->backward_mode != DNLS_IMPLICIT_EXACT) return DNLS_ERR_UNSUPPORTED;
+  if (opts->reduced_solver == DNLS_REDUCED_TC && !h->impl.h.tc_ok) return DNLS_ERR_UNSUPPORTED;
   if (opts->refine_max < 1 || !(opts->refine_tol >= 0.0)) return DNLS_ERR_ARG;
   if (!workspace || ((uintptr_t)workspace & 255) || (int64_t)workspace_bytes < h->impl.h.ws_bytes)
     return DNLS_ERR_WORKSPACE;
@@ -1541,9 +1686,14 @@ dnls_status dnls_ba_backward(const dnls_ba* h, const dnls_solver_opts* opts, con
   k_bab_refactored<<<nb, 256, 0, st>>>(a);
   k_bab_start<<<H.B, 256, 0, st>>>(a, h->impl.d_pt_off);
   // z = M^-1 r (block elimination with the cached Schur factorization): camera side into dc
+  // (tensor-core path: the cached FP32 factor applied once, z_c = D (L~ L~^T)^-1 D r_c, a fixed
+  // SPD operator, so the outer iteration stays plain preconditioned CG)
   auto precondition = [&]() {
     k_bap_cams<<<nblk((int64_t)H.C * 32, 256), 256, 0, st>>>(a);
-    reduced_solve(H, a, st, 1);
+    if (a.tc)
+      tc::launch_pcg(tc_batch(H, a), BAIO{a.d, a.bc, a.dc, a.st, 0}, 0, 0.0, 1, st);
+    else
+      reduced_solve(H, a, st, 1);
     k_bap_pts<<<nblk(H.P, 128), 128, 0, st>>>(a);
   };
   precondition();

@@ -24,6 +24,7 @@ GN, LM, DOGLEG = 0, 1, 2
 FP64, MIXED_FP32 = 0, 1
 IMPLICIT_EXACT, IMPLICIT_GN, BACKWARD_DLM, BACKWARD_UNROLL = 0, 1, 2, 3
 ORDER_MIN_DEGREE, ORDER_NATURAL = 0, 1
+REDUCED_AUTO, REDUCED_TC, REDUCED_FP64 = 0, 1, 2
 
 
 class SolverOpts(ctypes.Structure):
@@ -31,7 +32,7 @@ class SolverOpts(ctypes.Structure):
                 ("backward_mode", c_int32), ("refine_max", c_int32), ("threads", c_int32),
                 ("ctas_per_sm", c_int32), ("smem_factor", c_int32), ("lambda0", c_double),
                 ("tau", c_double), ("refine_tol", c_double), ("dlm_eps", c_double), ("radius0", c_double),
-                ("trunc_steps", c_int32), ("reserved", c_int32)]
+                ("trunc_steps", c_int32), ("reduced_solver", c_int32)]
 
 
 class GraphDesc(ctypes.Structure):

@@ -35,6 +35,7 @@ class Options:
     dlm_eps: float = 1e-2            # backward_mode "dlm": finite-difference scale eps
     radius0: float = 1.0             # algo "dogleg": initial trust radius
     trunc_steps: int = 0             # backward_mode "unroll": last k iterations only (0 = all)
+    reduced_solver: str = "auto"     # bundle adjustment: "auto" | "tc" | "fp64"
 
     def c(self) -> _d.SolverOpts:
         fp64 = self.precision == "fp64"
@@ -60,6 +61,10 @@ class Options:
         o.dlm_eps = float(self.dlm_eps)
         o.radius0 = float(self.radius0)
         o.trunc_steps = int(self.trunc_steps)
+        solvers = {"auto": _d.REDUCED_AUTO, "tc": _d.REDUCED_TC, "fp64": _d.REDUCED_FP64}
+        if self.reduced_solver not in solvers:
+            raise ValueError(f"unknown reduced_solver {self.reduced_solver!r}")
+        o.reduced_solver = solvers[self.reduced_solver]
         return o
 
 
