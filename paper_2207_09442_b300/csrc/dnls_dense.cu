@@ -96,7 +96,7 @@ dnls_status dnls_dense_spd_solve(int32_t batch, int32_t n, const double* A, cons
   const int64_t work = std::max<int64_t>(batch, (int64_t)batch * n);
   k_dense_init<<<(unsigned)((work + 255) / 256), 256, 0, st>>>(batch, n, np, rbytes, first, off, npv, base, x, steps,
                                                                resid);
-  dnls::tc::Batch tb = {batch, base, off, npv, nullptr, nullptr, nullptr, 0};
+  dnls::tc::Batch tb = {batch, np, base, off, npv, nullptr, nullptr, nullptr, 0};
   DenseSrc src = {A, n};
   dnls::tc::k_tc_densify<DenseSrc><<<dim3(np / dnls::tc::kNb, batch), 256, 0, st>>>(tb, src);
   if (dnls::tc::launch_factor(tb, st) != cudaSuccess) return DNLS_ERR_CUDA;

@@ -45,45 +45,61 @@ constexpr int kMaxPanels = kMaxN / kNb;
 constexpr int kTermBytes = kMaxN / 8 * 512;     // one BF16 split term of a panel, all rows
 constexpr int kBufBytes = 3 * kTermBytes;       // the three split terms
 constexpr int kFactorThreads = 128;             // warp w owns tensor-memory lanes 32w..32w+31
-constexpr int kPcgThreads = 256;
+constexpr int kPcgThreads = 384;  // = kMaxN: one thread per (row, K-split) of a CTA's rows
 constexpr int kMaxCluster = 8;
-// shared memory of the factor kernel: two panel buffers, the inverted diagonal blocks, the
-// diagonal-block scratch (32 x 33) and its reciprocal pivots, three mbarriers, the tensor-memory
-// address slot and two flags
-constexpr int kFactorSmem = 2 * kBufBytes + kMaxPanels * 1024 * 4 + 32 * 33 * 4 + 32 * 4 + 64;
+// shared memory of the factor kernel: two panel buffers, the diagonal blocks L_kk (transposed)
+// and their reciprocal pivots, three mbarriers, the tensor-memory address slot and two flags
+constexpr int kFactorSmem = 2 * kBufBytes + kMaxPanels * 1024 * 4 + kMaxPanels * 32 * 4 + 64;
 
 // Per-problem header at the start of its region.
+constexpr int kHdrBytes = 512;
+enum { kPartB = 0, kPartPQ, kPartRR, kPartRZ, kParts };
 struct Hdr {
   int32_t fstat;      // factor: 0 ok, 1 not positive definite after every shift, 2 timeout
-  int32_t steps;      // PCG steps of the last solve (-1: not run)
-  int32_t done;       // PCG: converged or stopped (shared by the cluster)
+  int32_t steps;      // PCG steps of the last solve
   int32_t attempts;   // factor: shifts tried
-  double resid;       // PCG: final ||b~ - A~ x~|| / ||b~||
-  double bnorm, rz, shift, alpha;
-  double part[kMaxCluster];  // per-CTA partial dot products
+  int32_t pad;
+  double resid;       // PCG: final ||b~ - A~ x~|| / ||b~|| (recurrence residual)
+  double shift;       // factor: the diagonal shift that succeeded
+  // per-CTA partials of the cluster's reductions, one slot array per quantity (a slot is
+  // rewritten only two cluster barriers after it was read)
+  double part[kParts][kMaxCluster];
 };
-static_assert(sizeof(Hdr) <= 256, "header");
+static_assert(sizeof(Hdr) <= kHdrBytes, "header");
 
 __host__ __device__ inline int64_t a256(int64_t x) { return (x + 255) & ~(int64_t)255; }
 
 // Byte offsets of a problem's arrays inside its region, for padded order np.
+//   A    FP64 scaled matrix, row-major (the CG products)
+//   Af   the same in FP32, chunk-major: chunk (s, c) = rows 128 s .. 128 s + 127, columns
+//        32 c .. 32 c + 31, each row's 32 values contiguous (coalesced slab loads of the factor)
+//   L    FP32 factor, row-major (lower triangle)       Linv  FP32 inverted diagonal blocks
+//   X    FP32 L~^-1, row-major (lower triangle), and XT its transpose, row-major: the
+//        preconditioner's two products read them with consecutive threads on consecutive rows
+//   split  BF16 split panels (MMA B operands of later slabs)    vec  CG vectors
 struct Region {
-  int64_t d, A, L, Linv, split, vec, bytes;
+  int64_t d, A, Af, L, Linv, X, XT, split, vec, bytes;
   __host__ __device__ static Region of(int np) {
     Region r;
-    int64_t o = 256;
+    int64_t o = kHdrBytes;
     r.d = o;
     o = a256(o + (int64_t)np * 8);
     r.A = o;
     o = a256(o + (int64_t)np * np * 8);
+    r.Af = o;
+    o = a256(o + (int64_t)np * np * 4);
     r.L = o;
     o = a256(o + (int64_t)np * np * 4);
     r.Linv = o;
     o = a256(o + (int64_t)(np / kNb) * 1024 * 4);
+    r.X = o;
+    o = a256(o + (int64_t)np * np * 4);
+    r.XT = o;
+    o = a256(o + (int64_t)np * np * 4);
     r.split = o;
     o = a256(o + (int64_t)(np / kNb) * 3 * np * 64);
-    r.vec = o;  // b, x, r, z, p, q
-    o = a256(o + (int64_t)6 * np * 8);
+    r.vec = o;  // p (FP64), r (FP32, scaled), y (FP32)
+    o = a256(o + (int64_t)np * 16);
     r.bytes = o;
     return r;
   }
@@ -94,6 +110,7 @@ struct Region {
 // bad[b * stride] = 1 are written where those pointers are set (ok = 1 on success).
 struct Batch {
   int B;
+  int np_max;  // largest np (host side: grid sizes)
   char* base;
   const int64_t* off;
   const int32_t* np;
@@ -250,12 +267,15 @@ __global__ void __launch_bounds__(256) k_tc_densify(Batch tb, Src src) {
   }
   __syncthreads();
   double* A = (double*)(R + rg.A);
+  float* Af = (float*)(R + rg.Af);
+  const int s = r0 / kSlab, P = np / kNb;
   for (int e = threadIdx.x; e < kNb * np; e += blockDim.x) {
     const int i = r0 + e / np, j = e % np;
     double v;
     if (i < n && j < n) v = (j <= i ? src.val(b, i, j) : src.val(b, j, i)) * ds[i] * ds[j];
     else v = i == j ? 1.0 : 0.0;
     A[(int64_t)i * np + j] = v;
+    Af[(((int64_t)s * P + j / kNb) * kSlab + (i % kSlab)) * kNb + j % kNb] = (float)v;
   }
   if (blockIdx.x == 0) {
     double* d = (double*)(R + rg.d);
@@ -264,75 +284,96 @@ __global__ void __launch_bounds__(256) k_tc_densify(Batch tb, Src src) {
 }
 
 // ----------------------------------------------------------------------------- factor
-// One CTA of kFactorThreads per active problem (dnls_tc.cu): L~ into the region's L / Linv.
-// Errors surface through the returned launch status.
+// One CTA of kFactorThreads per active problem (dnls_tc.cu): L~ into the region's L / Linv,
+// then X = L~^-1 (one CTA per problem and 32-column panel).  Errors surface through the
+// returned launch status.
 cudaError_t launch_factor(const Batch& tb, cudaStream_t st);
 
 // ----------------------------------------------------------------------------- solve
-// z = M^-1 r in FP32 (y = L~^-1 r, z = L~^-T y), one CTA: ys (shared, np floats) holds r on entry
-// and z on exit; Linv_s the staged inverted diagonal blocks; L row-major FP32.
-__device__ inline void tc_precond(float* ys, const float* Linv_s, const float* L, int np, float* tmp) {
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const int P = np / kNb;
-  for (int k = 0; k < P; ++k) {
-    const int base = k * kNb;
-    if (tid < 32) {
-      const float* Li = Linv_s + k * 1024 + tid * 32;
-      float acc = 0.0f;
+// Sum (or max) over the CTA in a fixed order: warp shuffles, then every thread adds the warps'
+// partials from shared memory `red` (>= 32 doubles).  Two barriers.
+__device__ __forceinline__ double cta_reduce(double v, double* red, bool is_max) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
-      for (int m = 0; m < 32; ++m) acc = fmaf(m <= tid ? Li[m] : 0.0f, ys[base + m], acc);
-      tmp[tid] = acc;
-    }
-    __syncthreads();
-    if (tid < 32) ys[base + tid] = tmp[tid];
-    for (int i = base + kNb + tid; i < np; i += nt) {
-      const float4* Lr = (const float4*)(L + (int64_t)i * np + base);
-      float acc = 0.0f;
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const float4 w = Lr[q];
-        acc = fmaf(w.x, tmp[4 * q], fmaf(w.y, tmp[4 * q + 1], fmaf(w.z, tmp[4 * q + 2], fmaf(w.w, tmp[4 * q + 3], acc))));
-      }
-      ys[i] -= acc;
-    }
-    __syncthreads();
+  for (int o = 16; o > 0; o >>= 1) {
+    const double w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = is_max ? fmax(v, w) : v + w;
   }
-  for (int k = P - 1; k >= 0; --k) {
-    const int base = k * kNb;
-    if (tid < 32) {
-      float acc = 0.0f;
-#pragma unroll
-      for (int m = 0; m < 32; ++m) acc = fmaf(m >= tid ? Linv_s[k * 1024 + m * 32 + tid] : 0.0f, ys[base + m], acc);
-      tmp[tid] = acc;
-    }
-    __syncthreads();
-    if (tid < 32) ys[base + tid] = tmp[tid];
-    for (int j = tid; j < base; j += nt) {
-      float acc = 0.0f;
-#pragma unroll 8
-      for (int m = 0; m < 32; ++m) acc = fmaf(L[(int64_t)(base + m) * np + j], tmp[m], acc);
-      ys[j] -= acc;
-    }
-    __syncthreads();
-  }
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double t = red[0];
+  for (int i = 1; i < nw; ++i) t = is_max ? fmax(t, red[i]) : t + red[i];
+  __syncthreads();
+  return t;
 }
 
-// Preconditioned conjugate gradients on A~ x~ = b~ (b~ = D b), M = L~ L~^T; kc CTAs per problem
-// in one thread-block cluster (kc in 1, 2, 4, 8; np / kc rows of the product each).
+// Barrier over the problem's kc CTAs (a thread-block cluster), with release / acquire at
+// cluster scope so that every global write before it is visible after it.
+__device__ __forceinline__ void pcg_sync(int kc) {
+  if (kc > 1) cluster_sync_all();
+  else __syncthreads();
+}
+
+// Cluster-wide reduction: each CTA publishes its partial in slot `kind`, and after the barrier
+// (whose acquire makes the other CTAs' writes visible) every CTA adds the kc partials in rank
+// order, the same value in every CTA.
+__device__ __forceinline__ double cluster_total(Hdr* hdr, int kind, int rank, int kc, double part, bool is_max) {
+  if (threadIdx.x == 0) hdr->part[kind][rank] = part;
+  pcg_sync(kc);
+  double v[kMaxCluster];
+#pragma unroll
+  for (int c = 0; c < kMaxCluster; ++c) v[c] = c < kc ? __ldcg(&hdr->part[kind][c]) : 0.0;
+  double t = v[0];
+  for (int c = 1; c < kc; ++c) t = is_max ? fmax(t, v[c]) : t + v[c];
+  return t;
+}
+
+// Two sums over the CTA at once (fixed order, as cta_reduce).
+__device__ __forceinline__ void cta_reduce2(double& a, double& c, double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    c += __shfl_xor_sync(0xffffffffu, c, o);
+  }
+  if (lane == 0) {
+    red[warp] = a;
+    red[32 + warp] = c;
+  }
+  __syncthreads();
+  double ta = red[0], tc = red[32];
+  for (int i = 1; i < nw; ++i) {
+    ta += red[i];
+    tc += red[32 + i];
+  }
+  __syncthreads();
+  a = ta;
+  c = tc;
+}
+
+// Preconditioned conjugate gradients on A~ x~ = b~ (b~ = D b) with M^-1 = X^T X, X = L~^-1;
+// kc CTAs per problem in one thread-block cluster (kc divides np / 32), CTA c owning rows
+// [c np / kc, (c + 1) np / kc).  Thread t < rows keeps x, r, p, z of row row0 + t in registers;
+// for the products thread t works on row row0 + t % rows over the column split t / rows
+// (nsplit = 384 / rows splits), and the split partials are added by the row's thread in split
+// order.  Per step: q = A~ p on own rows (FP64; A~ is symmetric, so row i is read as column i,
+// consecutive threads on consecutive addresses), alpha, x, r; y = X r on own rows (reading X^T)
+// and z = X^T y on own entries (reading X), FP32 with r scaled by the last ||r||; r.r and r.z in
+// one reduction; beta, p.  The cluster exchanges p, r and y through the region and its scalars
+// through the header's partial slots, five cluster barriers per step; every CTA takes the same
+// stop decision.
 //   IO::rhs_of(b, i)         b_i of the original system (i < n)
 //   IO::n(b)                 the order
 //   IO::out(b, i, x_i)       the solution (i < n), written once converged or stopped
 //   IO::report(b, steps, resid, ok)   per-problem outcome (ok false: a breakdown, p'Ap <= 0)
-// max_steps = 0 applies M^-1 once (x = D M^-1 D b).
-// Dynamic shared memory: kPcgSmem (the staged inverted diagonal blocks).
-constexpr int kPcgSmem = kMaxPanels * 1024 * 4;
+// max_steps = 0 applies M^-1 once (x = D X^T X D b).
 template <class IO>
-__global__ void __launch_bounds__(kPcgThreads) k_tc_pcg(Batch tb, IO io, int max_steps, double tol, int kc) {
-  __shared__ double ps[kMaxN];
-  __shared__ float ys[kMaxN];
-  __shared__ float tmp[32];
-  __shared__ double red[kPcgThreads];
-  extern __shared__ __align__(16) float Linv_s[];
+__global__ void __launch_bounds__(kPcgThreads, 1) k_tc_pcg(Batch tb, IO io, int max_steps, double tol, int kc) {
+  __shared__ double ps[kMaxN];                 // p, staged for the product
+  __shared__ float vs[kMaxN];                  // scaled r, then y, staged for the preconditioner
+  __shared__ double qpart[kPcgThreads];        // split partials of the row products
+  __shared__ float fpart[kPcgThreads];
+  __shared__ double red[64];
   const int b = blockIdx.x / kc, rank = blockIdx.x % kc;
   if (b >= tb.B || !tb.on(b)) return;  // the same for every CTA of the cluster
   const int np = tb.np[b];
@@ -342,134 +383,159 @@ __global__ void __launch_bounds__(kPcgThreads) k_tc_pcg(Batch tb, IO io, int max
   const Region rg = Region::of(np);
   const double* A = (const double*)(R + rg.A);
   const double* d = (const double*)(R + rg.d);
-  const float* L = (const float*)(R + rg.L);
-  double* vb = (double*)(R + rg.vec);
-  double *vx = vb + np, *vr = vb + 2 * np, *vz = vb + 3 * np, *vp = vb + 4 * np, *vq = vb + 5 * np;
+  const float* X = (const float*)(R + rg.X);
+  const float* XT = (const float*)(R + rg.XT);
+  double* vp = (double*)(R + rg.vec);
+  float* vr = (float*)(vp + np);
+  float* vy = vr + np;
   const int tid = threadIdx.x;
   const int n = io.n(b);
-  // M^-1 applied to vr into vz (rank 0), r scaled by its largest entry for the FP32 sweeps
-  auto precond = [&]() {
-    double mx = 0.0;
-    for (int i = tid; i < np; i += blockDim.x) mx = fmax(mx, fabs(vr[i]));
-    // block max through the sum buffer
-    red[tid] = mx;
-    __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-      if (tid < w) red[tid] = fmax(red[tid], red[tid + w]);
-      __syncthreads();
-    }
-    const double sc = red[0] > 0.0 ? red[0] : 1.0;
-    __syncthreads();
-    for (int i = tid; i < np; i += blockDim.x) ys[i] = (float)(vr[i] / sc);
-    __syncthreads();
-    tc_precond(ys, Linv_s, L, np, tmp);
-    for (int i = tid; i < np; i += blockDim.x) vz[i] = (double)ys[i] * sc;
-    __syncthreads();
-  };
-  if (rank == 0) {
-    const float* Lig = (const float*)(R + rg.Linv);
-    for (int i = tid; i < (np / kNb) * 1024; i += blockDim.x) Linv_s[i] = Lig[i];
-    double acc = 0.0;
-    for (int i = tid; i < np; i += blockDim.x) {
-      const double v = i < n ? io.rhs_of(b, i) * d[i] : 0.0;
-      vb[i] = v;
-      vr[i] = v;
-      vx[i] = 0.0;
-      acc += v * v;
-    }
-    const double bn = sqrt(block_sum(acc, red));
-    precond();
-    double rz = 0.0;
-    for (int i = tid; i < np; i += blockDim.x) {
-      vp[i] = vz[i];
-      rz += vr[i] * vz[i];
-    }
-    rz = block_sum(rz, red);
-    if (tid == 0) {
-      hdr->bnorm = bn;
-      hdr->rz = rz;
-      hdr->steps = 0;
-      hdr->resid = bn > 0.0 ? 1.0 : 0.0;
-      hdr->done = (max_steps <= 0 || !(bn > 0.0)) ? 1 : 0;
-    }
-    if (max_steps <= 0)
-      for (int i = tid; i < np; i += blockDim.x) vx[i] = vz[i];
-  }
-  if (kc > 1) cluster_sync_all();
-  else __syncthreads();
-  bool ok = true;
   const int rows = np / kc, row0 = rank * rows;
-  const int warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
-  for (int it = 0;; ++it) {
-    if (*(volatile int32_t*)&hdr->done) break;
-    for (int i = tid; i < np; i += blockDim.x) ps[i] = vp[i];
-    __syncthreads();
-    double part = 0.0;
-    for (int i = row0 + warp; i < row0 + rows; i += nw) {
-      const double* Ai = A + (int64_t)i * np;
-      double acc = 0.0;
-      for (int j = lane; j < np; j += 32) acc = fma(Ai[j], ps[j], acc);
+  const int nsplit = kPcgThreads / rows < 1 ? 1 : kPcgThreads / rows;
+  const int width = (np + nsplit - 1) / nsplit;
+  const int pr = row0 + tid % rows, sp = tid / rows;          // product row and split
+  const bool pact = sp < nsplit;
+  const int j0 = sp * width, j1 = j0 + width < np ? j0 + width : np;
+  const bool own = tid < rows;
+  const int ir = row0 + tid;                                    // own row
+  // q_pr = sum_j A~(j, pr) p_j over this thread's split, then summed per own row
+  auto rows_fp64 = [&]() -> double {
+    double a4[4] = {0.0, 0.0, 0.0, 0.0};
+    if (pact) {
+      const double* Ac = A + pr;
+      int j = j0;
+      for (; j + 8 <= j1; j += 8) {
+        double v[8];
 #pragma unroll
-      for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-      if (lane == 0) {
-        vq[i] = acc;
-        part += acc * ps[i];
+        for (int u = 0; u < 8; ++u) v[u] = __ldg(Ac + (int64_t)(j + u) * np);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) a4[u & 3] = fma(v[u], ps[j + u], a4[u & 3]);
       }
+      for (; j < j1; ++j) a4[0] = fma(__ldg(Ac + (int64_t)j * np), ps[j], a4[0]);
     }
-    part = block_sum(part, red);
-    if (tid == 0) hdr->part[rank] = part;
-    if (kc > 1) cluster_sync_all();
-    else __syncthreads();
-    if (rank == 0) {
-      double pq = 0.0;
-      for (int c = 0; c < kc; ++c) pq += *(volatile double*)&hdr->part[c];
-      const double rz = hdr->rz;
+    const double acc = (a4[0] + a4[1]) + (a4[2] + a4[3]);
+    qpart[tid] = acc;
+    __syncthreads();
+    double q = 0.0;
+    if (own)
+      for (int s = 0; s < nsplit; ++s) q += qpart[s * rows + tid];
+    __syncthreads();
+    return q;
+  };
+  // z = X^T X r for the own row, r given scaled by 1 / sc
+  auto precond = [&](double rv, double sc) -> double {
+    if (own) vr[ir] = (float)(rv / sc);
+    pcg_sync(kc);
+    for (int i = tid; i < np; i += kPcgThreads) vs[i] = vr[i];
+    __syncthreads();
+    // y_pr = sum_{j <= pr} X(pr, j) r_j, and below z_pr = sum_{i >= pr} X(i, pr) y_i: column
+    // sums over [lo, hi) of a row-major matrix M, 16 loads in flight per thread
+    auto colsum = [&](const float* M, int lo, int hi) -> float {
+      float f4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+      const float* Mc = M + pr;
+      int j = lo;
+      for (; j + 16 <= hi; j += 16) {
+        float v[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) v[u] = __ldg(Mc + (int64_t)(j + u) * np);
+#pragma unroll
+        for (int u = 0; u < 16; ++u) f4[u & 3] = fmaf(v[u], vs[j + u], f4[u & 3]);
+      }
+      for (; j < hi; ++j) f4[0] = fmaf(__ldg(Mc + (int64_t)j * np), vs[j], f4[0]);
+      return (f4[0] + f4[1]) + (f4[2] + f4[3]);
+    };
+    float acc = 0.0f;
+    if (pact) acc = colsum(XT, j0, j1 < pr + 1 ? j1 : pr + 1);
+    fpart[tid] = acc;
+    __syncthreads();
+    if (own) {
+      float y = 0.0f;
+      for (int s = 0; s < nsplit; ++s) y += fpart[s * rows + tid];
+      vy[ir] = y;
+    }
+    pcg_sync(kc);
+    for (int i = tid; i < np; i += kPcgThreads) vs[i] = vy[i];
+    __syncthreads();
+    acc = 0.0f;
+    if (pact) acc = colsum(X, j0 > pr ? j0 : pr, j1);
+    fpart[tid] = acc;
+    __syncthreads();
+    float z = 0.0f;
+    if (own)
+      for (int s = 0; s < nsplit; ++s) z += fpart[s * rows + tid];
+    __syncthreads();
+    return own ? (double)z * sc : 0.0;
+  };
+  double x = 0.0, r = own && ir < n ? io.rhs_of(b, ir) * d[ir] : 0.0, p = 0.0, z = 0.0;
+  const double bn = sqrt(cluster_total(hdr, kPartB, rank, kc, cta_reduce(r * r, red, false), false));
+  int steps = 0;
+  double rn = bn;
+  bool ok = true;
+  if (bn > 0.0) {
+    z = precond(r, bn);
+    double rz = cluster_total(hdr, kPartRZ, rank, kc, cta_reduce(r * z, red, false), false);
+    if (max_steps <= 0) x = z;
+    p = z;
+    while (steps < max_steps) {
+      if (own) vp[ir] = p;
+      pcg_sync(kc);
+      for (int i = tid; i < np; i += kPcgThreads) ps[i] = vp[i];
+      __syncthreads();
+      const double q = rows_fp64();
+      const double pq = cluster_total(hdr, kPartPQ, rank, kc, cta_reduce(p * q, red, false), false);
       const double alpha = rz / pq;
-      const bool good = pq > 0.0 && isfinite(alpha);
-      double r2 = 0.0;
-      if (good)
-        for (int i = tid; i < np; i += blockDim.x) {
-          vx[i] += alpha * vp[i];
-          vr[i] -= alpha * vq[i];
-          r2 += vr[i] * vr[i];
+      ++steps;
+      if (!(pq > 0.0) || !isfinite(alpha)) {
+        ok = false;
+        break;
+      }
+      x += alpha * p;
+      r -= alpha * q;
+      z = precond(r, rn);
+      double rr = r * r, rz2 = r * z;
+      cta_reduce2(rr, rz2, red);
+      if (threadIdx.x == 0) {
+        hdr->part[kPartRR][rank] = rr;
+        hdr->part[kPartRZ][rank] = rz2;
+      }
+      pcg_sync(kc);
+      {
+        double v1[kMaxCluster], v2[kMaxCluster];
+#pragma unroll
+        for (int c = 0; c < kMaxCluster; ++c) {
+          v1[c] = c < kc ? __ldcg(&hdr->part[kPartRR][c]) : 0.0;
+          v2[c] = c < kc ? __ldcg(&hdr->part[kPartRZ][c]) : 0.0;
         }
-      const double rn = sqrt(block_sum(r2, red));
-      const double bn = hdr->bnorm;
-      const bool stop = !good || !(rn > tol * bn) || it + 1 >= max_steps;
-      if (!stop) {
-        precond();
-        double rz2 = 0.0;
-        for (int i = tid; i < np; i += blockDim.x) rz2 += vr[i] * vz[i];
-        rz2 = block_sum(rz2, red);
-        const double beta = rz2 / rz;
-        for (int i = tid; i < np; i += blockDim.x) vp[i] = vz[i] + beta * vp[i];
-        if (tid == 0) hdr->rz = rz2;
+        rr = v1[0];
+        rz2 = v2[0];
+        for (int c = 1; c < kc; ++c) {
+          rr += v1[c];
+          rz2 += v2[c];
+        }
       }
-      if (tid == 0) {
-        hdr->steps = it + 1;
-        if (good) hdr->resid = rn / bn;
-        hdr->done = stop ? 1 : 0;
-      }
-      if (!good) ok = false;
+      rn = sqrt(rr);
+      if (!(rn > tol * bn) || steps >= max_steps) break;
+      const double beta = rz2 / rz;
+      rz = rz2;
+      p = z + beta * p;
     }
-    if (kc > 1) cluster_sync_all();
-    else __syncthreads();
   }
-  if (rank == 0) {
-    for (int i = tid; i < n; i += blockDim.x) io.out(b, i, vx[i] * d[i]);
-    if (tid == 0) io.report(b, hdr->steps, hdr->resid, ok);
+  if (own && ir < n) io.out(b, ir, x * d[ir]);
+  if (rank == 0 && tid == 0) {
+    const double res = bn > 0.0 ? rn / bn : 0.0;
+    hdr->steps = steps;
+    hdr->resid = res;
+    io.report(b, steps, res, ok);
   }
 }
 
 // Launch of the solve, shared with the bundle-adjustment path.
 template <class IO>
 inline cudaError_t launch_pcg(const Batch& tb, const IO& io, int steps, double tol, int kc, cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(k_tc_pcg<IO>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPcgSmem);
-  if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(tb.B * kc));
   cfg.blockDim = dim3(kPcgThreads);
-  cfg.dynamicSmemBytes = kPcgSmem;
+  cfg.dynamicSmemBytes = 0;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;

@@ -37,7 +37,7 @@ def _stack(cams, pts):
 
 
 # final relative residual of the forward's reduced CG solves (tensor-core path)
-INNER_TOL = {"fp64": 1e-12, "mixed_fp32": 1e-9}
+INNER_TOL = {"fp64": 1e-12, "mixed_fp32": 1e-7}
 
 
 @pytest.mark.parametrize("solver", ["tc", "fp64"])
