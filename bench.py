@@ -10,9 +10,11 @@ iteration runs in full: the freeze threshold is 0, so each problem executes all 
 SE(3) graphs with log-weights, 1024 SE(3) graphs of 16..256 poses, and 32 bundle-adjustment
 problems (64 cameras, 4096 points, Huber reprojection costs; backward w.r.t. observations).
 
-Reported next to it: the same solver on the plain FP64 per-problem path (one problem per
-launch, FP64 everywhere), the oracle on the host cores (cpu_baseline), the roofline of the
-dominant work (FP64-bound factorizations), clocks sampled during the timed region, and an
+Reported next to it: the forward + backward replayed from a CUDA graph, the same batch in FP64
+throughout (batched_fp64), the plain FP64 per-problem path (one problem per launch, FP64
+everywhere), the oracle on the host cores (cpu_baseline: a spawn pool of one single-threaded
+process per core, and one core alone), rooflines of the dominant kernels (bundle adjustment: from
+the library's per-phase event timers), clocks sampled during the timed region, and an
 end-to-end number through the public API with host buffers.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--workload W]
@@ -38,8 +40,8 @@ WORKLOAD = "pgo_se3_b256"
 PER_GPU = {"pgo_se2_b16": 16, "pgo_se3_b256": 256, "pgo_se3_implicit_b256": 256,
            "pgo_se3_uneven_b1024": 1024, "pgo_se3_robust_b256": 256, "ba_b32": 32}
 METRIC = "batched LM iters/s (fwd + implicit bwd) vs plain FP64 GPU path at 1e-5"
-# DRAM bytes (read + write) per launch of the dominant kernel, from an ncu capture of the forward
-# kernel's sources as they hash here (profiles/k_forward_pgo_se3_b64_full.md: 64-problem case,
+# DRAM bytes (read + write) per launch of the dominant kernel, from a full ncu capture of the
+# forward kernel built from the sources that hash to the recorded value (a 64-problem case,
 # scaled by 256/64 since every problem owns its own inputs and workspace region).  Reported only
 # while the sources still hash to the captured build; null otherwise.
 FORWARD_SOURCES = ["dnls_graph.cu", "dnls_blockchol.cuh", "dnls_cost.cuh", "dnls_lie.cuh",
@@ -212,38 +214,96 @@ def _oracle_sample(name, batch, idxs, iters, backward=True, algo=None, bmode="im
     return time.perf_counter() - t0, n_it, sols
 
 
+def _oracle_job(job):
+    """One problem through the oracle in a pool worker (one thread): (seconds, iterations)."""
+    name, first, count, b, iters, backward, algo, bmode, trunc = job
+    import torch
+    torch.set_num_threads(1)
+    from paper_2207_09442_b300 import synth
+    batch = synth.workload(name, batch=count, first=first)
+    secs, n, _ = _oracle_sample(name, batch, [b], iters, backward=backward, algo=algo, bmode=bmode, trunc=trunc)
+    return secs, n
+
+
+def _warm_worker(_):
+    import torch  # noqa: F401  (imports the oracle's dependencies once per worker)
+    from oracle import ba, pgo  # noqa: F401
+    return os.getpid()
+
+
+class OraclePool:
+    """The oracle on the host cores: a spawn pool of one single-threaded process per core (the
+    oracle's small-tensor torch code does not spread over threads), each solving whole problems."""
+
+    def __init__(self, jobs_max: int):
+        import multiprocessing as mp
+        self.cores = max(1, min(os.cpu_count() or 1, jobs_max))
+        self.pool = mp.get_context("spawn").Pool(self.cores)
+        self.pool.map(_warm_worker, range(self.cores))
+
+    def run(self, jobs):
+        """Wall seconds and total iterations of the jobs, spread over the pool."""
+        t0 = time.perf_counter()
+        res = self.pool.map(_oracle_job, jobs, chunksize=1)
+        return time.perf_counter() - t0, sum(r[1] for r in res)
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def _cpu_baseline(name, first, count, idxs, iters, backward, algo, bmode, trunc, what):
+    """cpu_baseline entry: the listed problems over the pool (all host cores), plus one problem
+    on one core (a worker alone)."""
+    jobs = [(name, first + b, 1, 0, iters, backward, algo, bmode, trunc) for b in idxs]
+    pool = OraclePool(len(jobs))
+    try:
+        secs, its = pool.run(jobs)
+        s1, i1 = pool.run(jobs[:1])
+    finally:
+        pool.close()
+    return {"value": its / secs, "unit": "LM iters/s", "cores": pool.cores, "kind": "oracle",
+            "sample": f"{len(jobs)} problems x ({what}), one single-threaded process per core, wall time",
+            "one_core": {"value": i1 / s1, "unit": "LM iters/s", "cores": 1, "sample": f"1 problem x ({what})"},
+            "host_cpus": os.cpu_count()}
+
+
 def run_reference(args):
-    """Reference arm: the FP64 oracle on the host cores, on a bounded sample of the workload
-    (pose graphs: one problem with all its iterations and the exact implicit backward per step;
-    bundle adjustment: two LM iterations of one problem per step)."""
+    """Reference arm: the FP64 oracle on the host cores, on a bounded sample of the workload:
+    each step one problem per host core, solved in a spawn pool of single-threaded processes
+    (pose graphs: all its iterations and the backward; bundle adjustment: two LM iterations,
+    whole-system sparse solve)."""
     rank, world, _ = _dist()
     if rank != 0:
         return
-    import torch
-    from paper_2207_09442_b300 import synth
     name = args.workload
     algo, iters, _, _ = _setting(name)
     is_ba = name.startswith("ba")
     algo = algo if is_ba else (args.algo or algo)
-    batch = synth.workload(name, batch=2)
     its_per = 2 if is_ba else iters
-    cores = torch.get_num_threads()
-    kw = dict(backward=not is_ba, algo=algo, bmode=args.backward, trunc=args.trunc)
-    for _ in range(1 if is_ba else args.warmup):
-        _oracle_sample(name, batch, [0], its_per, **kw)
-    secs, its = 0.0, 0
-    for s in range(args.steps):
-        dt, n, _ = _oracle_sample(name, batch, [s % 2], its_per, **kw)
-        secs += dt
-        its += n
+    B = PER_GPU[name]
+    pool = OraclePool(B)
+    cores = pool.cores
+    mk = lambda k: [(name, (k * cores + i) % B, 1, 0, its_per, not is_ba, algo, args.backward, args.trunc)
+                    for i in range(cores)]
+    try:
+        for w in range(max(1, min(args.warmup, 1 if is_ba else args.warmup))):
+            pool.run(mk(w))
+        secs, its = 0.0, 0
+        for s in range(args.steps):
+            dt, n = pool.run(mk(s))
+            secs += dt
+            its += n
+    finally:
+        pool.close()
     value = its / secs
-    sample = (f"1 problem x {its_per} LM its (whole-system sparse solve) per step" if is_ba else
-              f"1 problem x ({iters} {algo.upper()} its + {args.backward} bwd) per step")
+    sample = (f"{cores} problems x {its_per} LM its (whole-system sparse solve) per step" if is_ba else
+              f"{cores} problems x ({iters} {algo.upper()} its + {args.backward} bwd) per step")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "LM iters/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded generator)",
-            "config": {"workload": name, "problems_per_step": 1, "iterations": its_per,
+            "config": {"workload": name, "problems_per_step": cores, "iterations": its_per,
                        "algorithm": algo.upper(), "backward": "none" if is_ba else args.backward},
             "cpu_baseline": {"value": value, "unit": "LM iters/s", "cores": cores, "kind": "oracle",
                              "sample": sample},
@@ -286,6 +346,69 @@ def _timed_region(step, args, world, dist, dev, stream, local):
     clocks = clk.summary()
     ms_per_step = max_over_ranks(sum(step_ms), dist, dev) / args.steps
     return ms_per_step, statistics.mean(fwd_ms), statistics.mean(a - b for a, b in zip(step_ms, fwd_ms)), clocks
+
+
+def _graph_replay(run, steps, dev):
+    """Forward + backward captured once into a CUDA graph and replayed ``steps`` times (L2
+    flushed between replays, outside the events): median and spread of the replay times, ms.
+    Returns None where the launch sequence cannot be captured."""
+    import torch
+    side = torch.cuda.Stream(device=dev)
+    side.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    try:
+        with torch.cuda.stream(side):
+            run()  # warm the side stream (attributes, caches) before capturing
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g, stream=side):
+            run()
+    except RuntimeError as e:
+        return {"error": str(e).splitlines()[0]}
+    torch.cuda.synchronize()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    times = []
+    for s in range(3 + steps):
+        flush.fill_(s & 0xFF)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.replay()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if s >= 3:
+            times.append(e0.elapsed_time(e1))
+    del flush, g
+    return {"ms_per_step_median": statistics.median(times), "ms_min": min(times), "ms_max": max(times),
+            "replays": steps, "warmup_replays": 3, "l2": "flushed between replays"}
+
+
+def _time_steps(fn, steps, dev):
+    """Median CUDA-event time (ms) of fn over `steps` runs after 3 warm-ups, L2 flushed first."""
+    import torch
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    ts = []
+    for s in range(3 + steps):
+        flush.fill_(s & 0xFF)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if s >= 3:
+            ts.append(e0.elapsed_time(e1))
+    del flush
+    return statistics.median(ts)
+
+
+def _measured_peaks():
+    """The machine's measured peaks (MEASURED_PEAKS.json beside this file), else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            m = json.load(f)
+        return {"bf16_tflops": float(m["bf16_tflops"]), "hbm_gbs": float(m["hbm_gbs"]), "source": "of measured"}
+    except (OSError, KeyError, ValueError):
+        return {"bf16_tflops": 1800.0, "hbm_gbs": 6400.0, "source": "of fallback"}
 
 
 def _fp64_peak(stream):
@@ -372,6 +495,8 @@ def run_pose_graphs(args, rank, world, local, dist, out):
     executed = int(info["iterations"].sum())
     nfact = info["factorizations"].astype(np.float64)
     ms_per_step, fwd_ms, bwd_ms, clocks = _timed_region(step, args, world, dist, dev, stream, local)
+    graph = _graph_replay(lambda: step(torch.cuda.Event(enable_timing=True)), args.steps, dev) \
+        if bmode != "unroll" else None
     sizes = np.diff(batch.pose_offsets)
     out.update({
         "value": executed * world / (ms_per_step * 1e-3), "ms_per_step": ms_per_step,
@@ -397,6 +522,7 @@ def run_pose_graphs(args, rank, world, local, dist, out):
         "autotune_table": tuned["table"],
         "backward_refine_steps_mean": float(np.mean(info["refine_steps"])),
         "backward_not_converged": int((info["status"] == 1).sum()),
+        "graph_replay": graph,
         "clocks": clocks})
     if args.no_extras or rank != 0:
         return
@@ -413,6 +539,21 @@ def run_pose_graphs(args, rank, world, local, dist, out):
                        "kernel": f"{kname}<{batch.kind},{'double' if precision == 'fp64' else 'float'}>"
                                  " (algorithmic FP64 block Cholesky flops of the factorizations run)",
                        "peak_source": "FP64 FMA probe on this GPU (dnls_probe_fp64_peak), of measured"}
+    # the backward kernel: per adjoint CG step two triangular solves with the cached factor
+    # (2 flops per stored entry of L each) and one Hessian-vector product counted at its
+    # Gauss-Newton part (J x and J^T (J x): 2 x 2 x 12 x dof flops per between cost), FP64
+    if bmode in ("implicit", "implicit_gn"):
+        steps_b = np.asarray(solver.info_dict()["refine_steps"], dtype=np.float64)
+        solve_fl = 4.0 * stats["n_blocks_L"] * dof * dof / B
+        hvp_fl = 4.0 * 2 * dof * dof * st.n_costs / B
+        bw_flops = float(((steps_b + 1) * (solve_fl + hvp_fl)).sum())
+        achieved_b = bw_flops / (bwd_ms * 1e-3) / 1e12
+        out["rooflines"] = [dict(out["roofline"]),
+                            {"kernel": f"k_backward<{batch.kind}> (per CG step: two triangular solves + the "
+                                       "Gauss-Newton part of the Hessian product, FP64 flops)",
+                             "bound": "alu", "achieved": achieved_b, "peak": peak, "unit": "TFLOP/s",
+                             "frac": achieved_b / peak, "cg_steps_mean": float(steps_b.mean()),
+                             "peak_source": "FP64 FMA probe on this GPU, of measured"}]
     out["factor"] = {"flops_per_factorization_batch": stats["factor_flops"],
                      "dense_equivalent_flops": stats["dense_flops"],
                      "block_updates": stats["n_block_updates"], "levels_max": stats["n_levels_max"]}
@@ -451,9 +592,26 @@ def run_pose_graphs(args, rank, world, local, dist, out):
                        "grad_max_rel_err_vs_oracle": max(gerrs) if gerrs else None,
                        "grad_sampled_problems": sample_g,
                        "grad_tolerance": 1e-8 if precision == "fp64" else 1e-4}
-    # plain FP64 per-problem GPU path: same kernels, FP64 everywhere, one problem per launch
-    nplain = min(8, B)
-    per = []
+    # the same batched solver in FP64 throughout: what mixed precision adds on top of batching
+    if precision != "fp64":
+        import dataclasses
+        s64 = layer.PoseGraphSolver(st, dataclasses.replace(opts, precision="fp64"), dev)
+        th64 = torch.empty_like(theta0)
+
+        def step64():
+            th64.copy_(theta0)
+            s64.forward(th64, meas, wd, lw, out=th64, log_radius=lr)
+            s64.backward(th64, v, meas, wd, lw, gm, gl, log_radius=lr, grad_log_radius=gr)
+
+        ms64 = _time_steps(step64, args.steps, dev)
+        out["batched_fp64"] = {"ms_per_step_median": ms64, "lm_iters_per_s": executed / (ms64 * 1e-3),
+                               "mixed_speedup": ms64 / ms_per_step}
+        del s64
+    # plain FP64 per-problem GPU path: same kernels, FP64 everywhere, one problem per launch;
+    # each problem timed `reps` times with the L2 flushed before each repeat, median per problem
+    nplain, reps = min(8, B), 5
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    per, spread = [], []
     for b_ in range(nplain):
         one = batch.problem(b_)
         s1 = layer.PoseGraphSolver(layer.PoseGraphStructure.from_batch(one),
@@ -466,15 +624,23 @@ def run_pose_graphs(args, rank, world, local, dist, out):
         v1 = t64(rng.normal(size=(int(one.pose_offsets[-1]), dof)) * 1e-2)
         s1.backward(s1.forward(*a1, log_radius=lr1), v1, *a1[1:], log_radius=lr1)
         torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        s1.backward(s1.forward(*a1, log_radius=lr1), v1, *a1[1:], log_radius=lr1)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        per.append(e0.elapsed_time(e1))
+        ts = []
+        for r_ in range(reps):
+            flush.fill_(r_ & 0xFF)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s1.backward(s1.forward(*a1, log_radius=lr1), v1, *a1[1:], log_radius=lr1)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        per.append(statistics.median(ts))
+        spread.append((max(ts) - min(ts)) / statistics.median(ts))
+    del flush
     plain_ms = statistics.mean(per) * B
     out["plain_fp64_per_problem"] = {"ms_per_batch": plain_ms, "lm_iters_per_s": executed / (plain_ms * 1e-3),
-                                     "sample": f"{nplain} problems timed one launch each, x{B}"}
+                                     "sample": f"{nplain} problems, {reps} repeats each (L2 flushed), "
+                                               f"median per problem, mean x{B}",
+                                     "max_relative_spread": max(spread)}
     out["speedup_vs_plain_fp64"] = plain_ms / ms_per_step
     # end to end through the public API with host (pinned) buffers
     h_in = [torch.as_tensor(np.ascontiguousarray(a)).pin_memory() for a in
@@ -493,13 +659,10 @@ def run_pose_graphs(args, rank, world, local, dist, out):
         return (d_in[0], gm, gl) if lr is None else (d_in[0], gm, gl, gr)
 
     out["e2e"] = _e2e(run, h_in, h_out, d_in, args.steps, stream, executed)
-    # CPU baseline: the oracle as it stands on a bounded sample (2 problems, fwd + bwd)
-    secs, its, _ = _oracle_sample(name, batch, list(range(min(2, B))), iters, algo=algo, bmode=bmode,
-                                  trunc=args.trunc)
-    out["cpu_baseline"] = {"value": its / secs, "unit": "LM iters/s", "cores": torch.get_num_threads(),
-                           "kind": "oracle",
-                           "sample": f"{min(2, B)} problems x ({iters} {algo.upper()} its + {bmode} "
-                                     "bwd), FP64 torch CPU"}
+    # CPU baseline: the oracle as it stands on a bounded sample (one problem per host core)
+    ncpu = min(os.cpu_count() or 1, B, 32)
+    out["cpu_baseline"] = _cpu_baseline(name, first, per_rank, list(range(ncpu)), iters, True, algo, bmode,
+                                        args.trunc, f"{iters} {algo.upper()} its + {bmode} bwd, FP64 torch CPU")
 
 
 # ----------------------------------------------------------------------------- bundle adjustment
@@ -540,9 +703,23 @@ def run_ba(args, rank, world, local, dist, out):
 
     step(torch.cuda.Event(enable_timing=True))
     torch.cuda.synchronize()
-    info = solver.info_dict()
+    info = solver.info_dict()  # the backward overwrites refine_* with its own adjoint solve
+    solver.forward(cams0, pts0, obs, pm, pw, b.focal, b.huber_delta)
+    torch.cuda.synchronize()
+    fwd_info = solver.info_dict()  # the forward alone: refine_* = its reduced CG solves
     executed = int(info["iterations"].sum())
     ms_per_step, fwd_ms, bwd_ms, clocks = _timed_region(step, args, world, dist, dev, stream, local)
+    graph = _graph_replay(lambda: step(torch.cuda.Event(enable_timing=True)), args.steps, dev)
+    # per-phase times from the library's event timers, in a separate pass of the same steps
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    st.set_timing(True)
+    for s_ in range(args.steps):
+        flush.fill_(s_ & 0xFF)
+        step(torch.cuda.Event(enable_timing=True))
+    phases = st.timing()
+    st.set_timing(False)
+    del flush
+    phase_ms = {k: v[0] / args.steps for k, v in phases.items()}
     C, Pn = int(np.diff(b.cam_offsets)[0]), int(np.diff(b.pt_offsets)[0])
     out.update({
         "value": executed * world / (ms_per_step * 1e-3), "ms_per_step": ms_per_step,
@@ -558,26 +735,63 @@ def run_ba(args, rank, world, local, dist, out):
         "fwd_ms": fwd_ms, "bwd_ms": bwd_ms,
         "executed_lm_iterations_per_step": executed,
         "gpu_launches": args.steps * ba_launches(iters, opts.refine_max),
-        "backward_refine_steps_mean": float(np.mean(info["refine_steps"])),
-        "backward_not_converged": int((info["status"] == 1).sum()),
+        "reduced_solver": "tensor-core FP32 factor (BF16-split tcgen05 updates) + FP64 CG",
+        "reduced_cg_steps_per_solve": float(np.sum(fwd_info["refine_steps"]) / max(1, np.sum(fwd_info["factorizations"]))),
+        "reduced_cg_resid_max": float(np.max(fwd_info["refine_resid"])),
+        "phase_ms_per_step": phase_ms,
+        "graph_replay": graph,
         "clocks": clocks})
     if args.no_extras or rank != 0:
         return
-    # roofline of the forward: per iteration the Schur gathers (a point seen k times adds
-    # k(k+1)/2 products Y_i W_j^T of 6x3x6 FMAs) plus the Cholesky of the reduced camera system
-    # (dense: every camera pair shares points), FP64 flops / forward time vs the FP64 peak
+    # rooflines of the step's kernels, from the phase timers: algorithmic work per launch x the
+    # launches in a step / the phase's time per step
     peak = _fp64_peak(stream)
+    peaks = _measured_peaks()
     pairs = 0
     for p in range(b.batch):
         k = np.bincount(b.obs_pt[b.obs_offsets[p]:b.obs_offsets[p + 1]])
         pairs += int((k * (k + 1) // 2).sum())
     n_red = 6 * C
-    flops_iter = (2.0 * 108 * pairs + b.batch * n_red ** 3 / 3.0) / b.batch
-    achieved = flops_iter * executed / (fwd_ms * 1e-3) / 1e12
-    out["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                       "frac": achieved / peak, "traffic": None,
-                       "kernel": "BA forward launch sequence (Schur gathers + reduced Cholesky)",
-                       "peak_source": "FP64 FMA probe on this GPU (dnls_probe_fp64_peak), of measured"}
+    np_red = -(-n_red // 128) * 128
+    refac = int((fwd_info["lambda"] > 1e-6).sum())  # problems the backward refactors
+    nfact = iters * b.batch + refac                 # reduced factorizations per step
+    # Schur gathers: a point seen k times adds k(k+1)/2 products Y_i W_j^T (6x3x6 FMAs), FP64
+    schur_fl = 2.0 * 108 * pairs * nfact / b.batch
+    # tensor-core factor: the Cholesky's n^3/3 FP32-level flops, each made of six BF16 products
+    # on the tensor cores; the MMAs issued (BF16 flops): per slab s and panel k the trailing
+    # update 128 x (128 (s+1) - 32 (k+1)) x 32, six products
+    fact_fl = nfact * n_red ** 3 / 3.0
+    mma_fl = 0.0
+    for s_ in range(np_red // 128):
+        for k_ in range(4 * s_ + 4):
+            mma_fl += 6 * 2.0 * 128 * max(0, 128 * (s_ + 1) - 32 * (k_ + 1)) * 32
+    mma_fl *= nfact
+    # forward CG: one FP64 product with the scaled reduced matrix (2 np^2) per step
+    cg_steps = float(np.sum(fwd_info["refine_steps"]))
+    cg_fl = cg_steps * 2.0 * np_red ** 2
+    sp = phase_ms
+    split_peak = peaks["bf16_tflops"] / 6.0
+    roofs = [
+        {"kernel": "k_ba_schur (Schur gathers S_c = H_cc - sum Y W^T, FP64)", "bound": "alu",
+         "achieved": schur_fl / (sp["schur"] * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+         "ms_per_step": sp["schur"], "peak_source": "FP64 FMA probe on this GPU, of measured"},
+        {"kernel": "k_tc_factor (reduced camera system, FP32 Cholesky with BF16-split tcgen05 "
+                   "trailing updates; flops = n^3/3 per factorization)", "bound": "tensor",
+         "achieved": fact_fl / (sp["factor"] * 1e-3) / 1e12, "peak": split_peak, "unit": "TFLOP/s",
+         "ms_per_step": sp["factor"], "factorizations_per_step": nfact,
+         "mma_bf16_tflops": mma_fl / (sp["factor"] * 1e-3) / 1e12,
+         "peak_source": f"measured bf16 {peaks['bf16_tflops']:.0f} TFLOP/s ({peaks['source']}) / 6 BF16 "
+                        "products per FP32-level product"},
+        {"kernel": "k_tc_pcg (forward reduced CG: FP64 products 2 n^2 per step)", "bound": "alu",
+         "achieved": cg_fl / (sp["solve"] * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+         "ms_per_step": sp["solve"], "cg_steps_per_step": cg_steps,
+         "peak_source": "FP64 FMA probe on this GPU, of measured"},
+    ]
+    for r_ in roofs:
+        r_["frac"] = r_["achieved"] / r_["peak"]
+    top = max(roofs, key=lambda r_: r_["ms_per_step"])
+    out["roofline"] = dict(top, traffic=None)
+    out["rooflines"] = roofs
     # accuracy on problem 0 against the oracle's whole-system sparse LM
     from oracle import ba as oba
     _, _, sols = _oracle_sample(name, b, [0], iters, backward=False)
@@ -597,27 +811,56 @@ def run_ba(args, rank, world, local, dist, out):
                                                          float((d0 - rd).norm() / rd.norm())),
                        "grad_sampled_problems": [0], "grad_tolerance": 1e-4,
                        "grads": "observations and log Huber radius"}
-    # plain FP64 per-problem GPU path: problem 0 alone, FP64 everywhere, times the batch size
-    one = b.problem(0)
-    s1 = ba_layer.BASolver(ba_layer.BAStructure.from_batch(one),
-                           layer.Options(algo=algo, iters=iters, precision="fp64", tau=0.0,
-                                         lambda0=lam0), dev)
-    a1 = (t64(one.cams_init), t64(one.pts_init), t64(one.obs_uv), t64(one.prior_meas), t64(one.prior_wdiag))
+    # the same batched solver in FP64 throughout (FP64 assembly, same reduced solver)
+    if precision != "fp64":
+        s64 = ba_layer.BASolver(st, layer.Options(algo=algo, iters=iters, precision="fp64", tau=0.0,
+                                                  lambda0=lam0), dev)
 
-    def plain():
-        c1, p1 = s1.forward(*a1, one.focal, one.huber_delta)
-        s1.backward(c1, p1, v_c[:C], v_p[:Pn], *a1[2:], one.focal, one.huber_delta)
+        def step64():
+            c_, p_ = s64.forward(cams0, pts0, obs, pm, pw, b.focal, b.huber_delta)
+            s64.backward(c_, p_, v_c, v_p, obs, pm, pw, b.focal, b.huber_delta, with_log_delta=True)
 
-    plain()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    plain()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    plain_ms = e0.elapsed_time(e1) * b.batch
+        ms64 = _time_steps(step64, args.steps, dev)
+        out["batched_fp64"] = {"ms_per_step_median": ms64, "lm_iters_per_s": executed / (ms64 * 1e-3),
+                               "mixed_speedup": ms64 / ms_per_step}
+        del s64
+    # plain FP64 per-problem GPU path: one problem per launch sequence, FP64 everywhere (FP64
+    # assembly, FP64 block Cholesky of the reduced system with direct solves); `nplain` problems,
+    # each timed `reps` times with the L2 flushed before each repeat, median per problem
+    nplain, reps = min(4, b.batch), 3
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    per, spread = [], []
+    for q in range(nplain):
+        one = b.problem(q)
+        c0_, c1_ = int(b.cam_offsets[q]), int(b.cam_offsets[q + 1])
+        s1 = ba_layer.BASolver(ba_layer.BAStructure.from_batch(one),
+                               layer.Options(algo=algo, iters=iters, precision="fp64", tau=0.0,
+                                             lambda0=lam0, reduced_solver="fp64"), dev)
+        a1 = (t64(one.cams_init), t64(one.pts_init), t64(one.obs_uv), t64(one.prior_meas), t64(one.prior_wdiag))
+
+        def plain():
+            c1, p1 = s1.forward(*a1, one.focal, one.huber_delta)
+            s1.backward(c1, p1, v_c[c0_:c1_], v_p[:Pn], *a1[2:], one.focal, one.huber_delta)
+
+        plain()
+        torch.cuda.synchronize()
+        ts = []
+        for r_ in range(reps):
+            flush.fill_(r_ & 0xFF)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            plain()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        per.append(statistics.median(ts))
+        spread.append((max(ts) - min(ts)) / statistics.median(ts))
+    del flush
+    plain_ms = statistics.mean(per) * b.batch
     out["plain_fp64_per_problem"] = {"ms_per_batch": plain_ms, "lm_iters_per_s": executed / (plain_ms * 1e-3),
-                                     "sample": f"problem 0 timed alone, x{b.batch}"}
+                                     "sample": f"{nplain} problems, {reps} repeats each (L2 flushed), median "
+                                               f"per problem, mean x{b.batch}",
+                                     "max_relative_spread": max(spread)}
     out["speedup_vs_plain_fp64"] = plain_ms / ms_per_step
     # end to end through the public API with host (pinned) buffers
     h_in = [torch.as_tensor(np.ascontiguousarray(a)).pin_memory() for a in
@@ -632,10 +875,9 @@ def run_ba(args, rank, world, local, dist, out):
         return c, p, g
 
     out["e2e"] = _e2e(run, h_in, h_out, d_in, args.steps, stream, executed)
-    secs, its, _ = _oracle_sample(name, b, [0], 2, backward=False)
-    out["cpu_baseline"] = {"value": its / secs, "unit": "LM iters/s", "cores": torch.get_num_threads(),
-                           "kind": "oracle",
-                           "sample": "problem 0 x 2 LM iterations (whole-system sparse solve, no Schur)"}
+    ncpu = min(os.cpu_count() or 1, b.batch)
+    out["cpu_baseline"] = _cpu_baseline(name, first, per_rank, list(range(ncpu)), 2, False, algo, "implicit", 0,
+                                        "2 LM its, whole-system sparse solve, no Schur")
 
 
 def main():

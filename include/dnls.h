@@ -44,7 +44,10 @@ typedef enum {
   DNLS_ERR_ARG = 1,          /* invalid argument (null pointer, bad index, bad size, bad enum) */
   DNLS_ERR_CUDA = 2,         /* a CUDA runtime call failed (launch error, out of memory, ...) */
   DNLS_ERR_WORKSPACE = 3,    /* workspace pointer null/misaligned or smaller than required */
-  DNLS_ERR_TIMEOUT = 4,      /* a bounded device-side wait gave up */
+  DNLS_ERR_TIMEOUT = 4,      /* reserved: no call returns it.  The device-side waits (the
+                                tensor-core factor's mbarrier waits, bounded at 1 s) report per
+                                problem instead: see dnls_dense_spd_solve's steps = -3, and a
+                                bundle-adjustment LM step is rejected as on a failed factor */
   DNLS_ERR_UNSUPPORTED = 5   /* option combination not implemented */
 } dnls_status;
 
@@ -112,11 +115,14 @@ typedef struct {
   double S_init;        /* objective at the initial poses */
   double S_final;       /* objective at the returned poses */
   double lambda;        /* damping of the last factorization */
-  double refine_resid;  /* backward: final ||v - H x|| / ||v|| */
+  double refine_resid;  /* backward: final ||v - H x|| / ||v||; bundle-adjustment forward on the
+                           tensor-core reduced solver: the largest final relative residual of its
+                           conjugate-gradient solves (0 on the FP64 direct path) */
   int32_t iterations;   /* iterations run (<= iters; fewer if the problem froze) */
   int32_t accepted;     /* accepted steps */
   int32_t status;       /* DNLS_PROBLEM_* (forward); backward overwrites on failure */
-  int32_t refine_steps; /* backward: adjoint-solve steps taken */
+  int32_t refine_steps; /* backward: adjoint-solve steps taken; bundle-adjustment forward on the
+                           tensor-core reduced solver: total CG steps of its reduced solves */
   int32_t factorizations; /* forward: numeric Cholesky factorizations run (GN/LM: one per
                              iteration; dogleg: one per linearization) */
   int32_t reserved;     /* zero */
@@ -228,7 +234,11 @@ dnls_status dnls_graph_backward(const dnls_graph* g, const dnls_solver_opts* opt
  *     cached factorization); the work counter it needs zeroed is cleared by each call.  Calls
  *     whose executions overlap on the GPU (other streams, other host threads) race on the array
  *     and must be serialised by the caller.  dnls_graph_backward cannot use this scratch.
- *   - Errors: DNLS_ERR_ARG, DNLS_ERR_WORKSPACE (batch too large), DNLS_ERR_CUDA. */
+ *   - The current device must be the one the handle was created on (else DNLS_ERR_ARG).
+ *   - backward_mode DNLS_BACKWARD_UNROLL (which needs per-iteration records beyond the scratch)
+ *     is refused with DNLS_ERR_UNSUPPORTED.
+ *   - Errors: DNLS_ERR_ARG, DNLS_ERR_WORKSPACE (batch too large), DNLS_ERR_UNSUPPORTED,
+ *     DNLS_ERR_CUDA. */
 #define DNLS_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
 dnls_status dnls_graph_forward_noalloc(const dnls_graph* g, const dnls_solver_opts* opts,
                                        const dnls_graph_inputs* in, double* theta, void* stream,
@@ -315,6 +325,22 @@ dnls_status dnls_ba_backward(const dnls_ba* h, const dnls_solver_opts* opts, con
                              const double* v_pts, double* grad_obs, double* grad_log_delta,
                              void* workspace, size_t workspace_bytes, void* stream, dnls_info* info);
 
+/* Phase timing of the bundle-adjustment launch sequences, for measurement (the paper has no
+ * counterpart).  With timing on, dnls_ba_forward / dnls_ba_backward record a CUDA event on their
+ * stream at every change of phase; dnls_ba_get_timing waits for the recorded events, adds the
+ * elapsed milliseconds of every interval to its phase (host ms[DNLS_BA_PHASES]; segments, may be
+ * NULL: the number of intervals) and releases them.  dnls_ba_set_timing(h, 0 or 1) discards
+ * earlier records.  Keep timing off while a stream is being captured into a CUDA graph.
+ * Phases: LINEARIZE (reprojection Jacobians, point and camera blocks), SCHUR (reduced-system
+ * gathers), DENSIFY / FACTOR / INVERSE (tensor-core path: scaled dense copy, the factor, its
+ * inverse; FP64 path: FACTOR only), SOLVE (forward reduced solve), STEP (candidate, objective,
+ * acceptance), HVP (backward Hessian products), PRECOND (backward preconditioner), OTHER. */
+enum { DNLS_BA_PHASE_LINEARIZE = 0, DNLS_BA_PHASE_SCHUR, DNLS_BA_PHASE_DENSIFY, DNLS_BA_PHASE_FACTOR,
+       DNLS_BA_PHASE_INVERSE, DNLS_BA_PHASE_SOLVE, DNLS_BA_PHASE_STEP, DNLS_BA_PHASE_HVP,
+       DNLS_BA_PHASE_PRECOND, DNLS_BA_PHASE_OTHER, DNLS_BA_PHASES };
+dnls_status dnls_ba_set_timing(dnls_ba* h, int32_t on);
+dnls_status dnls_ba_get_timing(dnls_ba* h, double* ms, int32_t* segments);
+
 /* ------------------------------------------------------------------------------------------
  * Dense batched SPD solves on the tensor cores (the dense solve of the normal equations, Sec. 2;
  * the reduced camera systems left by the Schur complement, Sec. 4.2, are solved the same way
@@ -331,7 +357,8 @@ dnls_status dnls_ba_backward(const dnls_ba* h, const dnls_solver_opts* opts, con
  *   rhs: device [batch, n] FP64.   x: device [batch, n] FP64 output (NaN where the factor failed).
  *   max_steps = 0 returns x = D (L~ L~^T)^-1 D rhs, the preconditioner alone (FP32 accuracy).
  *   steps (device int32 [batch], may be NULL): CG steps taken; -1 when the factorization failed
- *        at every shift, -2 on a CG breakdown (p^T A p <= 0: A not positive definite).
+ *        at every shift, -2 on a CG breakdown (p^T A p <= 0: A not positive definite), -3 when
+ *        a bounded wait of the factor kernel gave up (1 s; the problem is left unsolved).
  *   resid (device double [batch], may be NULL): final ||D rhs - A~ y|| / ||D rhs||.
  *   workspace: device, 256-byte aligned, dnls_dense_spd_workspace_size bytes, owned by the caller.
  * n <= DNLS_DENSE_MAX_N (DNLS_ERR_UNSUPPORTED beyond).  Errors: DNLS_ERR_ARG,

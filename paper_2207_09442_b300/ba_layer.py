@@ -38,6 +38,17 @@ class BAStructure:
     def handle(self):
         return self._h
 
+    def set_timing(self, on: bool) -> None:
+        """Record per-phase CUDA events in the following forward / backward calls (off: stop)."""
+        _d.check(_d.lib().dnls_ba_set_timing(self._h, 1 if on else 0), "dnls_ba_set_timing")
+
+    def timing(self) -> dict:
+        """Milliseconds and interval counts per phase since set_timing(True) (waits for them)."""
+        ms = (ctypes.c_double * len(_d.BA_PHASES))()
+        seg = (ctypes.c_int32 * len(_d.BA_PHASES))()
+        _d.check(_d.lib().dnls_ba_get_timing(self._h, ms, seg), "dnls_ba_get_timing")
+        return {n: (ms[i], seg[i]) for i, n in enumerate(_d.BA_PHASES)}
+
     def __del__(self):
         if getattr(self, "_h", None) is not None and _d._lib is not None:
             _d.lib().dnls_ba_destroy(self._h)

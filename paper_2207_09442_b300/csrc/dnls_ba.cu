@@ -506,6 +506,8 @@ struct BAIO {
     s.inner_resid = fmax(s.inner_resid, resid);
     if (!ok) s.bad = 1;
   }
+  // the factor kernel has already marked the step bad and the factor unusable
+  __device__ void factor_failed(int, int) const {}
 };
 
 // one CTA per problem: factor the reduced system (already damped) and solve for delta_c;
@@ -1143,6 +1145,31 @@ struct BAHandle {
   int64_t* d_prior_off = nullptr;
   int64_t* d_pt_off = nullptr;
   int sms = 148;
+  // optional per-phase timing (dnls_ba_set_timing): events recorded on the caller's stream at
+  // each change of phase; ev_phase[i] is the phase of the interval that ends at ev[i]
+  mutable bool timing = false;
+  mutable std::vector<cudaEvent_t> ev;
+  mutable std::vector<int> ev_phase;
+};
+
+// Marks the start of each phase of a forward / backward launch sequence when timing is on.
+struct PhaseTimer {
+  const BAHandle& G;
+  cudaStream_t st;
+  int cur = -1;
+  void mark(int ph) {
+    if (!G.timing || ph == cur) return;
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      cudaGetLastError();
+      return;
+    }
+    cudaEventRecord(e, st);
+    G.ev.push_back(e);
+    G.ev_phase.push_back(cur);
+    cur = ph;
+  }
+  void end() { mark(-2); }
 };
 
 }  // namespace dnls
@@ -1521,27 +1548,36 @@ constexpr int kInnerMax = 40;
 
 // one LM iteration's linearise -> eliminate -> factor -> solve chain; lam_override >= 0 replaces
 // lambda (the backward's undamped refactorization, which solves nothing)
-void ba_eliminate_and_factor(const dnls_ba* h, BAArgs& a, cudaStream_t st, double lam_override) {
+void ba_eliminate_and_factor(const dnls_ba* h, BAArgs& a, cudaStream_t st, double lam_override, PhaseTimer& pt) {
   const BAHost& H = h->impl.h;
+  pt.mark(DNLS_BA_PHASE_LINEARIZE);
   if (a.mixed && lam_override < 0.0)
     k_ba_lin<float><<<nblk(H.O, 256), 256, 0, st>>>(a);
   else
     k_ba_lin<double><<<nblk(H.O, 256), 256, 0, st>>>(a);
   k_ba_points<<<nblk(H.P, 128), 128, 0, st>>>(a, lam_override);
   k_ba_cameras<<<nblk((int64_t)H.C * 32, 256), 256, 0, st>>>(a);  // one warp per camera
+  pt.mark(DNLS_BA_PHASE_SCHUR);
   k_ba_schur<<<nblk(H.red.meta.empty() ? 1 : (int64_t)H.tgt_cam.size() * 36, 128), 128, 0, st>>>(a, lam_override);
   if (a.tc) {
     const tc::Batch tb = tc_batch(H, a);
+    pt.mark(DNLS_BA_PHASE_DENSIFY);
     tc::k_tc_densify<BASrc><<<dim3((unsigned)(H.tc_np_max / tc::kNb), (unsigned)H.B), 256, 0, st>>>(tb, BASrc{a.d, a.ws});
+    pt.mark(DNLS_BA_PHASE_FACTOR);
     tc::launch_factor(tb, st);
+    pt.mark(DNLS_BA_PHASE_INVERSE);
+    tc::launch_inverse(tb, st);
     if (lam_override < 0.0) {
       const int steps = kInnerMax;
+      pt.mark(DNLS_BA_PHASE_SOLVE);
       tc::launch_pcg(tb, BAIO{a.d, a.bc, a.dc, a.st, 1}, steps, a.mixed ? kInnerTolMixed : kInnerTolFP64,
                      tc_cluster(h->impl, steps), st);
     }
     return;
   }
+  pt.mark(DNLS_BA_PHASE_FACTOR);
   launch_reduced_factor(H, a, st);
+  pt.mark(DNLS_BA_PHASE_SOLVE);
   reduced_solve(H, a, st, 2);
 }
 
@@ -1608,6 +1644,7 @@ dnls_status dnls_ba_create(const dnls_ba_desc* desc, dnls_ba** out) {
 
 void dnls_ba_destroy(dnls_ba* h) {
   if (!h) return;
+  for (cudaEvent_t e : h->impl.ev) cudaEventDestroy(e);
   for (void* p : h->impl.dev_bufs) cudaFree(p);
   delete h;
 }
@@ -1638,13 +1675,16 @@ dnls_status dnls_ba_forward(const dnls_ba* h, const dnls_solver_opts* opts, cons
   a.info = info;
   cudaStream_t st = (cudaStream_t)stream;
   const unsigned nb = nblk(H.B), nco = nblk(H.C + H.P);
+  PhaseTimer pt{h->impl, st};
+  pt.mark(DNLS_BA_PHASE_STEP);
   k_ba_init<<<nb, 256, 0, st>>>(a);
   k_ba_eval<<<nblk(H.O, 256), 256, 0, st>>>(a, 0);
   k_ba_eval_priors<<<nblk(H.C, 128), 128, 0, st>>>(a, 0);
   k_ba_accept<<<H.B, 256, 0, st>>>(a, 0, h->impl.d_prior_off);
   k_ba_info_init<<<nb, 256, 0, st>>>(a);
   for (int it = 0; it < opts->iters; ++it) {
-    ba_eliminate_and_factor(h, a, st, -1.0);
+    ba_eliminate_and_factor(h, a, st, -1.0, pt);
+    pt.mark(DNLS_BA_PHASE_STEP);
     k_ba_update<<<nco, 256, 0, st>>>(a);
     k_ba_eval<<<nblk(H.O, 256), 256, 0, st>>>(a, 1);
     k_ba_eval_priors<<<nblk(H.C, 128), 128, 0, st>>>(a, 1);
@@ -1652,6 +1692,7 @@ dnls_status dnls_ba_forward(const dnls_ba* h, const dnls_solver_opts* opts, cons
     k_ba_commit<<<nco, 256, 0, st>>>(a);
   }
   k_ba_info<<<nb, 256, 0, st>>>(a, 0);
+  pt.end();
   return cudaGetLastError() == cudaSuccess ? DNLS_OK : DNLS_ERR_CUDA;
 }
 
@@ -1682,15 +1723,19 @@ dnls_status dnls_ba_backward(const dnls_ba* h, const dnls_solver_opts* opts, con
   a.mixed = 0;  // the backward works in FP64
   cudaStream_t st = (cudaStream_t)stream;
   const unsigned nb = nblk(H.B);
+  PhaseTimer pt{h->impl, st};
   // undamped FP64 refactorization at theta* where the cached factor is unusable or too damped
+  pt.mark(DNLS_BA_PHASE_OTHER);
   k_bab_init<<<nb, 256, 0, st>>>(a, 0);
-  ba_eliminate_and_factor(h, a, st, 0.0);
+  ba_eliminate_and_factor(h, a, st, 0.0, pt);
+  pt.mark(DNLS_BA_PHASE_OTHER);
   k_bab_refactored<<<nb, 256, 0, st>>>(a);
   k_bab_start<<<H.B, 256, 0, st>>>(a, h->impl.d_pt_off);
   // z = M^-1 r (block elimination with the cached Schur factorization): camera side into dc
   // (tensor-core path: the cached FP32 factor applied once, z_c = D (L~ L~^T)^-1 D r_c, a fixed
   // SPD operator, so the outer iteration stays plain preconditioned CG)
   auto precondition = [&]() {
+    pt.mark(DNLS_BA_PHASE_PRECOND);
     k_bap_cams<<<nblk((int64_t)H.C * 32, 256), 256, 0, st>>>(a);
     if (a.tc)
       tc::launch_pcg(tc_batch(H, a), BAIO{a.d, a.bc, a.dc, a.st, 0}, 0, 0.0, 1, st);
@@ -1699,20 +1744,61 @@ dnls_status dnls_ba_backward(const dnls_ba* h, const dnls_solver_opts* opts, con
     k_bap_pts<<<nblk(H.P, 128), 128, 0, st>>>(a);
   };
   precondition();
+  pt.mark(DNLS_BA_PHASE_OTHER);
   k_pcg<<<H.B, kPcgThreads, 0, st>>>(a, h->impl.d_pt_off, 0, 0);
   for (int it = 0; it < opts->refine_max; ++it) {
+    pt.mark(DNLS_BA_PHASE_HVP);
     k_bahvp_obs<<<nblk(H.O, 128), 128, 0, st>>>(a, 0);   // h = H p (true Hessian)
     k_bahvp_cams<<<nblk((int64_t)H.C * 32, 256), 256, 0, st>>>(a);
     k_bahvp_pts<<<nblk(H.P, 128), 128, 0, st>>>(a);
+    pt.mark(DNLS_BA_PHASE_OTHER);
     k_pcg<<<H.B, kPcgThreads, 0, st>>>(a, h->impl.d_pt_off, 1, it);
     precondition();
+    pt.mark(DNLS_BA_PHASE_OTHER);
     k_pcg<<<H.B, kPcgThreads, 0, st>>>(a, h->impl.d_pt_off, 2, it);
   }
   k_pcg_sol<<<nblk(H.C * 6 + H.P * 3, 256), 256, 0, st>>>(a);
   k_bab_finish<<<nb, 256, 0, st>>>(a);
   k_bahvp_obs<<<nblk(H.O, 128), 128, 0, st>>>(a, 1);
   k_ba_info<<<nb, 256, 0, st>>>(a, 1);
+  pt.end();
   return cudaGetLastError() == cudaSuccess ? DNLS_OK : DNLS_ERR_CUDA;
+}
+
+dnls_status dnls_ba_set_timing(dnls_ba* h, int32_t on) {
+  if (!h) return DNLS_ERR_ARG;
+  BAHandle& G = h->impl;
+  for (cudaEvent_t e : G.ev) cudaEventDestroy(e);
+  G.ev.clear();
+  G.ev_phase.clear();
+  G.timing = on != 0;
+  return DNLS_OK;
+}
+
+dnls_status dnls_ba_get_timing(dnls_ba* h, double* ms, int32_t* segments) {
+  if (!h || !ms) return DNLS_ERR_ARG;
+  BAHandle& G = h->impl;
+  for (int p = 0; p < DNLS_BA_PHASES; ++p) {
+    ms[p] = 0.0;
+    if (segments) segments[p] = 0;
+  }
+  dnls_status s = DNLS_OK;
+  if (!G.ev.empty() && cudaEventSynchronize(G.ev.back()) != cudaSuccess) s = DNLS_ERR_CUDA;
+  for (size_t i = 1; s == DNLS_OK && i < G.ev.size(); ++i) {
+    const int p = G.ev_phase[i];
+    if (p < 0 || p >= DNLS_BA_PHASES) continue;
+    float t = 0.0f;
+    if (cudaEventElapsedTime(&t, G.ev[i - 1], G.ev[i]) != cudaSuccess) {
+      s = DNLS_ERR_CUDA;
+      break;
+    }
+    ms[p] += t;
+    if (segments) segments[p] += 1;
+  }
+  for (cudaEvent_t e : G.ev) cudaEventDestroy(e);
+  G.ev.clear();
+  G.ev_phase.clear();
+  return s;
 }
 
 }  // extern "C"

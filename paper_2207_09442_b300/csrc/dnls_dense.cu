@@ -35,6 +35,9 @@ struct DenseIO {
     if (steps) steps[b] = ok ? st : -2;
     if (resid) resid[b] = res;
   }
+  __device__ void factor_failed(int b, int fstat) const {
+    if (steps) steps[b] = fstat == 2 ? -3 : -1;
+  }
 };
 
 int padded(int n) { return ((n + dnls::tc::kSlab - 1) / dnls::tc::kSlab) * dnls::tc::kSlab; }
@@ -99,7 +102,8 @@ dnls_status dnls_dense_spd_solve(int32_t batch, int32_t n, const double* A, cons
   dnls::tc::Batch tb = {batch, np, base, off, npv, nullptr, nullptr, nullptr, 0};
   DenseSrc src = {A, n};
   dnls::tc::k_tc_densify<DenseSrc><<<dim3(np / dnls::tc::kNb, batch), 256, 0, st>>>(tb, src);
-  if (dnls::tc::launch_factor(tb, st) != cudaSuccess) return DNLS_ERR_CUDA;
+  if (dnls::tc::launch_factor(tb, st) != cudaSuccess || dnls::tc::launch_inverse(tb, st) != cudaSuccess)
+    return DNLS_ERR_CUDA;
   DenseIO io = {rhs, x, steps, resid, n};
   const int kc = pick_cluster(batch, np, max_steps, sms);
   if (dnls::tc::launch_pcg(tb, io, max_steps, tol, kc, st) != cudaSuccess) return DNLS_ERR_CUDA;

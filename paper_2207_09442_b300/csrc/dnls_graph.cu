@@ -1742,6 +1742,12 @@ extern "C" dnls_status dnls_graph_forward_noalloc(const dnls_graph* g, const dnl
   if (!g || !in || !theta || !in->meas || !in->wdiag) return DNLS_ERR_ARG;
   dnls_status s = check_opts(opts);
   if (s != DNLS_OK) return s;
+  // the records an unrolled backward needs would not fit the fixed scratch: not offered here
+  if (opts->backward_mode == DNLS_BACKWARD_UNROLL) return DNLS_ERR_UNSUPPORTED;
+  // the scratch is per device: the handle's structure lives on the device it was created on
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess) return DNLS_ERR_CUDA;
+  if (cur != g->impl.device) return DNLS_ERR_ARG;
   if (g->impl.h.ws_bytes > (int64_t)DNLS_NOALLOC_SCRATCH_BYTES) return DNLS_ERR_WORKSPACE;
   void* scratch = nullptr;
   if ((s = noalloc_scratch(&scratch)) != DNLS_OK) return s;

@@ -380,7 +380,11 @@ cudaError_t launch_factor(const Batch& tb, cudaStream_t st) {
   cudaError_t e = cudaFuncSetAttribute(k_tc_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, kFactorSmem);
   if (e != cudaSuccess) return e;
   k_tc_factor<<<tb.B, kFactorThreads, kFactorSmem, st>>>(tb, 1000000000ull);
-  e = cudaFuncSetAttribute(k_tc_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, kInverseSmem);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_inverse(const Batch& tb, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(k_tc_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, kInverseSmem);
   if (e != cudaSuccess) return e;
   k_tc_inverse<<<dim3((unsigned)(tb.np_max / kNb), (unsigned)tb.B), 256, kInverseSmem, st>>>(tb);
   return cudaGetLastError();

@@ -8,8 +8,8 @@
 //            FP64 scaled system is the original one; diagonal in [1, 4)), FP64 row-major np x np
 //   factor   L~ L~^T = A~ (+ sigma I on retry) in FP32: right-looking by 32-wide panels; the
 //            128-row slab being factored lives in tensor memory as an FP32 accumulator, each
-//            panel's diagonal block is factored and inverted in FP32 by one warp, the panel rows
-//            below it are L_ik = A_ik L_kk^-T, and the trailing update A_ij -= L_ik L_jk^T is
+//            panel's diagonal block is factored in FP32 by one warp, the panel rows below it
+//            solve L_ik L_kk^T = A_ik by substitution, and the trailing update A_ij -= L_ik L_jk^T is
 //            issued as tcgen05.mma (kind::f16, BF16 operands, FP32 accumulation) on the 3-term
 //            BF16 split x = x0 + x1 + x2 of the FP32 panel (products x0y0 + x0y1 + x1y0 + x0y2 +
 //            x1y1 + x2y0, which keeps FP32-level accuracy: Henry, Tang & Heinecke, "Leveraging
@@ -17,10 +17,12 @@
 //            ARITH 2019).  Slabs are taken in turn (left-looking over slabs, right-looking inside
 //            one): the rows of earlier slabs enter a later slab's updates as MMA B operands,
 //            copied from a global staging area into shared memory with cp.async.bulk.
-//   solve    preconditioned conjugate gradients in FP64 on A~ x~ = D b with M = L~ L~^T
-//            (FP32 triangular solves), then x = D x~.  A thread-block cluster per problem: every
-//            CTA multiplies its rows of A~ (FP64), CTA 0 runs the updates and the triangular
-//            solves.  With max_steps = 0 the call applies M^-1 once (a preconditioner).
+//   inverse  X = L~^-1 in FP32 by 32-column panels (one CTA per problem and panel), stored with
+//            its transpose, so that applying M^-1 = X^T X is two dense products
+//   solve    preconditioned conjugate gradients in FP64 on A~ x~ = D b with M = L~ L~^T, then
+//            x = D x~.  A thread-block cluster per problem: each CTA owns a block of rows and
+//            forms their part of the FP64 product with A~ and of the two FP32 products with X.
+//            With max_steps = 0 the call applies M^-1 once (a preconditioner).
 //
 // Operand layout for tcgen05.mma (K-major, no swizzle): a 32-column BF16 panel of R rows is
 // stored as core matrices of 8 rows x 16 bytes; the core matrix of row group g and K chunk q
@@ -284,10 +286,11 @@ __global__ void __launch_bounds__(256) k_tc_densify(Batch tb, Src src) {
 }
 
 // ----------------------------------------------------------------------------- factor
-// One CTA of kFactorThreads per active problem (dnls_tc.cu): L~ into the region's L / Linv,
-// then X = L~^-1 (one CTA per problem and 32-column panel).  Errors surface through the
-// returned launch status.
+// One CTA of kFactorThreads per active problem (dnls_tc.cu): L~ into the region's L / Linv;
+// launch_inverse then forms X = L~^-1 and X^T (one CTA per problem and 32-column panel).
+// Errors surface through the returned launch status.
 cudaError_t launch_factor(const Batch& tb, cudaStream_t st);
+cudaError_t launch_inverse(const Batch& tb, cudaStream_t st);
 
 // ----------------------------------------------------------------------------- solve
 // Sum (or max) over the CTA in a fixed order: warp shuffles, then every thread adds the warps'
@@ -366,6 +369,7 @@ __device__ __forceinline__ void cta_reduce2(double& a, double& c, double* red) {
 //   IO::n(b)                 the order
 //   IO::out(b, i, x_i)       the solution (i < n), written once converged or stopped
 //   IO::report(b, steps, resid, ok)   per-problem outcome (ok false: a breakdown, p'Ap <= 0)
+//   IO::factor_failed(b, fstat)       the factor failed (1) or timed out (2): nothing solved
 // max_steps = 0 applies M^-1 once (x = D X^T X D b).
 template <class IO>
 __global__ void __launch_bounds__(kPcgThreads, 1) k_tc_pcg(Batch tb, IO io, int max_steps, double tol, int kc) {
@@ -379,7 +383,10 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_tc_pcg(Batch tb, IO io, int 
   const int np = tb.np[b];
   char* R = tb.base + tb.off[b];
   Hdr* hdr = (Hdr*)R;
-  if (hdr->fstat != 0) return;  // written by the factor launch; the same for the whole cluster
+  if (hdr->fstat != 0) {  // written by the factor launch; the same for the whole cluster
+    if (rank == 0 && threadIdx.x == 0) io.factor_failed(b, hdr->fstat);
+    return;
+  }
   const Region rg = Region::of(np);
   const double* A = (const double*)(R + rg.A);
   const double* d = (const double*)(R + rg.d);

@@ -63,6 +63,7 @@ class BAInputs(ctypes.Structure):
 
 
 DENSE_MAX_N = 384
+BA_PHASES = ["linearize", "schur", "densify", "factor", "inverse", "solve", "step", "hvp", "precond", "other"]
 INFO_BYTES = 56  # dnls_info: 4 doubles + 6 int32
 
 
@@ -100,6 +101,8 @@ _SIGS = {
                                    c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                    c_void_p, c_size_t, c_void_p, c_void_p]),
     "dnls_probe_fp64_peak": (c_int32, [c_int32, c_void_p, ctypes.POINTER(c_double)]),
+    "dnls_ba_set_timing": (c_int32, [c_void_p, c_int32]),
+    "dnls_ba_get_timing": (c_int32, [c_void_p, c_void_p, c_void_p]),
     "dnls_dense_spd_workspace_size": (c_int32, [c_int32, c_int32, ctypes.POINTER(c_size_t)]),
     "dnls_dense_spd_solve": (c_int32, [c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_int32, c_double,
                                        c_void_p, c_size_t, c_void_p, c_void_p, c_void_p]),

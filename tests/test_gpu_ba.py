@@ -123,3 +123,72 @@ def test_full_ba_b32_forward_backward_sampled(full_ba, precision, tol, gtol):
     ref = oba.implicit_grad_obs(P, th, v)[0]
     gerr = rel(g[:int(b.obs_offsets[1])], ref)
     assert gerr < gtol, gerr
+
+
+def _ba_inputs(b):
+    return (t64(b.cams_init), t64(b.pts_init), t64(b.obs_uv), t64(b.prior_meas), t64(b.prior_wdiag))
+
+
+@pytest.mark.parametrize("solver", ["tc", "fp64"])
+def test_ba_cuda_graph_capture_replays_forward_and_backward(solver):
+    """The BA forward + implicit backward launch sequence (Schur gathers, the reduced solver's
+    cluster launches, the adjoint CG) captured once in a CUDA graph and replayed on new
+    observations gives the eager results."""
+    from paper_2207_09442_b300 import ba_layer, layer
+    b = synth.ba(batch=3, n_cams=12, n_pts=80, config_id=62)
+    st = ba_layer.BAStructure.from_batch(b)
+    opts = layer.Options(algo="lm", iters=6, precision="mixed_fp32", reduced_solver=solver)
+    sol = ba_layer.BASolver(st, opts)
+    cams0, pts0, obs, pm, pw = _ba_inputs(b)
+    v_c = t64(np.random.default_rng(3).normal(size=(st.n_cams, 6)) * 1e-2)
+    v_p = torch.zeros(st.n_pts, 3, dtype=torch.float64, device=DEV)
+    f, dl = b.focal, b.huber_delta
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):  # warm-up outside capture
+        c, p = sol.forward(cams0, pts0, obs, pm, pw, f, dl)
+        sol.backward(c, p, v_c, v_p, obs, pm, pw, f, dl)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        c, p = sol.forward(cams0, pts0, obs, pm, pw, f, dl)
+        g = sol.backward(c, p, v_c, v_p, obs, pm, pw, f, dl)
+    obs.add_(torch.as_tensor(np.random.default_rng(4).normal(size=tuple(obs.shape)) * 0.1, device=DEV))
+    graph.replay()
+    torch.cuda.synchronize()
+    got = (c.clone(), p.clone(), g.clone())
+    ref = ba_layer.BASolver(st, opts)
+    ce, pe = ref.forward(cams0, pts0, obs, pm, pw, f, dl)
+    ge = ref.backward(ce, pe, v_c, v_p, obs, pm, pw, f, dl)
+    torch.cuda.synchronize()
+    assert rel(got[0], ce) < 1e-12 and rel(got[1], pe) < 1e-12
+    assert rel(got[2], ge) < 1e-10
+
+
+def test_ba_phase_timers_cover_the_step():
+    """The library's per-phase event timers: every phase of the tensor-core path is timed, the
+    Schur phase once per factorization, and the phases add up to the step's wall time."""
+    from paper_2207_09442_b300 import ba_layer, layer
+    b = synth.ba(batch=2, n_cams=12, n_pts=80, config_id=63)
+    st = ba_layer.BAStructure.from_batch(b)
+    sol = ba_layer.BASolver(st, layer.Options(algo="lm", iters=5, precision="mixed_fp32", reduced_solver="tc"))
+    cams0, pts0, obs, pm, pw = _ba_inputs(b)
+    v_c = t64(np.random.default_rng(5).normal(size=(st.n_cams, 6)) * 1e-2)
+    v_p = torch.zeros(st.n_pts, 3, dtype=torch.float64, device=DEV)
+    sol.forward(cams0, pts0, obs, pm, pw, b.focal, b.huber_delta)
+    torch.cuda.synchronize()
+    st.set_timing(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    c, p = sol.forward(cams0, pts0, obs, pm, pw, b.focal, b.huber_delta)
+    sol.backward(c, p, v_c, v_p, obs, pm, pw, b.focal, b.huber_delta)
+    e1.record()
+    ph = st.timing()
+    st.set_timing(False)
+    wall = e0.elapsed_time(e1)
+    for k in ("linearize", "schur", "densify", "factor", "inverse", "solve", "step", "hvp", "precond", "other"):
+        assert ph[k][0] > 0.0 and ph[k][1] > 0, k
+    assert 5 <= ph["schur"][1] <= 6  # five LM iterations and at most one backward refactorization
+    total = sum(v[0] for v in ph.values())
+    assert 0.5 * wall < total <= wall * 1.001 + 0.05, (total, wall)

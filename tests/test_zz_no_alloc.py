@@ -92,3 +92,35 @@ def test_noalloc_rejects_batch_larger_than_its_scratch():
     assert rc == dnls.ERR_WORKSPACE
     torch.cuda.synchronize()
     assert torch.equal(theta, th0)  # nothing was launched
+
+
+def test_noalloc_refuses_unrolled_backward_records():
+    """An unrolled backward needs per-iteration records that the fixed scratch does not hold:
+    the call is refused before anything is launched."""
+    from paper_2207_09442_b300 import synth
+    L, dnls = _lib()
+    batch = synth.pgo_se3(batch=2, n_poses=16, n_lc=4, config_id=33)
+    st, opts, (th0, meas, wd, lw) = _setup(batch, "fp64")
+    copts = opts.c()
+    copts.backward_mode = dnls.BACKWARD_UNROLL
+    theta = th0.clone()
+    inp = dnls.GraphInputs(meas.data_ptr(), wd.data_ptr(), lw.data_ptr())
+    rc = L.dnls_graph_forward_noalloc(st.handle, ctypes.byref(copts), ctypes.byref(inp),
+                                      theta.data_ptr(), torch.cuda.current_stream().cuda_stream, None)
+    assert rc == dnls.ERR_UNSUPPORTED
+    torch.cuda.synchronize()
+    assert torch.equal(theta, th0)
+
+
+@pytest.mark.skipif(torch.cuda.device_count() < 2, reason="needs a second GPU to make another device current")
+def test_noalloc_refuses_a_handle_of_another_device():
+    from paper_2207_09442_b300 import synth
+    L, dnls = _lib()
+    batch = synth.pgo_se3(batch=2, n_poses=16, n_lc=4, config_id=34)
+    st, opts, (th0, meas, wd, lw) = _setup(batch, "fp64")  # created on device 0
+    copts = opts.c()
+    inp = dnls.GraphInputs(meas.data_ptr(), wd.data_ptr(), lw.data_ptr())
+    with torch.cuda.device(1):
+        rc = L.dnls_graph_forward_noalloc(st.handle, ctypes.byref(copts), ctypes.byref(inp),
+                                          th0.data_ptr(), None, None)
+    assert rc == dnls.ERR_ARG
