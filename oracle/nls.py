@@ -4,9 +4,9 @@ TEST INFRASTRUCTURE ONLY (see the package docstring).
 
 One iteration: H = J^T J, g = J^T r; LM adds lambda * D with D = diag(max(diag H, 1e-9));
 delta = -(H + lambda D)^-1 g (Cholesky, dense via torch.linalg, or sparse LU via SciPy);
-theta_c = theta (+) delta; accept iff S(theta_c) < S(theta) (GN always accepts); on accept
+theta_c = theta (+) delta; accept iff S(theta_c) <= S(theta) (GN always accepts); on accept
 lambda <- max(lambda/10, 1e-12) and the problem is re-linearised at theta_c, on reject
-lambda <- min(10 lambda, 1e12).  A tie (S(theta_c) == S(theta)) is accepted: near the optimum
+lambda <- min(10 lambda, 1e12).  The tie (S(theta_c) == S(theta)) is accepted: near the optimum
 of an ill-conditioned problem S is flat to FP64 resolution along weak directions, and the GN step
 (computed from the accurate gradient) must still be allowed to move there.  With tau > 0 a
 problem stops ("freezes") once |S_old - S_c| <= tau S_old; tau = 0 runs every iteration.

@@ -82,10 +82,22 @@ def test_dlm_through_autograd_layer():
                                                  backward_mode="dlm", dlm_eps=1e-3))
     t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=DEV)
     logw = torch.zeros(len(b.logw), dtype=torch.float32, device=DEV, requires_grad=True)
-    sol, _ = lay({"theta": t(b.theta_init), "meas": t(b.meas), "wdiag": t(b.wdiag), "logw": logw})
+    meas = t(b.meas).requires_grad_(True)
+    sol, _ = lay({"theta": t(b.theta_init), "meas": meas, "wdiag": t(b.wdiag), "logw": logw})
     loss = ((sol["theta"] - t(b.theta_gt)) ** 2).sum()
     loss.backward()
-    assert logw.grad is not None and torch.isfinite(logw.grad).all() and float(logw.grad.abs().max()) > 0
+    # against the oracle's DLM gradients at the GPU's solution, through the projection / lift
+    g_tan = layer.project_grad(2, meas.detach(), meas.grad).cpu()
+    theta = sol["theta"].detach()
+    for k in range(b.batch):
+        g = pgo.graph_from_batch(b, k)
+        g.logw = torch.zeros_like(g.logw)  # the layer gets zero log-weights here
+        th_k = poses_of(b, theta, k)
+        gt_k = torch.as_tensor(b.theta_gt[b.pose_offsets[k]:b.pose_offsets[k + 1]])
+        vk = pgo.tangent_grad(2, lambda X: ((X - gt_k) ** 2).sum(), th_k)
+        rm, rl, _ = pgo.dlm_grads(g, th_k, vk, 1e-3)
+        assert rel(edges_of(b, g_tan, k), rm) < 1e-8, (k, rel(edges_of(b, g_tan, k), rm))
+        assert rel(edges_of(b, logw.grad, k).double(), rl) < 1e-7, (k, rel(edges_of(b, logw.grad, k).double(), rl))
 
 
 def test_dlm_rejects_nonpositive_eps():

@@ -82,7 +82,15 @@ def test_robust_radius_gradient_through_autograd_layer():
     sol, _ = lay({"theta": t64(b.theta_init), "meas": t64(b.meas), "wdiag": t64(b.wdiag),
                   "logw": t32(b.logw), "log_radius": lr})
     ((sol["theta"] - t64(b.theta_gt)) ** 2).sum().backward()
-    assert lr.grad is not None and torch.isfinite(lr.grad).all() and float(lr.grad.abs().max()) > 0
+    # against the oracle's Eq. 3 gradient w.r.t. the log radii at the GPU's solution
+    theta = sol["theta"].detach()
+    for k in range(b.batch):
+        g = pgo.graph_from_batch(b, k)
+        th_k = poses_of(b, theta, k)
+        gt_k = torch.as_tensor(b.theta_gt[b.pose_offsets[k]:b.pose_offsets[k + 1]])
+        vk = pgo.tangent_grad(3, lambda X: ((X - gt_k) ** 2).sum(), th_k)
+        rr = pgo.implicit_grad_log_radius(g, th_k, vk, "exact")
+        assert rel(edges_of(b, lr.grad, k), rr) < 1e-8, (k, rel(edges_of(b, lr.grad, k), rr))
 
 
 def test_dlm_with_robust_costs_is_unsupported():

@@ -593,6 +593,130 @@ def test_ba_implicit_gradient_wrt_huber_radius_vs_fd():
     assert float(gd[inside].abs().max()) == 0.0
 
 
+def test_ba_point_jacobian_vs_central_differences():
+    """The point Jacobian of the reprojection residual (the camera one is checked above)."""
+    b = synth.ba(batch=1, n_cams=10, n_pts=40, config_id=402)
+    P = ba.ba_from_batch(b, 0)
+    c, Jc, Jp, rq, Jq = ba._local_jacobians(P, (P.cams_init, P.pts_init))
+    h = 1e-6
+    z6 = torch.zeros(len(P.obs_cam), 6, dtype=F64)
+    for a in range(3):
+        e = torch.zeros(len(P.obs_cam), 3, dtype=F64)
+        e[:, a] = h
+        cp = ba.reproj_cost(P.cams_init[P.obs_cam], P.pts_init[P.obs_pt], P.obs_uv, P.focal, z6, e, 0)
+        cm = ba.reproj_cost(P.cams_init[P.obs_cam], P.pts_init[P.obs_pt], P.obs_uv, P.focal, z6, -e, 0)
+        assert ((cp - cm) / (2 * h) - Jp[:, :, a]).abs().max() < 1e-5 * (1 + Jp.abs().max())
+
+
+def _ba_tangent_gradient(P, cams, pts):
+    """d S(cams Exp(xi), pts + dp) / d(xi, dp) at 0 by autograd through the oracle's objective."""
+    xi = torch.zeros(P.n_cams, 6, dtype=F64, requires_grad=True)
+    dp = torch.zeros(P.n_pts, 3, dtype=F64, requires_grad=True)
+    c2 = lie.flat_se3(lie.se3_retract(lie.as_se3(cams), xi))
+    S = ba.objective(P, (c2, pts + dp))
+    gx, gp = torch.autograd.grad(S, (xi, dp))
+    return torch.cat([gx.reshape(-1), gp.reshape(-1)])
+
+
+def test_ba_lm_result_is_stationary():
+    """At the result of the oracle's LM loop the gradient of the robust objective (autograd, an
+    independent route from the IRLS-weighted J^T r the loop uses) vanishes: a wrong IRLS weight
+    (rho' for sqrt(rho')) or point retraction would leave it at the size of the initial one."""
+    b = synth.ba(batch=1, n_cams=8, n_pts=40, config_id=403)
+    P = ba.ba_from_batch(b, 0)
+    g0 = _ba_tangent_gradient(P, P.cams_init, P.pts_init)
+    (cams, pts), info = ba.solve(P, iters=40, tau=0.0)
+    g1 = _ba_tangent_gradient(P, cams, pts)
+    assert float(g1.norm()) <= 1e-9 * float(g0.norm()), (float(g1.norm()), float(g0.norm()))
+    # some observations sit beyond the Huber radius, so the robust weights are exercised
+    cs = ba.reproj_cost(cams[P.obs_cam], pts[P.obs_pt], P.obs_uv, P.focal,
+                        torch.zeros(len(P.obs_cam), 6, dtype=F64), torch.zeros(len(P.obs_cam), 3, dtype=F64), 0)
+    assert bool((cs.norm(dim=-1) > P.delta).any())
+
+
+def _independent_ba_objective(P):
+    """The BA objective written from its definition with NumPy / SciPy only: cameras as
+    (rotation vector, translation) of the camera-to-world pose, p_c = R^T (p - t), pinhole
+    projection, Huber on the squared pixel error, camera priors 1/2 ||w (x) Log(Z^-1 T)||^2 with
+    the SE(3) logarithm taken as the matrix logarithm."""
+    C, Np = P.n_cams, P.n_pts
+    oc, op, uv = P.obs_cam.numpy(), P.obs_pt.numpy(), P.obs_uv.numpy()
+    f, dl = P.focal, P.delta
+    Z = [P.prior_meas[q].numpy().reshape(3, 4) for q in range(len(P.prior_cam))]
+    W = P.prior_w.numpy()
+
+    def unpack(x):
+        R = Rotation.from_rotvec(x[:3 * C].reshape(C, 3)).as_matrix()
+        t = x[3 * C:6 * C].reshape(C, 3)
+        return R, t, x[6 * C:].reshape(Np, 3)
+
+    def S(x):
+        R, t, pts = unpack(x)
+        pc = np.einsum("oji,oj->oi", R[oc], pts[op] - t[oc])
+        e = f * pc[:, :2] / pc[:, 2:3] - uv
+        s = (e * e).sum(1)
+        rho = np.where(s <= dl * dl, s, 2 * dl * np.sqrt(np.maximum(s, dl * dl)) - dl * dl)
+        tot = 0.5 * rho.sum()
+        for q, c in enumerate(P.prior_cam.tolist()):
+            T = np.eye(4)
+            T[:3, :3], T[:3, 3] = R[c], t[c]
+            Zq = np.eye(4)
+            Zq[:3, :] = Z[q]
+            Lg = np.real(sla.logm(np.linalg.solve(Zq, T)))
+            xi = np.concatenate([Lg[:3, 3], [Lg[2, 1], Lg[0, 2], Lg[1, 0]]])
+            tot += 0.5 * float(((W[q] * xi) ** 2).sum())
+        return tot
+
+    def pack(cams, pts):
+        T = cams.numpy().reshape(C, 3, 4)
+        return np.concatenate([Rotation.from_matrix(T[:, :, :3]).as_rotvec().reshape(-1),
+                               T[:, :, 3].reshape(-1), pts.numpy().reshape(-1)])
+
+    return S, pack, unpack
+
+
+def test_tiny_ba_against_scipy_minimize():
+    """Three cameras, ten points: the oracle's LM optimum is the minimiser SciPy finds for the
+    independently written robust objective (started at the oracle's initial point)."""
+    b = synth.ba(batch=1, n_cams=3, n_pts=10, k_range=(2, 3), config_id=404, pixel_sigma=2.0, huber_delta=1.0)
+    P = ba.ba_from_batch(b, 0)
+    (cams, pts), _ = ba.solve(P, iters=60, tau=0.0)
+    S, pack, unpack = _independent_ba_objective(P)
+    x_or = pack(cams, pts)
+    assert abs(S(x_or) - float(ba.objective(P, (cams, pts)))) < 1e-10 * S(x_or)  # same objective
+    x0 = pack(P.cams_init, P.pts_init)
+    res = so.minimize(S, x0, method="BFGS", options={"gtol": 1e-10, "maxiter": 20000})
+    assert S(x_or) <= res.fun * (1 + 1e-10)                     # the oracle's point is no worse
+    # the independent objective is stationary there (central differences, relative to the start)
+    grad = lambda x: np.array([(S(x + e) - S(x - e)) / 2e-7 for e in np.eye(len(x)) * 1e-7])
+    assert np.linalg.norm(grad(x_or)) < 1e-5 * np.linalg.norm(grad(x0))
+    Rs, ts, ps = unpack(res.x)
+    Ro, to, po = unpack(x_or)
+    err = max(np.abs(ts - to).max(), np.abs(ps - po).max(), np.abs(Rs - Ro).max())
+    assert err < 5e-5, err  # BFGS on finite differences stops within ~1e-5 of the minimiser
+    # the robust branch is exercised at the optimum
+    pc = np.einsum("oji,oj->oi", Ro[P.obs_cam.numpy()], po[P.obs_pt.numpy()] - to[P.obs_cam.numpy()])
+    e = P.focal * pc[:, :2] / pc[:, 2:3] - P.obs_uv.numpy()
+    assert (np.linalg.norm(e, axis=1) > P.delta).any()
+
+
+def test_ba_tangent_grad_vs_central_differences():
+    """ba.tangent_grad (the outer loss's gradient on the camera tangents) against central
+    differences of camera_loss along the right perturbation; points get zeros."""
+    b = synth.ba(batch=1, n_cams=6, n_pts=20, k_range=(2, 4), config_id=405)
+    P = ba.ba_from_batch(b, 0)
+    v = ba.tangent_grad(P, P.cams_init)
+    h = 1e-6
+    for c in (0, 3, 5):
+        for a in range(6):
+            xi = torch.zeros(P.n_cams, 6, dtype=F64)
+            xi[c, a] = h
+            lp = ba.camera_loss(lie.flat_se3(lie.se3_retract(lie.as_se3(P.cams_init), xi)), P.cams_gt)
+            lm = ba.camera_loss(lie.flat_se3(lie.se3_retract(lie.as_se3(P.cams_init), -xi)), P.cams_gt)
+            assert abs(float((lp - lm) / (2 * h)) - float(v[6 * c + a])) < 1e-8
+    assert float(v[6 * P.n_cams:].abs().max()) == 0.0
+
+
 # ----------------------------------------------------------------------------- unrolled / truncated
 def test_truncated_over_all_iterations_is_the_unrolled_gradient():
     b = synth.pgo_se3(batch=1, n_poses=10, n_lc=3, config_id=130, log_weights=True)
