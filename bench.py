@@ -38,7 +38,8 @@ WORKLOAD = "pgo_se3_b256"
 # problems per GPU of each named workload (algorithm, iterations, precision and lambda0 come
 # from the workload table of the synthetic-data module)
 PER_GPU = {"pgo_se2_b16": 16, "pgo_se3_b256": 256, "pgo_se3_implicit_b256": 256,
-           "pgo_se3_uneven_b1024": 1024, "pgo_se3_robust_b256": 256, "ba_b32": 32}
+           "pgo_se3_uneven_b1024": 1024, "pgo_se3_robust_b256": 256, "ba_b32": 32,
+           "pgo_se3_p2048_b256": 256, "pgo_se3_p4096_b64": 64}
 METRIC = "batched LM iters/s (fwd + implicit bwd) vs plain FP64 GPU path at 1e-5"
 # DRAM bytes (read + write) per launch of the dominant kernel, from a full ncu capture of the
 # forward kernel built from the sources that hash to the recorded value (a 64-problem case,
@@ -85,6 +86,9 @@ def _args():
     ap.add_argument("--no-extras", action="store_true", help="skip baselines (for profiling)")
     ap.add_argument("--batch", type=int, default=0,
                     help="first N problems only (profiling captures); default: the full workload")
+    ap.add_argument("--scaling", default="weak", choices=["weak", "strong"],
+                    help="pose graphs: weak = every rank solves its own full batch; strong = one "
+                         "batch split over the ranks, balanced by per-problem factorization flops")
     ap.add_argument("--shape", default="",
                     help="threads,ctas_per_sm,smem_factor: fixed launch shape instead of autotuning")
     return ap.parse_args()
@@ -109,12 +113,36 @@ def rank_problems(rank: int, per_rank: int):
     return rank * per_rank, per_rank
 
 
+def balanced_partition(costs, world: int):
+    """Strong scaling: the problems of one batch split over `world` ranks so that the ranks'
+    summed costs (per-problem factorization flops) are nearly equal: longest first, each to the
+    least-loaded rank (ties to the lower rank), every rank's list then sorted.  Deterministic, so
+    every rank computes the same partition without a collective."""
+    order = sorted(range(len(costs)), key=lambda i: (-float(costs[i]), i))
+    load = [0.0] * world
+    parts = [[] for _ in range(world)]
+    for i in order:
+        r = min(range(world), key=lambda k: (load[k], k))
+        parts[r].append(i)
+        load[r] += float(costs[i])
+    return [sorted(p) for p in parts], load
+
+
 def max_over_ranks(value: float, dist, device) -> float:
     """The slowest rank's time (the job's time); a no-op on one process."""
     import torch
     t = torch.tensor([value], dtype=torch.float64, device=device)
     if dist is not None and dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(value: float, dist, device) -> float:
+    """The units all ranks processed (their sum); the value itself on one process."""
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    if dist is not None and dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
     return float(t.item())
 
 
@@ -455,8 +483,18 @@ def run_pose_graphs(args, rank, world, local, dist, out):
     algo = args.algo or algo
     bmode = args.backward
     dev = torch.device("cuda", local)
-    first, per_rank = rank_problems(rank, args.batch or PER_GPU[name])
-    batch = synth.workload(name, batch=per_rank, first=first)
+    part_info = None
+    if args.scaling == "strong" and world > 1:
+        # one batch over all ranks: costs from the library's symbolic factorization of it
+        full = synth.workload(name, batch=args.batch or PER_GPU[name])
+        costs = layer.PoseGraphStructure.from_batch(full).factor_flops_per_problem()
+        parts, load = balanced_partition(costs, world)
+        batch = full.subset(parts[rank])
+        first, per_rank = 0, batch.batch
+        part_info = {"problems": [len(p) for p in parts], "flops_max_over_mean": max(load) / (sum(load) / world)}
+    else:
+        first, per_rank = rank_problems(rank, args.batch or PER_GPU[name])
+        batch = synth.workload(name, batch=per_rank, first=first)
     B, dof = batch.batch, batch.dof
     st = layer.PoseGraphStructure.from_batch(batch)
     stats = st.stats()
@@ -473,7 +511,8 @@ def run_pose_graphs(args, rank, world, local, dist, out):
         thr, ctas, smem = (int(x) for x in args.shape.split(","))
         tuned = {"threads": thr, "ctas_per_sm": ctas, "smem_factor": smem, "table": "fixed by --shape"}
     else:
-        tuned = autotune.tune(st, opts, (theta0, meas, wd, lw), v, use_cache=False)
+        big = int(np.diff(batch.pose_offsets).max()) > 1024
+        tuned = autotune.tune(st, opts, (theta0, meas, wd, lw), v, use_cache=False, reps=1 if big else 2)
     opts = autotune.apply(opts, tuned)
     solver = layer.PoseGraphSolver(st, opts, dev)
     theta = torch.empty_like(theta0)
@@ -499,7 +538,7 @@ def run_pose_graphs(args, rank, world, local, dist, out):
         if bmode != "unroll" else None
     sizes = np.diff(batch.pose_offsets)
     out.update({
-        "value": executed * world / (ms_per_step * 1e-3), "ms_per_step": ms_per_step,
+        "value": sum_over_ranks(executed, dist, dev) / (ms_per_step * 1e-3), "ms_per_step": ms_per_step,
         "dtype": ("f64" if precision == "fp64" else
                   "mixed: f32 linearize/assemble, f64 factor/solve/accept/backward"),
         "data": f"synthetic (seeded generator, random-walk SE({batch.kind}) graphs)",
@@ -524,6 +563,10 @@ def run_pose_graphs(args, rank, world, local, dist, out):
         "backward_not_converged": int((info["status"] == 1).sum()),
         "graph_replay": graph,
         "clocks": clocks})
+    if part_info is not None:
+        out["scaling"] = "strong"
+        out["partition"] = part_info
+        out["config"]["parallelism"] = f"{world} GPU(s), one batch split by factorization flops (strong)"
     if args.no_extras or rank != 0:
         return
     # roofline of the dominant kernel (the forward, FP64-factorization bound): algorithmic FP64
@@ -558,7 +601,10 @@ def run_pose_graphs(args, rank, world, local, dist, out):
                      "dense_equivalent_flops": stats["dense_flops"],
                      "block_updates": stats["n_block_updates"], "levels_max": stats["n_levels_max"]}
     # accuracy at this configuration against the oracle on sampled problems
-    sample = sorted({0, B // 2, B - 1, int(sizes.argmax())})
+    # problems above 1024 poses: the oracle's dense solve takes minutes per problem, so no
+    # oracle samples here (their parity is the 1024-pose SE(3) GPU test)
+    big = int(sizes.max()) > 1024
+    sample = sorted({0, B // 2, B - 1, int(sizes.argmax())}) if not big else []
     _, _, sols = _oracle_sample(name, batch, sample, iters, backward=False, algo=algo)
     th_cpu = theta.cpu()
     errs = [float((th_cpu[int(batch.pose_offsets[b]):int(batch.pose_offsets[b + 1])] - sols[b]).norm()
@@ -587,7 +633,7 @@ def run_pose_graphs(args, rank, world, local, dist, out):
             rr = pgo.implicit_grad_log_radius(g_, th_cpu[p0:p1], v_cpu[p0:p1], om)
             errs_b.append(float((gr.cpu()[e0:e1] - rr).norm() / rr.norm()))
         gerrs.append(max(errs_b))
-    out["accuracy"] = {"max_rel_err_vs_oracle": max(errs), "sampled_problems": sample,
+    out["accuracy"] = {"max_rel_err_vs_oracle": max(errs) if errs else None, "sampled_problems": sample,
                        "tolerance": 1e-9 if precision == "fp64" else 1e-5,
                        "grad_max_rel_err_vs_oracle": max(gerrs) if gerrs else None,
                        "grad_sampled_problems": sample_g,
@@ -609,7 +655,7 @@ def run_pose_graphs(args, rank, world, local, dist, out):
         del s64
     # plain FP64 per-problem GPU path: same kernels, FP64 everywhere, one problem per launch;
     # each problem timed `reps` times with the L2 flushed before each repeat, median per problem
-    nplain, reps = min(8, B), 5
+    nplain, reps = (min(8, B), 5) if not big else (min(2, B), 2)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
     per, spread = [], []
     for b_ in range(nplain):
@@ -661,16 +707,21 @@ def run_pose_graphs(args, rank, world, local, dist, out):
     out["e2e"] = _e2e(run, h_in, h_out, d_in, args.steps, stream, executed)
     # CPU baseline: the oracle as it stands on a bounded sample (one problem per host core)
     ncpu = min(os.cpu_count() or 1, B, 32)
+    if big:
+        out["cpu_baseline"] = {"value": None, "unit": "LM iters/s", "cores": 0, "kind": "oracle",
+                               "sample": "not run: the oracle's dense solve of one problem takes minutes"}
+        return
     out["cpu_baseline"] = _cpu_baseline(name, first, per_rank, list(range(ncpu)), iters, True, algo, bmode,
                                         args.trunc, f"{iters} {algo.upper()} its + {bmode} bwd, FP64 torch CPU")
 
 
 # ----------------------------------------------------------------------------- bundle adjustment
-def ba_launches(iters: int, refine_max: int) -> int:
+def ba_launches(iters: int, refine_max: int, tc: bool = True) -> int:
     """Kernels one bundle-adjustment forward + backward launches (the launch sequence of the
-    library's BA entry points: 6 + 11 per iteration forward, 17 + 8 per PCG step backward; the
-    reduced-system factorization is one cluster launch)."""
-    return 6 + 11 * iters + 17 + 8 * refine_max
+    library's BA entry points).  Tensor-core reduced solver: 6 + 13 per LM iteration forward
+    (linearize, points, cameras, Schur, densify, factor, inverse, CG, update, two evaluations,
+    accept, commit), 18 + 8 per adjoint CG step backward; FP64 block Cholesky: 6 + 11 and 17 + 8."""
+    return (6 + 13 * iters + 18 + 8 * refine_max) if tc else (6 + 11 * iters + 17 + 8 * refine_max)
 
 
 def run_ba(args, rank, world, local, dist, out):
@@ -684,10 +735,13 @@ def run_ba(args, rank, world, local, dist, out):
     b = synth.workload(name, batch=per_rank, first=first)
     st = ba_layer.BAStructure.from_batch(b)
     opts = layer.Options(algo=algo, iters=iters, precision=precision, tau=0.0, lambda0=lam0)
-    solver = ba_layer.BASolver(st, opts, dev)
     t64 = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
     cams0, pts0 = t64(b.cams_init), t64(b.pts_init)
     obs, pm, pw = t64(b.obs_uv), t64(b.prior_meas), t64(b.prior_wdiag)
+    from paper_2207_09442_b300 import autotune
+    tuned = autotune.tune_ba(st, opts, (cams0, pts0, obs, pm, pw), b.focal, b.huber_delta, use_cache=False)
+    opts = layer.Options(**{**opts.__dict__, "cg_ctas": tuned["cg_ctas"]})
+    solver = ba_layer.BASolver(st, opts, dev)
     rng = np.random.default_rng(1234)
     v_c = t64(rng.normal(size=(st.n_cams, 6)) * 1e-2)  # synthetic outer-loss camera gradient
     v_p = torch.zeros(st.n_pts, 3, dtype=torch.float64, device=dev)
@@ -722,7 +776,7 @@ def run_ba(args, rank, world, local, dist, out):
     phase_ms = {k: v[0] / args.steps for k, v in phases.items()}
     C, Pn = int(np.diff(b.cam_offsets)[0]), int(np.diff(b.pt_offsets)[0])
     out.update({
-        "value": executed * world / (ms_per_step * 1e-3), "ms_per_step": ms_per_step,
+        "value": sum_over_ranks(executed, dist, dev) / (ms_per_step * 1e-3), "ms_per_step": ms_per_step,
         "dtype": "mixed: f32 reprojection linearize, f64 Schur/factor/solve/accept/backward",
         "data": "synthetic (seeded generator: ring of cameras, uniform points, 1 px noise)",
         "config": {"workload": name, "problems": b.batch, "cameras": C, "points": Pn,
@@ -736,6 +790,7 @@ def run_ba(args, rank, world, local, dist, out):
         "executed_lm_iterations_per_step": executed,
         "gpu_launches": args.steps * ba_launches(iters, opts.refine_max),
         "reduced_solver": "tensor-core FP32 factor (BF16-split tcgen05 updates) + FP64 CG",
+        "launch_shape": {"cg_ctas": tuned["cg_ctas"]}, "autotune_table": tuned["table"],
         "reduced_cg_steps_per_solve": float(np.sum(fwd_info["refine_steps"]) / max(1, np.sum(fwd_info["factorizations"]))),
         "reduced_cg_resid_max": float(np.max(fwd_info["refine_resid"])),
         "phase_ms_per_step": phase_ms,

@@ -108,6 +108,11 @@ typedef struct {
                               iterations (truncated backpropagation); 0 = all (unrolling) */
   int32_t reduced_solver;  /* bundle adjustment: DNLS_REDUCED_AUTO (0), DNLS_REDUCED_TC or
                               DNLS_REDUCED_FP64; pose graphs ignore it */
+  int32_t cg_ctas;         /* bundle adjustment, tensor-core reduced solver: CTAs per problem of the
+                              forward's conjugate-gradient solve (one thread-block cluster): 0 =
+                              library choice (enough to cover the SMs, >= 32 rows each), else
+                              1, 2, 4 or 8; pose graphs ignore it */
+  int32_t reserved;        /* zero */
 } dnls_solver_opts;
 
 /* Per-problem report (device array of `batch` entries, written by forward/backward). */

@@ -1,4 +1,5 @@
-"""Launch-shape autotuner for the persistent pose-graph kernels.
+"""Launch-shape autotuner for the persistent pose-graph kernels and the bundle-adjustment
+reduced solve.
 
 The numeric work does not depend on the launch shape; only speed does.  The tuner times the
 forward (and backward) of the caller's own batch for each candidate (threads per CTA, resident
@@ -97,3 +98,65 @@ def tune(st: layer.PoseGraphStructure, opts: layer.Options, inputs, v: Optional[
 def apply(opts: layer.Options, tuned: dict) -> layer.Options:
     return layer.Options(**{**opts.__dict__, "threads": tuned["threads"],
                             "ctas_per_sm": tuned["ctas_per_sm"], "smem_factor": tuned["smem_factor"]})
+
+
+# ----------------------------------------------------------------------------- bundle adjustment
+BA_CANDIDATES = [1, 2, 4, 8]  # CTAs per problem of the reduced conjugate-gradient solve
+
+
+def _ba_key(st, opts: layer.Options) -> str:
+    cams = int(max(st.cam_offsets[1:] - st.cam_offsets[:-1]))
+    obs = int(max(st.obs_offsets[1:] - st.obs_offsets[:-1]))
+    bb = int(2 ** math.ceil(math.log2(max(1, st.batch))))
+    ob = int(2 ** math.ceil(math.log2(max(2, obs))))
+    dev = torch.cuda.get_device_properties(torch.cuda.current_device())
+    return (f"ba|{opts.precision}|{opts.reduced_solver}|cams<={cams}|obs<={ob}|B<={bb}|"
+            f"{dev.name}|{dev.multi_processor_count}")
+
+
+def tune_ba(st, opts: layer.Options, inputs, focal: float, huber_delta: float, reps: int = 2,
+            use_cache: bool = True, candidates=None) -> dict:
+    """Launch shape of the bundle-adjustment forward: the CTAs per problem (a thread-block
+    cluster) of the tensor-core path's reduced conjugate-gradient solve.  Times the caller's own
+    batch for each candidate and keeps the fastest; returns {"cg_ctas", "ms", "table"}.
+    ``inputs`` = (cams0, pts0, obs, prior_meas, prior_w) on the device."""
+    from . import ba_layer
+    key = _ba_key(st, opts)
+    cache = _load()
+    if use_cache and key in cache:
+        return cache[key]
+    stream = torch.cuda.current_stream()
+    table = []
+    for kc in (candidates or BA_CANDIDATES):
+        o = layer.Options(**{**opts.__dict__, "cg_ctas": kc})
+        try:
+            sol = ba_layer.BASolver(st, o, inputs[0].device)
+            sol.forward(*inputs, focal, huber_delta)
+            torch.cuda.synchronize()
+            best = float("inf")
+            for _ in range(reps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                sol.forward(*inputs, focal, huber_delta)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                best = min(best, e0.elapsed_time(e1))
+            table.append({"cg_ctas": kc, "ms": best})
+            del sol
+        except _d.DnlsError as err:
+            table.append({"cg_ctas": kc, "ms": None, "error": str(err)})
+            torch.cuda.synchronize()
+    ok = [r for r in table if r["ms"] is not None]
+    if not ok:
+        raise RuntimeError(f"no bundle-adjustment launch shape ran: {table}")
+    win = min(ok, key=lambda r: r["ms"])
+    out = {"cg_ctas": win["cg_ctas"], "ms": win["ms"], "table": table,
+           "tuned_at": time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime())}
+    cache[key] = out
+    try:
+        with open(CACHE, "w") as f:
+            json.dump(cache, f, indent=1, sort_keys=True)
+    except OSError:
+        pass
+    return out

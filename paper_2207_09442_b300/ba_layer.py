@@ -22,6 +22,7 @@ class BAStructure:
                       np.ascontiguousarray(obs_pt, np.int32), np.ascontiguousarray(prior_offsets, np.int64),
                       np.ascontiguousarray(prior_cam, np.int32)]
         k = self._keep
+        self.cam_offsets, self.obs_offsets = k[0], k[2]
         self.batch = len(k[0]) - 1
         self.n_cams, self.n_pts, self.n_obs, self.n_priors = int(k[0][-1]), int(k[1][-1]), int(k[2][-1]), int(k[5][-1])
         desc = _d.BADesc(self.batch, *[a.ctypes.data for a in k])

@@ -88,7 +88,7 @@ struct BAArgs {
   double *solc, *solp, *zc, *zp, *hc, *hp;
   BAState* st;
   // options
-  int algo, mixed, iters, tc;
+  int algo, mixed, iters, tc, cg_ctas;
   double lam0, tau, refine_tol;
   const double* v_cams;
   const double* v_pts;
@@ -1429,6 +1429,8 @@ dnls_status ba_check_opts(const dnls_solver_opts* o) {
   if (o->precision != DNLS_FP64 && o->precision != DNLS_MIXED_FP32) return DNLS_ERR_ARG;
   if (!(o->lambda0 >= 0.0) || !(o->tau >= 0.0)) return DNLS_ERR_ARG;
   if (o->reduced_solver < DNLS_REDUCED_AUTO || o->reduced_solver > DNLS_REDUCED_FP64) return DNLS_ERR_ARG;
+  if (o->cg_ctas != 0 && o->cg_ctas != 1 && o->cg_ctas != 2 && o->cg_ctas != 4 && o->cg_ctas != 8)
+    return DNLS_ERR_ARG;
   return DNLS_OK;
 }
 
@@ -1474,6 +1476,7 @@ BAArgs ba_args(const dnls_ba* h, const dnls_solver_opts* o, const dnls_ba_inputs
   a.hp = (double*)(w + H.w_hp);
   a.algo = o->algo;
   a.tc = H.tc_ok && o->reduced_solver != DNLS_REDUCED_FP64;
+  a.cg_ctas = o->cg_ctas;
   a.mixed = o->precision == DNLS_MIXED_FP32;
   a.iters = o->iters;
   a.lam0 = o->lambda0;
@@ -1531,9 +1534,11 @@ tc::Batch tc_batch(const BAHost& H, const BAArgs& a) {
   return tb;
 }
 
-// CTAs per problem of the reduced CG solve: enough to cover the SMs, at least 32 rows each
-int tc_cluster(const BAHandle& G, int steps) {
+// CTAs per problem of the reduced CG solve: the caller's choice, else enough to cover the SMs,
+// at least 32 rows each
+int tc_cluster(const BAHandle& G, int steps, int requested) {
   if (steps <= 0) return 1;
+  if (requested > 0) return requested;
   int kc = 1;
   while (kc < tc::kMaxCluster && (int64_t)G.h.B * kc * 2 <= G.sms && G.h.tc_np_max / (kc * 2) >= 32) kc *= 2;
   return kc;
@@ -1571,7 +1576,7 @@ void ba_eliminate_and_factor(const dnls_ba* h, BAArgs& a, cudaStream_t st, doubl
       const int steps = kInnerMax;
       pt.mark(DNLS_BA_PHASE_SOLVE);
       tc::launch_pcg(tb, BAIO{a.d, a.bc, a.dc, a.st, 1}, steps, a.mixed ? kInnerTolMixed : kInnerTolFP64,
-                     tc_cluster(h->impl, steps), st);
+                     tc_cluster(h->impl, steps, a.cg_ctas), st);
     }
     return;
   }

@@ -32,7 +32,8 @@ class SolverOpts(ctypes.Structure):
                 ("backward_mode", c_int32), ("refine_max", c_int32), ("threads", c_int32),
                 ("ctas_per_sm", c_int32), ("smem_factor", c_int32), ("lambda0", c_double),
                 ("tau", c_double), ("refine_tol", c_double), ("dlm_eps", c_double), ("radius0", c_double),
-                ("trunc_steps", c_int32), ("reduced_solver", c_int32)]
+                ("trunc_steps", c_int32), ("reduced_solver", c_int32),
+                ("cg_ctas", c_int32), ("reserved", c_int32)]
 
 
 class GraphDesc(ctypes.Structure):

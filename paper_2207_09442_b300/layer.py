@@ -36,6 +36,7 @@ class Options:
     radius0: float = 1.0             # algo "dogleg": initial trust radius
     trunc_steps: int = 0             # backward_mode "unroll": last k iterations only (0 = all)
     reduced_solver: str = "auto"     # bundle adjustment: "auto" | "tc" | "fp64"
+    cg_ctas: int = 0                 # bundle adjustment: CTAs per problem of the reduced CG (0 = library)
 
     def c(self) -> _d.SolverOpts:
         fp64 = self.precision == "fp64"
@@ -65,6 +66,7 @@ class Options:
         if self.reduced_solver not in solvers:
             raise ValueError(f"unknown reduced_solver {self.reduced_solver!r}")
         o.reduced_solver = solvers[self.reduced_solver]
+        o.cg_ctas = int(self.cg_ctas)
         return o
 
 

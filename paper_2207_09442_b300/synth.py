@@ -15,6 +15,8 @@ models; their exact generators are not given, so the recipes below are this proj
   pgo_se3_implicit_b256  256 SE(3) graphs, 64 poses, chain + 16 loop closures, log-weights
   pgo_se3_uneven_b1024   1024 SE(3) graphs, 16..256 poses, floor(N/4) loop closures
   ba_b32        32 bundle-adjustment problems, 64 cameras on a 10 m ring, 4096 points
+  pgo_se3_p2048_b256 / pgo_se3_p4096_b64   256 x 2048-pose / 64 x 4096-pose SE(3) graphs,
+                loop closures 25 % of the poses, 10 LM iterations (mixed)
 
 Seeds: ``numpy.random.Generator(PCG64(SeedSequence([config_id, b])))`` per problem ``b``.
 
@@ -351,6 +353,10 @@ def workload(name: str, batch: Optional[int] = None, **kw):
                        radius=0.03, **kw)
     if name == "ba_b32":
         return ba(batch=batch or 32, **kw)
+    if name == "pgo_se3_p2048_b256":
+        return pgo_se3(batch=batch or 256, n_poses=2048, n_lc=512, config_id=7, **kw)
+    if name == "pgo_se3_p4096_b64":
+        return pgo_se3(batch=batch or 64, n_poses=4096, n_lc=1024, config_id=8, **kw)
     raise KeyError(name)
 
 
@@ -362,5 +368,8 @@ WORKLOADS = {
     "pgo_se3_uneven_b1024": ("lm", 15, "mixed_fp32", 1e-3),
     "pgo_se3_robust_b256": ("lm", 20, "mixed_fp32", 1e-3),
     "ba_b32": ("lm", 10, "mixed_fp32", 1e-3),
+    # large graphs (the scale of the paper's scalability study, App. F: 10 inner iterations)
+    "pgo_se3_p2048_b256": ("lm", 10, "mixed_fp32", 1e-3),
+    "pgo_se3_p4096_b64": ("lm", 10, "mixed_fp32", 1e-3),
 }
 

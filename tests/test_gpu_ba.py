@@ -192,3 +192,23 @@ def test_ba_phase_timers_cover_the_step():
     assert 5 <= ph["schur"][1] <= 6  # five LM iterations and at most one backward refactorization
     total = sum(v[0] for v in ph.values())
     assert 0.5 * wall < total <= wall * 1.001 + 0.05, (total, wall)
+
+
+def test_ba_autotuner_returns_a_runnable_shape_and_shapes_agree():
+    """The bundle-adjustment tuner times every CTA count of the reduced CG solve; the numeric
+    work does not depend on it (only the order of the cluster's partial sums does)."""
+    from paper_2207_09442_b300 import autotune, ba_layer, layer
+    b = synth.ba(batch=3, n_cams=12, n_pts=80, config_id=64)
+    st = ba_layer.BAStructure.from_batch(b)
+    opts = layer.Options(algo="lm", iters=6, precision="fp64", reduced_solver="tc")
+    inp = _ba_inputs(b)
+    tuned = autotune.tune_ba(st, opts, inp, b.focal, b.huber_delta, use_cache=False)
+    assert tuned["cg_ctas"] in (1, 2, 4, 8)
+    assert all(r["ms"] is not None for r in tuned["table"])
+    sols = []
+    for kc in (1, 2, 4, 8):
+        sol = ba_layer.BASolver(st, layer.Options(**{**opts.__dict__, "cg_ctas": kc}))
+        sols.append(sol.forward(*inp, b.focal, b.huber_delta))
+    torch.cuda.synchronize()
+    for c, p in sols[1:]:
+        assert rel(c, sols[0][0]) < 1e-11 and rel(p, sols[0][1]) < 1e-11

@@ -73,6 +73,28 @@ def test_large_single_problem():
     assert sol.info_dict()["status"][0] == 0
 
 
+def test_large_se3_problem_1024_poses():
+    """One 1024-pose SE(3) graph with 256 loop closures (the scale of the paper's scalability
+    study, App. F): 6144 unknowns, a deep elimination tree with heavy fill from the random loop
+    closures.  FP64 forward and implicit measurement gradients against the oracle's dense solve,
+    with the conditioning-based tolerance of the 1000-pose case above."""
+    b = synth.pgo_se3(batch=1, n_poses=1024, n_lc=256, config_id=154)
+    opts = layer.Options(algo="lm", iters=10, precision="fp64", tau=0.0)
+    sol, theta, (meas, wd, lw) = run_forward(b, opts)
+    st = layer.PoseGraphStructure.from_batch(b).stats()
+    assert st["n_levels_max"] > 30
+    assert st["factor_flops"] < st["dense_flops"] / 100  # block-sparse, far below dense
+    g, ref, _ = oracle_solve(b, 0, opts)
+    assert rel(poses_of(b, theta, 0), ref) < 1e-7
+    th = poses_of(b, theta, 0)
+    v = pgo.tangent_grad(3, lambda X: pgo.pose_error_loss(3, X, g.theta_gt), th)
+    gm, gl = sol.backward(theta, v.to(DEV), meas, wd, lw)
+    torch.cuda.synchronize()
+    rm, rl, _ = pgo.implicit_grads(g, th, v, "exact")
+    assert rel(edges_of(b, gm, 0), rm) < 1e-6
+    assert sol.info_dict()["status"][0] == 0
+
+
 def test_pure_chain_graph_every_level_one_column():
     """Odometry chains without loop closures: the elimination tree is a path, every level holds
     one column, and the whole factor is the top chain (its forward-solve pre-pass has no pairs
