@@ -47,7 +47,7 @@ METRIC = "batched LM iters/s (fwd + implicit bwd) vs plain FP64 GPU path at 1e-5
 # while the sources still hash to the captured build; null otherwise.
 FORWARD_SOURCES = ["dnls_graph.cu", "dnls_blockchol.cuh", "dnls_cost.cuh", "dnls_lie.cuh",
                    "dnls_graph.h", "dnls_symbolic.cpp"]
-CAPTURED_TRAFFIC = {"pgo_se3_b256": ("e490dcb270193919", (4.644096e6 + 1.865984e6) * 256 / 64)}
+CAPTURED_TRAFFIC = {"pgo_se3_b256": ("de7dc412ff9b3917", (4.636928e6 + 1.759488e6) * 256 / 64)}
 
 
 def forward_sources_sha() -> str:
@@ -90,7 +90,8 @@ def _args():
                     help="pose graphs: weak = every rank solves its own full batch; strong = one "
                          "batch split over the ranks, balanced by per-problem factorization flops")
     ap.add_argument("--shape", default="",
-                    help="threads,ctas_per_sm,smem_factor: fixed launch shape instead of autotuning")
+                    help="fixed launch shape instead of autotuning: pose graphs threads,ctas_per_sm,"
+                         "smem_factor; bundle adjustment the reduced CG's CTAs per problem")
     return ap.parse_args()
 
 
@@ -739,7 +740,10 @@ def run_ba(args, rank, world, local, dist, out):
     cams0, pts0 = t64(b.cams_init), t64(b.pts_init)
     obs, pm, pw = t64(b.obs_uv), t64(b.prior_meas), t64(b.prior_wdiag)
     from paper_2207_09442_b300 import autotune
-    tuned = autotune.tune_ba(st, opts, (cams0, pts0, obs, pm, pw), b.focal, b.huber_delta, use_cache=False)
+    if args.shape:
+        tuned = {"cg_ctas": int(args.shape), "table": "fixed by --shape"}
+    else:
+        tuned = autotune.tune_ba(st, opts, (cams0, pts0, obs, pm, pw), b.focal, b.huber_delta, use_cache=False)
     opts = layer.Options(**{**opts.__dict__, "cg_ctas": tuned["cg_ctas"]})
     solver = ba_layer.BASolver(st, opts, dev)
     rng = np.random.default_rng(1234)
