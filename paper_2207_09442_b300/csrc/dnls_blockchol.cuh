@@ -19,6 +19,12 @@ __device__ __forceinline__ double lane_sum(double v, int lanes) {
   for (int o = 1; o < lanes; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+__device__ __forceinline__ float lane_sum(float v, int lanes) {
+  for (int o = 1; o < lanes; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
 
 // ----------------------------------------------------------------------------- helpers
 __device__ __forceinline__ double block_sum(double v, double* red) {
@@ -329,11 +335,13 @@ __device__ bool block_factor_cluster(F& p, double lam, int rank, int nranks, int
 // In place: x <- (L L^T)^-1 x (positions order, FP64), level by level.  kTopChain = false leaves
 // out the top chain's pre-pass (the same result up to summation order, less code: used where
 // registers are scarce).
-template <int D, bool kTopChain = true, class F>
-__device__ void block_solve(F& p, double* x) {
+// Forward and back substitution with the block factor, in the scalar type T of the given
+// factor copy (L, Linv: blocks as in p.L / p.Linv) and vectors (x: right-hand side in, solution
+// out; tmp: scratch of the same length).
+template <int D, bool kTopChain, class T, class F>
+__device__ void block_solve_t(F& p, const T* L, const T* Linv, T* x, T* tmp) {
   const int chain_lev = kTopChain ? p.chain_lev : p.nlev;
   constexpr int BS = D * D;
-  const double* L = p.L;
   for (int lv = 0; lv < p.nlev; ++lv) {
     const int c0 = p.lvlptr[lv], c1 = p.lvlptr[lv + 1];
     // Rows of the top chain (levels chain_lev.., one column each): their pairs from columns
@@ -346,21 +354,21 @@ __device__ void block_solve(F& p, double* x) {
       const int n1 = (p.nlev - lv) * D * LN;
       for (int base = 0; base < n1; base += blockDim.x) {
         const int it = base + threadIdx.x;
-        double acc = 0.0;
+        T acc = T(0);
         int k = 0, i = 0;
         if (it < n1) {
           const int e2 = it >> lsh, lane = it & (LN - 1);
           k = p.lvlcols[c0 + e2 / D];
           i = e2 % D;
           for (int q = p.rowptr[k] + lane; q < p.rsplit[k]; q += LN) {
-            const double* B = L + (int64_t)p.rowent[2 * q] * BS + i * D;
-            const double* y = x + p.rowent[2 * q + 1] * D;
+            const T* B = L + (int64_t)p.rowent[2 * q] * BS + i * D;
+            const T* y = x + p.rowent[2 * q + 1] * D;
 #pragma unroll
-            for (int mm = 0; mm < D; ++mm) acc = fma(B[mm], y[mm], acc);
+            for (int mm = 0; mm < D; ++mm) acc = fma_t(B[mm], y[mm], acc);
           }
         }
         if (LN > 1) acc = lane_sum(acc, LN);
-        if (it < n1 && (it & (LN - 1)) == 0) p.tmp[k * D + i] = x[k * D + i] - acc;
+        if (it < n1 && (it & (LN - 1)) == 0) tmp[k * D + i] = x[k * D + i] - acc;
       }
       __syncthreads();
     }
@@ -368,30 +376,30 @@ __device__ void block_solve(F& p, double* x) {
     const int n1 = (c1 - c0) * D * LN;
     for (int base = 0; base < n1; base += blockDim.x) {
       const int it = base + threadIdx.x;
-      double acc = 0.0;
+      T acc = T(0);
       int k = 0, i = 0;
       if (it < n1) {
         const int e2 = it >> lsh, lane = it & (LN - 1);
         k = p.lvlcols[c0 + e2 / D];
         i = e2 % D;
         for (int q = (chain ? p.rsplit[k] : p.rowptr[k]) + lane; q < p.rowptr[k + 1]; q += LN) {
-          const double* B = L + (int64_t)p.rowent[2 * q] * BS + i * D;
-          const double* y = x + p.rowent[2 * q + 1] * D;
+          const T* B = L + (int64_t)p.rowent[2 * q] * BS + i * D;
+          const T* y = x + p.rowent[2 * q + 1] * D;
 #pragma unroll
-          for (int mm = 0; mm < D; ++mm) acc = fma(B[mm], y[mm], acc);
+          for (int mm = 0; mm < D; ++mm) acc = fma_t(B[mm], y[mm], acc);
         }
       }
       if (LN > 1) acc = lane_sum(acc, LN);
-      if (it < n1 && (it & (LN - 1)) == 0) p.tmp[k * D + i] = (chain ? p.tmp[k * D + i] : x[k * D + i]) - acc;
+      if (it < n1 && (it & (LN - 1)) == 0) tmp[k * D + i] = (chain ? tmp[k * D + i] : x[k * D + i]) - acc;
     }
     __syncthreads();
     for (int it = threadIdx.x; it < (c1 - c0) * D; it += blockDim.x) {
       const int k = p.lvlcols[c0 + it / D], i = it % D;
-      const double* I = p.Linv + (int64_t)k * BS + i * D;
-      double s = 0.0;
+      const T* I = Linv + (int64_t)k * BS + i * D;
+      T s = T(0);
 #pragma unroll
       for (int mm = 0; mm < D; ++mm)
-        if (mm <= i) s = fma(I[mm], p.tmp[k * D + mm], s);
+        if (mm <= i) s = fma_t(I[mm], tmp[k * D + mm], s);
       x[k * D + i] = s;
     }
     __syncthreads();
@@ -402,7 +410,7 @@ __device__ void block_solve(F& p, double* x) {
     const int n1 = (c1 - c0) * D * LN;
     for (int base = 0; base < n1; base += blockDim.x) {
       const int it = base + threadIdx.x;
-      double acc = 0.0;
+      T acc = T(0);
       int k = 0, i = 0;
       if (it < n1) {
         const int e2 = it >> lsh, lane = it & (LN - 1);
@@ -411,27 +419,32 @@ __device__ void block_solve(F& p, double* x) {
         const int basec = p.colptr[k];
         const int cnt = p.colptr[k + 1] - basec;
         for (int aa = lane; aa < cnt; aa += LN) {
-          const double* B = L + (int64_t)(p.N + basec + aa) * BS + i;
-          const double* y = x + p.rows[basec + aa] * D;
+          const T* B = L + (int64_t)(p.N + basec + aa) * BS + i;
+          const T* y = x + p.rows[basec + aa] * D;
 #pragma unroll
-          for (int mm = 0; mm < D; ++mm) acc = fma(B[mm * D], y[mm], acc);
+          for (int mm = 0; mm < D; ++mm) acc = fma_t(B[mm * D], y[mm], acc);
         }
       }
       if (LN > 1) acc = lane_sum(acc, LN);
-      if (it < n1 && (it & (LN - 1)) == 0) p.tmp[k * D + i] = x[k * D + i] - acc;
+      if (it < n1 && (it & (LN - 1)) == 0) tmp[k * D + i] = x[k * D + i] - acc;
     }
     __syncthreads();
     for (int it = threadIdx.x; it < (c1 - c0) * D; it += blockDim.x) {
       const int k = p.lvlcols[c0 + it / D], i = it % D;
-      const double* I = p.Linv + (int64_t)k * BS;
-      double s = 0.0;
+      const T* I = Linv + (int64_t)k * BS;
+      T s = T(0);
 #pragma unroll
       for (int mm = 0; mm < D; ++mm)
-        if (mm >= i) s = fma(I[mm * D + i], p.tmp[k * D + mm], s);
+        if (mm >= i) s = fma_t(I[mm * D + i], tmp[k * D + mm], s);
       x[k * D + i] = s;
     }
     __syncthreads();
   }
+}
+
+template <int D, bool kTopChain = true, class F>
+__device__ void block_solve(F& p, double* x) {
+  block_solve_t<D, kTopChain, double>(p, p.L, p.Linv, x, p.tmp);
 }
 
 

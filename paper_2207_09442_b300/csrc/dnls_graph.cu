@@ -19,6 +19,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <type_traits>
 
 #include "../../include/dnls.h"
 #include "dnls_blockchol.cuh"
@@ -78,6 +79,7 @@ struct Prob {
   const double* logrc;  // per-cost log Welsch radius (null: plain squares)
   double* theta;
   double *H, *L, *Lg, *Linv, *g, *dx, *tmp, *thc, *bx, *bv, *br, *bhx, *ebuf, *W;
+  float *Lf, *Linvf;  // FP32 copies of the factor for the mixed-path forward solves
   void* J;
   ProbState* st;
   const ProbMeta* m;
@@ -125,6 +127,8 @@ struct Prob {
     ebuf = (double*)(w + m->w_ebuf);
     st = (ProbState*)(w + m->w_state);
     W = (double*)(w + m->w_W);
+    Lf = (float*)(w + m->w_Lf);
+    Linvf = (float*)(w + m->w_Linvf);
     const int32_t* s = gsym;
     stage = 0;
     if (smem) {
@@ -456,9 +460,25 @@ __device__ void forward_problem(const KArgs& a, int b, char* smem, double* red, 
       lam = fmin(lam * 10.0, kLamMax);
       continue;
     }
-    for (int k = threadIdx.x; k < n; k += blockDim.x) p.dx[k] = -p.g[k];
-    __syncthreads();
-    chol_solve<KIND>(p, p.dx);
+    if (std::is_same<P, float>::value && !a.rec) {
+      // mixed path: the LM step solved with an FP32 copy of the FP64 factor (H itself was
+      // assembled in FP32, so the step keeps its accuracy class; the fixed point, g = 0 in FP64
+      // sums, is unchanged); FP32 instructions keep the level chains short.  A forward that
+      // records its steps for the unrolled backward solves in FP64, as that backward assumes.
+      const int nb = (p.N + p.nnzL) * D * D;
+      for (int k = threadIdx.x; k < nb; k += blockDim.x) p.Lf[k] = (float)p.L[k];
+      for (int k = threadIdx.x; k < p.N * D * D; k += blockDim.x) p.Linvf[k] = (float)p.Linv[k];
+      float* xf = (float*)p.bx;  // the backward's vector, free during the forward: x, then tmp
+      for (int k = threadIdx.x; k < n; k += blockDim.x) xf[k] = (float)(-p.g[k]);
+      __syncthreads();
+      block_solve_t<D, true, float>(p, p.Lf, p.Linvf, xf, xf + n);
+      for (int k = threadIdx.x; k < n; k += blockDim.x) p.dx[k] = (double)xf[k];
+      __syncthreads();
+    } else {
+      for (int k = threadIdx.x; k < n; k += blockDim.x) p.dx[k] = -p.g[k];
+      __syncthreads();
+      chol_solve<KIND>(p, p.dx);
+    }
     if (a.rec) {
       double* rdel = rv.del + (int64_t)it * a.rec_nmax * D;
       for (int k = threadIdx.x; k < n; k += blockDim.x) rdel[k] = p.dx[k];

@@ -43,6 +43,8 @@ struct ProbMeta {
   int32_t w_H, w_L, w_Linv;    // workspace byte offsets
   int32_t w_g, w_dx, w_tmp, w_thc, w_J;
   int32_t w_bx, w_bv, w_br, w_bhx, w_ebuf, w_state, w_W;
+  int32_t w_Lf, w_Linvf;       // FP32 copies of L and the inverted diagonal blocks (mixed-path
+                               // forward solves)
   int32_t L_bytes;             // bytes of this problem's factor storage
   int32_t blob_len;            // int32 count of this problem's symbolic data
   int32_t arena_bytes;         // shared memory to stage blob + L + L^-1 + two solve vectors

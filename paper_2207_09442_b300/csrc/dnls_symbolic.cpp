@@ -457,6 +457,8 @@ int build_graph_host(int kind, int B, const int64_t* pose_offsets, const int64_t
     m.w_ebuf = take((int64_t)E * 4 * D * 8);
     m.w_state = take(64);
     m.w_W = take((int64_t)E * D * 8);
+    m.w_Lf = take((int64_t)(N + nnzL) * BS * 4);
+    m.w_Linvf = take((int64_t)N * BS * 4);
     {
       auto a16 = [](int64_t x) { return (x + 15) & ~(int64_t)15; };
       const int64_t arena = a16((int64_t)m.blob_len * 4) + a16(m.L_bytes) + a16((int64_t)N * BS * 8) +
