@@ -376,11 +376,22 @@ dnls_status dnls_dense_spd_solve(int32_t batch, int32_t n, const double* A, cons
 
 /* Sizes of the symbolic factorization (host values; for reports and tests). */
 typedef struct {
-  int64_t n_poses, n_costs, n_blocks_L, n_block_updates, n_levels_max;
-  double factor_flops;   /* FP64 flops of one numeric factorization of the whole batch */
+  int64_t n_poses, n_costs;
+  int64_t n_blocks_L;       /* stored factor blocks (a dense supernode's explicit zeros included) */
+  int64_t n_block_updates;  /* algorithmic block products of one factorization (no explicit zeros) */
+  int64_t n_levels_max;
+  double factor_flops;   /* FP64 flops of one numeric factorization of the whole batch
+                            (algorithmic: the structure before supernode amalgamation) */
   double dense_flops;    /* flops an n^3/3 dense Cholesky would take on the same batch */
+  int64_t supernode_cols_max;  /* block columns of the largest dense supernode (the top of the
+                                  elimination tree amalgamated and factored right-looking; App. E's
+                                  supernodal Cholesky), 0 if no problem has one */
+  int64_t n_supernodes;        /* problems with a dense supernode */
 } dnls_graph_stats;
 dnls_status dnls_graph_get_stats(const dnls_graph* g, dnls_graph_stats* out);
+/* The same sizes from the symbolic analysis alone (host only: no device, no handle).  Errors as
+ * dnls_graph_create's argument checks. */
+dnls_status dnls_graph_analyze(const dnls_graph_desc* desc, dnls_graph_stats* out);
 
 /* FP64 flops of one numeric block Cholesky factorization of each problem (from the symbolic
  * structure; the same count dnls_graph_stats.factor_flops sums), written to the host array

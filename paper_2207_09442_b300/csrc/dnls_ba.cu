@@ -99,7 +99,7 @@ struct BAArgs {
 
 // view of one problem's reduced system for block_factor / block_solve
 struct RedView {
-  int N, nnzL, nlev, chain_lev;
+  int N, nnzL, nlev, chain_lev, dense_lev;
   const int32_t *perm, *iperm, *colptr, *rows, *rowptr, *rowent, *lvlptr, *lvlcols, *tgtptr, *tgt,
       *gptr, *gsrc, *panptr, *pan, *lsrc, *glanes, *slanes, *gsplit, *rsplit;
   double *H, *L, *Linv, *dx, *tmp;
@@ -109,6 +109,7 @@ struct RedView {
     nnzL = m->nnzL;
     nlev = m->nlev;
     chain_lev = m->chain_lev;
+    dense_lev = m->dense_lev;
     const int32_t* s = a.d.rsym + m->sym;
     perm = s + m->o_perm;
     iperm = s + m->o_iperm;
@@ -1264,7 +1265,8 @@ int build_ba_host(const dnls_ba_desc* desc, BAHost& H) {
     red_ej.push_back(-1);
   }
   int rc = build_graph_host(DNLS_SE3, B, H.cam_off.data(), red_edge_off.data(), red_ei.data(),
-                            red_ej.data(), DNLS_ORDER_MIN_DEGREE, &H.red, kRedCluster * 256);
+                            red_ej.data(), DNLS_ORDER_MIN_DEGREE, &H.red, kRedCluster * 256,
+                            /*dense_chain=*/false);
   if (rc != DNLS_OK) return rc;
   H.red_chain = true;
   for (const ProbMeta& m : H.red.meta) {

@@ -1,9 +1,9 @@
 // Level-scheduled, left-looking block Cholesky of a block-sparse SPD matrix and the matching
 // triangular solves, run by one CTA or by the CTAs of a thread-block cluster (Sec. 4.2's sparse
 // Cholesky with a symbolic factorization computed once per structure).  The view type F supplies
-// the symbolic structure and buffers (fields N, nnzL, nlev, chain_lev, H, L, Linv, tmp, lsrc,
-// tgtptr, tgt, gptr, gsrc, gsplit, lvlptr, lvlcols, panptr, pan, rowptr, rowent, rsplit, colptr,
-// rows, glanes, slanes; see ProbMeta in dnls_graph.h for their meaning).
+// the symbolic structure and buffers (fields N, nnzL, nlev, chain_lev, dense_lev, H, L, Linv,
+// tmp, lsrc, tgtptr, tgt, gptr, gsrc, gsplit, lvlptr, lvlcols, panptr, pan, rowptr, rowent,
+// rsplit, colptr, rows, glanes, slanes; see ProbMeta in dnls_graph.h for their meaning).
 // Every output element is produced by one thread in a fixed order: no atomics, bitwise
 // reproducible results.
 #pragma once
@@ -151,16 +151,16 @@ __device__ __forceinline__ void panel_subst(F& p, double* L, int lv, int tid, in
   }
 }
 
-// Subtracts from each target block of level lv the products of its source pairs: mode 0 all
-// pairs, 1 the early ones (gptr .. gsplit), 2 the late ones (gsplit .. next gptr).  Each output
-// element is summed by LN = glanes[lv] adjacent lanes and combined by a fixed-order shuffle
-// reduction.  Runs on the team threads tid = 0 .. nthr-1 (whole warps: tid and nthr advance
-// warp by warp, so every warp taking part is whole).
+// Subtracts from each target block t0 .. t1-1 (of the target list) the products of its source
+// pairs: mode 0 all pairs, 1 the early ones (gptr .. gsplit), 2 the late ones (gsplit .. next
+// gptr).  Each output element is summed by LN adjacent lanes (a power of two) and combined by a
+// fixed-order shuffle reduction.  Runs on the team threads tid = 0 .. nthr-1 (whole warps: tid
+// and nthr advance warp by warp, so every warp taking part is whole).
 template <int D, class F>
-__device__ __forceinline__ void gather_level(F& p, double* L, int lv, int mode, int tid, int nthr) {
+__device__ __forceinline__ void gather_targets(F& p, double* L, int t0, int t1, int LN, int mode,
+                                               int tid, int nthr) {
   constexpr int BS = D * D;
-  const int t0 = p.tgtptr[lv], t1 = p.tgtptr[lv + 1];
-  const int LN = p.glanes[lv], lsh = __ffs(LN) - 1;  // LN is a power of two
+  const int lsh = __ffs(LN) - 1;
   const int n1 = (t1 - t0) * BS * LN;
   for (int base = 0; base < n1; base += nthr) {
     const int it = base + tid;
@@ -183,6 +183,12 @@ __device__ __forceinline__ void gather_level(F& p, double* L, int lv, int mode, 
     if (LN > 1) acc = lane_sum(acc, LN);
     if (it < n1 && (it & (LN - 1)) == 0 && s1 > s0) L[(int64_t)p.tgt[q] * BS + el] -= acc;
   }
+}
+
+// The targets of level lv, LN = glanes[lv].
+template <int D, class F>
+__device__ __forceinline__ void gather_level(F& p, double* L, int lv, int mode, int tid, int nthr) {
+  gather_targets<D>(p, L, p.tgtptr[lv], p.tgtptr[lv + 1], p.glanes[lv], mode, tid, nthr);
 }
 
 // L <- H (fill-in blocks zero) by the team threads tid = 0 .. nthr-1.  Each thread first fetches
@@ -230,8 +236,67 @@ __device__ __forceinline__ void damp_diagonal(F& p, double* L, double lam, doubl
   }
 }
 
+// The dense supernode (levels dense_lev .. nlev-1: one block column each, every block of its
+// lower triangle stored), factored right-looking once the sparse levels are final: (1) every
+// supernode block minus its products with sparse columns, one gather over all its targets;
+// then for each supernode column i: (2) its diagonal block factored by warp 0, (3) its
+// off-diagonal blocks L(r,i) by substitution, (4) every trailing block (r, s), i < s <= r,
+// minus L(r,i) L(s,i)^T, one block row (D outputs, D^2 FMAs from registers) per thread.  The
+// products are those of the level schedule, summed column by column.  Returns false (uniformly)
+// on a pivot that is not positive and finite, after writing `gen` into *sflag.
+template <int D, class F>
+__device__ bool dense_supernode(F& p, double* L, int* sflag, int gen) {
+  constexpr int BS = D * D;
+  const int d0 = p.dense_lev, m = p.nlev - d0;
+  gather_targets<D>(p, L, p.tgtptr[d0], p.tgtptr[p.nlev], p.glanes[p.nlev], 1, threadIdx.x,
+                    blockDim.x);
+  __syncthreads();
+  for (int i = 0; i < m; ++i) {
+    const int c0 = p.lvlptr[d0 + i];
+    if (threadIdx.x < 32) diag_rows_factor<D>(p, L, c0, c0 + 1, sflag, gen);
+    __syncthreads();
+    if (*sflag == gen) return false;
+    panel_subst<D>(p, L, d0 + i, threadIdx.x, blockDim.x);
+    __syncthreads();
+    const int M = m - 1 - i;  // trailing supernode columns
+    if (M == 0) break;
+    // column i's off-diagonal blocks, rows i+1 .. m-1 of the supernode in order
+    const double* P = L + (int64_t)(p.N + p.colptr[p.lvlcols[c0]]) * BS;
+    // trailing blocks in column-major order: column s' (supernode column i+1+s') holds rows
+    // r' = s' .. M-1 and starts at first(s') = s' M - s' (s' - 1) / 2.  T D fits in int32: the
+    // whole factor of one problem is below 2^31 bytes.
+    const int T = M * (M + 1) / 2;
+    const int twoM1 = 2 * M + 1;
+    for (int it = threadIdx.x; it < T * D; it += blockDim.x) {
+      const int q = it / D, a = it - q * D;
+      int sc = (int)(0.5f * ((float)twoM1 - sqrtf((float)(twoM1 * twoM1 - 8 * q))));
+      sc = max(0, min(sc, M - 1));
+      while (sc > 0 && sc * M - sc * (sc - 1) / 2 > q) --sc;
+      while (sc + 1 < M && (sc + 1) * M - (sc + 1) * sc / 2 <= q) ++sc;
+      const int rc = sc + q - (sc * M - sc * (sc - 1) / 2);
+      const int ks = p.lvlcols[p.lvlptr[d0 + i + 1 + sc]];
+      double* A = L + (int64_t)(rc == sc ? ks : p.N + p.colptr[ks] + (rc - sc - 1)) * BS + a * D;
+      const double* Lr = P + (int64_t)rc * BS + a * D;
+      const double* Ls = P + (int64_t)sc * BS;
+      double x[D];
+#pragma unroll
+      for (int mm = 0; mm < D; ++mm) x[mm] = Lr[mm];
+#pragma unroll
+      for (int b = 0; b < D; ++b) {
+        double acc = A[b];
+#pragma unroll
+        for (int mm = 0; mm < D; ++mm) acc = fma(-x[mm], Ls[b * D + mm], acc);
+        A[b] = acc;
+      }
+    }
+    __syncthreads();
+  }
+  return true;
+}
+
 // L <- H + lam * diag(max(diag H, floor)) + shift * I, then left-looking block Cholesky level
-// by level, and finally the inverses of the diagonal blocks (used by the solves only).
+// by level (the dense supernode, if any, right-looking after the sparse levels), and finally
+// the inverses of the diagonal blocks (used by the solves only).
 // Returns false (uniformly across the CTA) if a pivot is not positive or not finite.  A failing
 // thread writes the call's generation number `gen` into *sflag; the flag is never reset, so a
 // slow thread can never see a later call's state.
@@ -250,16 +315,17 @@ __device__ bool block_factor(F& p, double lam, int* sflag, int gen, double shift
   // final); that level's gather then only adds the pairs from the level just factored.  On a
   // wide level every warp factors CPW diagonal blocks at a time.
   bool early_done = false;
-  for (int lv = 0; lv < p.nlev; ++lv) {
+  const int nsparse = p.dense_lev;  // levels of the level schedule
+  for (int lv = 0; lv < nsparse; ++lv) {
     gather_level<D>(p, L, lv, early_done ? 2 : 0, threadIdx.x, blockDim.x);
     __syncthreads();
     const int c0 = p.lvlptr[lv], c1 = p.lvlptr[lv + 1];
     if (c1 - c0 <= CPW && nwarps >= 2) {
       if (warp == 0)
         diag_rows_factor<D>(p, L, c0, c1, sflag, gen);
-      else if (lv + 1 < p.nlev)
+      else if (lv + 1 < nsparse)
         gather_level<D>(p, L, lv + 1, 1, threadIdx.x - 32, blockDim.x - 32);
-      early_done = lv + 1 < p.nlev;
+      early_done = lv + 1 < nsparse;
     } else {
       for (int cc = c0 + warp * CPW; cc < c1; cc += nwarps * CPW)
         diag_rows_factor<D>(p, L, cc, min(cc + CPW, c1), sflag, gen);
@@ -270,6 +336,7 @@ __device__ bool block_factor(F& p, double lam, int* sflag, int gen, double shift
     panel_subst<D>(p, L, lv, threadIdx.x, blockDim.x);
     __syncthreads();
   }
+  if (nsparse < p.nlev && !dense_supernode<D>(p, L, sflag, gen)) return false;
   for (int cc = warp * CPW; cc < p.N; cc += nwarps * CPW)
     diag_rows_inverse<D>(p, L, cc, min(cc + CPW, p.N), nullptr);
   __syncthreads();
@@ -291,7 +358,8 @@ __device__ __forceinline__ void cluster_sync_all() {
 // takes the next level's early gather pairs, and cluster barriers between the phases.  The
 // factor lives in global memory; `gflag` (global, one per problem, set to -1 by the caller
 // before the launch) records a failed pivot as for block_factor.  Returns the same value in
-// every thread of the cluster.
+// every thread of the cluster.  The structure must have no dense supernode (dense_lev = nlev:
+// the bundle-adjustment reduced system is analysed without one).
 template <int D, class F>
 __device__ bool block_factor_cluster(F& p, double lam, int rank, int nranks, int* gflag, int gen) {
   double* L = p.L;

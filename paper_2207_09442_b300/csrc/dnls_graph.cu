@@ -70,7 +70,7 @@ struct KArgs {
 template <int KIND>
 struct Prob {
   static constexpr int D = Group<KIND>::DOF, PW = Group<KIND>::PW, BS = D * D, JW = 2 * BS + D;
-  int N, E, npair, nnzL, nlev, chain_lev;
+  int N, E, npair, nnzL, nlev, chain_lev, dense_lev;
   const int32_t *perm, *iperm, *colptr, *rows, *rowptr, *rowent, *lvlptr, *lvlcols, *tgtptr, *tgt,
       *gptr, *gsrc, *panptr, *pan, *incptr, *inc, *pairptr, *pairs, *pairtgt, *lsrc, *glanes, *slanes, *gsplit, *rsplit;
   const int32_t *ei, *ej;
@@ -99,6 +99,7 @@ struct Prob {
     nnzL = m->nnzL;
     nlev = m->nlev;
     chain_lev = m->chain_lev;
+    dense_lev = m->dense_lev;
     gsym = a.g.sym + m->sym;
     ei = a.g.ei + m->edge_off;
     ej = a.g.ej + m->edge_off;
@@ -1566,6 +1567,25 @@ dnls_status launch_forward(const dnls_graph* g, const dnls_solver_opts* opts, KA
 
 }  // namespace
 
+namespace {
+void fill_stats(const GraphHost& h, dnls_graph_stats* out) {
+  out->n_poses = h.P_total;
+  out->n_costs = h.E_total;
+  out->n_blocks_L = h.n_blocks_L;
+  out->n_block_updates = h.n_upd;
+  out->n_levels_max = h.max_nlev;
+  out->factor_flops = h.factor_flops;
+  out->dense_flops = h.dense_flops;
+  out->supernode_cols_max = 0;
+  out->n_supernodes = 0;
+  for (const ProbMeta& m : h.meta)
+    if (m.dense_lev < m.nlev) {
+      out->supernode_cols_max = std::max<int64_t>(out->supernode_cols_max, m.nlev - m.dense_lev);
+      ++out->n_supernodes;
+    }
+}
+}  // namespace
+
 extern "C" {
 
 dnls_status dnls_graph_create(const dnls_graph_desc* desc, dnls_graph** out) {
@@ -1708,14 +1728,17 @@ dnls_status dnls_graph_get_problem_flops(const dnls_graph* g, double* flops) {
 
 dnls_status dnls_graph_get_stats(const dnls_graph* g, dnls_graph_stats* out) {
   if (!g || !out) return DNLS_ERR_ARG;
-  const GraphHost& h = g->impl.h;
-  out->n_poses = h.P_total;
-  out->n_costs = h.E_total;
-  out->n_blocks_L = h.n_blocks_L;
-  out->n_block_updates = h.n_upd;
-  out->n_levels_max = h.max_nlev;
-  out->factor_flops = h.factor_flops;
-  out->dense_flops = h.dense_flops;
+  fill_stats(g->impl.h, out);
+  return DNLS_OK;
+}
+
+dnls_status dnls_graph_analyze(const dnls_graph_desc* desc, dnls_graph_stats* out) {
+  if (!desc || !out) return DNLS_ERR_ARG;
+  GraphHost h;
+  const int rc = build_graph_host(desc->kind, desc->batch, desc->pose_offsets, desc->edge_offsets,
+                                  desc->edge_i, desc->edge_j, desc->ordering, &h);
+  if (rc != DNLS_OK) return (dnls_status)rc;
+  fill_stats(h, out);
   return DNLS_OK;
 }
 

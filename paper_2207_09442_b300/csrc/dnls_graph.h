@@ -28,18 +28,23 @@ struct ProbMeta {
   int32_t o_rowptr, o_rowent;  // [N+1], [2 nnzL]: row structure, pairs (block id, column j)
   int32_t o_lvlptr, o_lvlcols; // [nlev+1], [N]: columns grouped by elimination-tree level
   int32_t o_tgtptr, o_tgt;     // [nlev+1], [N + nnzL]: factor target blocks grouped by level
-  int32_t o_gptr, o_gsrc;      // [N + nnzL + 1] (parallel to tgt), [2 n_upd]: source pairs
+  int32_t o_gptr, o_gsrc;      // [N + nnzL + 1] (parallel to tgt), [2 x pairs]: source pairs
   int32_t o_panptr, o_pan;     // [nlev+1], [2 nnzL]: (off-diagonal block, column) by level
   int32_t o_incptr, o_inc;     // [N+1] by position, [incidences]: cost << 1 | slot
   int32_t o_pairptr, o_pairs;  // [npair+1], [n_between]: cost << 1 | orientation
   int32_t o_pairtgt, o_lsrc;   // [npair]: L block id of each pair; [nnzL]: pair of each L block or -1
-  int32_t o_glanes, o_slanes;  // [nlev], [nlev + 1]: lanes per output in the level's gathers / solve
-                               // sweeps (1, 2, 4 or 8)
+  int32_t o_glanes, o_slanes;  // [nlev + 1], [nlev + 1]: lanes per output in the level's gathers /
+                               // solve sweeps (1, 2, 4 or 8); glanes[nlev]: the dense supernode's
+                               // gather of its sparse sources
   int32_t o_gsplit, o_rsplit;  // [N + nnzL] (parallel to tgt): end of the target's "early" source
                                // pairs (columns two or more levels below), which come first;
                                // [N]: start of row k's pairs from top-chain columns (rowent)
-  int32_t chain_lev, pad0;     // first level of the top chain (nlev: none); slanes[nlev] holds
+  int32_t chain_lev;           // first level of the top chain (nlev: none); slanes[nlev] holds
                                // the lanes of its pre-pass
+  int32_t dense_lev;           // first level of the dense supernode (nlev: none): the top chain
+                               // amalgamated into one dense block (explicit zero blocks added),
+                               // factored right-looking after the sparse levels; its targets'
+                               // source lists hold only the pairs from sparse columns
   int32_t w_H, w_L, w_Linv;    // workspace byte offsets
   int32_t w_g, w_dx, w_tmp, w_thc, w_J;
   int32_t w_bx, w_bv, w_br, w_bhx, w_ebuf, w_state, w_W;
@@ -78,8 +83,14 @@ constexpr int64_t kWsHeader = 256;
 // Returns 0 on success, or a DNLS_ERR_* code; fills `out`.
 // `threads` = the threads that will run one problem's factorization (0: one CTA's default),
 // used to choose the lanes per output of each level's sums.
+// `dense_chain`: amalgamate a long, mostly dense top chain into one dense supernode (pose
+// graphs); the bundle-adjustment reduced system (factored by a cluster of CTAs) keeps the level
+// schedule throughout.
 int build_graph_host(int kind, int B, const int64_t* pose_offsets, const int64_t* edge_offsets,
                      const int32_t* edge_i, const int32_t* edge_j, int ordering, GraphHost* out,
-                     int threads = 0);
+                     int threads = 0, bool dense_chain = true);
+
+// Smallest top chain (block columns) amalgamated into a dense supernode.
+constexpr int kDenseChainMin = 32;
 
 }  // namespace dnls

@@ -87,7 +87,7 @@ int64_t align256(int64_t x) { return (x + 255) & ~(int64_t)255; }
 
 int build_graph_host(int kind, int B, const int64_t* pose_offsets, const int64_t* edge_offsets,
                      const int32_t* edge_i, const int32_t* edge_j, int ordering, GraphHost* out,
-                     int threads) {
+                     int threads, bool dense_chain) {
   if (!out || !pose_offsets || !edge_offsets || !edge_i || !edge_j) return DNLS_ERR_ARG;
   if ((kind != DNLS_SE2 && kind != DNLS_SE3) || B < 1) return DNLS_ERR_ARG;
   if (ordering != DNLS_ORDER_MIN_DEGREE && ordering != DNLS_ORDER_NATURAL) return DNLS_ERR_ARG;
@@ -146,6 +146,55 @@ int build_graph_host(int kind, int B, const int64_t* pose_offsets, const int64_t
       for (int v : spose[k]) rows[k].push_back(iperm[v]);
       std::sort(rows[k].begin(), rows[k].end());
     }
+    // levels (height above the leaves of the elimination tree; the parent of column k is its
+    // first row)
+    std::vector<int> lev(N, 0);
+    for (int k = 0; k < N; ++k)
+      if (!rows[k].empty()) lev[rows[k][0]] = std::max(lev[rows[k][0]], lev[k] + 1);
+    int nlev = 0;
+    for (int k = 0; k < N; ++k) nlev = std::max(nlev, lev[k] + 1);
+    std::vector<std::vector<int>> bylev(nlev);
+    for (int k = 0; k < N; ++k) bylev[lev[k]].push_back(k);
+    // the top chain: the longest run of one-column levels ending at the root (the columns of
+    // the separator eliminated last); its rows' sums over columns outside it are formed in one
+    // pass of the forward solve before its levels (at least two such levels, else none)
+    int chain_lev = nlev;
+    while (chain_lev > 0 && bylev[chain_lev - 1].size() == 1) --chain_lev;
+    if (nlev - chain_lev < 2) chain_lev = nlev;
+    // algorithmic work on this structure (before any amalgamation): column j with c_j
+    // off-diagonal blocks takes part in c_j (c_j + 1) / 2 block updates, c_j of them into
+    // diagonal blocks
+    int64_t n_upd = 0, n_upd_diag = 0, nnz_alg = 0;
+    for (int j = 0; j < N; ++j) {
+      const int64_t c = (int64_t)rows[j].size();
+      n_upd += c * (c + 1) / 2;
+      n_upd_diag += c;
+      nnz_alg += c;
+    }
+    // Supernode amalgamation of the top chain.  Chain column i (level chain_lev + i) has only
+    // chain columns above it as rows, and on large pose graphs almost all of them: the chain is
+    // the dense trailing block of the factor.  A chain of at least kDenseChainMin columns that
+    // holds at least half of its lower-triangle blocks is made fully dense (the missing blocks
+    // are explicit zeros: every product that would fill them has a structurally zero factor, so
+    // they stay exactly zero) and factored as one dense supernode, right-looking, after the
+    // sparse levels.  The parents (first rows) are unchanged, so are the levels.
+    int dense_lev = nlev;
+    if (dense_chain && nlev - chain_lev >= kDenseChainMin) {
+      const int mc = nlev - chain_lev;
+      std::vector<int> cc(mc);
+      for (int i = 0; i < mc; ++i) cc[i] = bylev[chain_lev + i][0];
+      int64_t have = 0;
+      bool nested = true;
+      for (int i = 0; i < mc; ++i) {
+        have += (int64_t)rows[cc[i]].size();
+        for (int r : rows[cc[i]]) nested = nested && lev[r] > lev[cc[i]];
+        if (i + 1 < mc) nested = nested && cc[i + 1] > cc[i];
+      }
+      if (nested && 2 * have >= (int64_t)mc * (mc - 1) / 2) {
+        for (int i = 0; i < mc; ++i) rows[cc[i]].assign(cc.begin() + i + 1, cc.end());
+        dense_lev = chain_lev;
+      }
+    }
     std::vector<int> colptr(N + 1, 0);
     for (int k = 0; k < N; ++k) colptr[k + 1] = colptr[k] + (int)rows[k].size();
     const int nnzL = colptr[N];
@@ -160,29 +209,17 @@ int build_graph_host(int kind, int B, const int64_t* pose_offsets, const int64_t
     for (int j = 0; j < N; ++j)
       for (int a = 0; a < (int)rows[j].size(); ++a)
         rowl[rows[j][a]].push_back({N + colptr[j] + a, j});
-    // levels (height above the leaves of the elimination tree)
-    std::vector<int> lev(N, 0);
-    for (int k = 0; k < N; ++k)
-      if (!rows[k].empty()) lev[rows[k][0]] = std::max(lev[rows[k][0]], lev[k] + 1);
-    int nlev = 0;
-    for (int k = 0; k < N; ++k) nlev = std::max(nlev, lev[k] + 1);
-    std::vector<std::vector<int>> bylev(nlev);
-    for (int k = 0; k < N; ++k) bylev[lev[k]].push_back(k);
-    // the top chain: the longest run of one-column levels ending at the root (the columns of
-    // the separator eliminated last); its rows' sums over columns outside it are formed in one
-    // pass of the forward solve before its levels (at least two such levels, else none)
-    int chain_lev = nlev;
-    while (chain_lev > 0 && bylev[chain_lev - 1].size() == 1) --chain_lev;
-    if (nlev - chain_lev < 2) chain_lev = nlev;
-    // gather lists: per target block of column k, the (L(r,j), L(k,j)) pairs, j in rowl[k]
+    // gather lists: per target block of column k, the (L(r,j), L(k,j)) pairs, j in rowl[k]; the
+    // dense supernode's own products (source column in it) are applied right-looking by the
+    // numeric factorization and are not listed
     std::vector<std::vector<std::vector<int>>> gl(N);  // gl[k][t] flat pairs, t=0 diag, 1+a off
     std::vector<std::vector<std::vector<int>>> glv(N);  // level of each pair's source column
-    int64_t n_upd = 0, n_upd_diag = 0;  // block updates; those into diagonal blocks
     for (int k = 0; k < N; ++k) {
       gl[k].assign(1 + rows[k].size(), {});
       glv[k].assign(1 + rows[k].size(), {});
       for (auto& pr : rowl[k]) {
         const int bkj = pr.first, j = pr.second;
+        if (lev[j] >= dense_lev) continue;
         auto it = std::lower_bound(rows[j].begin(), rows[j].end(), k);
         for (; it != rows[j].end(); ++it) {
           const int r = *it;
@@ -198,8 +235,6 @@ int build_graph_host(int kind, int B, const int64_t* pose_offsets, const int64_t
           gl[k][t].push_back(a_src);
           gl[k][t].push_back(bkj);
           glv[k][t].push_back(lev[j]);
-          ++n_upd;
-          n_upd_diag += t == 0;
         }
       }
     }
@@ -286,6 +321,7 @@ int build_graph_host(int kind, int B, const int64_t* pose_offsets, const int64_t
     m.o_rsplit = mark();
     blob.insert(blob.end(), rsplit.begin(), rsplit.end());
     m.chain_lev = chain_lev;
+    m.dense_lev = dense_lev;
     m.o_lvlptr = mark();
     {
       int acc = 0;
@@ -322,9 +358,11 @@ int build_graph_host(int kind, int B, const int64_t* pose_offsets, const int64_t
         // pairs within each part is kept
         const std::vector<int>& pr = gl[e.k][e.t];
         const std::vector<int>& pl = glv[e.k][e.t];
+        // (in the dense supernode every listed pair comes from a sparse column, final before
+        // the supernode starts: all of them count as early)
         for (int late = 0; late < 2; ++late) {
           for (int q = 0; q < (int)pl.size(); ++q)
-            if ((pl[q] >= l - 1) == (late == 1)) {
+            if ((l < dense_lev && pl[q] >= l - 1) == (late == 1)) {
               gsrc.push_back(pr[2 * q]);
               gsrc.push_back(pr[2 * q + 1]);
             }
@@ -405,6 +443,11 @@ int build_graph_host(int kind, int B, const int64_t* pose_offsets, const int64_t
       const double avg = t1 > t0 ? (double)pairs_l / (t1 - t0) : 0.0;
       blob.push_back(lanes_for((int64_t)(t1 - t0) * BS, avg, 1));
     }
+    {  // glanes[nlev]: the dense supernode's gather of its sparse sources (all its targets)
+      const int t0 = tgtptr[dense_lev], t1 = tgtptr[nlev];
+      const int64_t pairs_d = gptr[t1] - gptr[t0];
+      blob.push_back(t1 > t0 ? lanes_for((int64_t)(t1 - t0) * BS, (double)pairs_d / (t1 - t0), 1) : 1);
+    }
     m.o_slanes = mark();
     int64_t pre_terms = 0;  // terms of the top chain's pre-pass
     for (int l = 0; l < nlev; ++l) {
@@ -478,7 +521,7 @@ int build_graph_host(int kind, int B, const int64_t* pose_offsets, const int64_t
     // algorithmic count: an update into a diagonal block needs only its lower triangle
     // (D (D + 1) / 2 outputs; the kernel forms the full block)
     const double ff = 2.0 * (n_upd - n_upd_diag) * D3 + (double)n_upd_diag * D * D * (D + 1) +
-                      (double)nnzL * D * D * (D + 1) + N * (2.0 * D3 / 3.0);
+                      (double)nnz_alg * D * D * (D + 1) + N * (2.0 * D3 / 3.0);
     G.factor_flops += ff;
     G.prob_flops.push_back(ff);
     G.dense_flops += (double)n * n * n / 3.0;

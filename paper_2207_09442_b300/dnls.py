@@ -49,7 +49,8 @@ class GraphInputs(ctypes.Structure):
 class GraphStats(ctypes.Structure):
     _fields_ = [("n_poses", c_int64), ("n_costs", c_int64), ("n_blocks_L", c_int64),
                 ("n_block_updates", c_int64), ("n_levels_max", c_int64),
-                ("factor_flops", c_double), ("dense_flops", c_double)]
+                ("factor_flops", c_double), ("dense_flops", c_double),
+                ("supernode_cols_max", c_int64), ("n_supernodes", c_int64)]
 
 
 class BADesc(ctypes.Structure):
@@ -91,6 +92,7 @@ _SIGS = {
     "dnls_project_grad": (c_int32, [c_int32, c_int64, c_void_p, c_void_p, c_void_p, c_void_p]),
     "dnls_lift_grad": (c_int32, [c_int32, c_int64, c_void_p, c_void_p, c_void_p, c_void_p]),
     "dnls_graph_get_stats": (c_int32, [c_void_p, ctypes.POINTER(GraphStats)]),
+    "dnls_graph_analyze": (c_int32, [ctypes.POINTER(GraphDesc), ctypes.POINTER(GraphStats)]),
     "dnls_graph_get_problem_flops": (c_int32, [c_void_p, c_void_p]),
     "dnls_status_string": (ctypes.c_char_p, [c_int32]),
     "dnls_ba_create": (c_int32, [ctypes.POINTER(BADesc), ctypes.POINTER(c_void_p)]),

@@ -70,6 +70,22 @@ class Options:
         return o
 
 
+def analyze(batch, ordering: str = "min_degree") -> dict:
+    """Sizes of the symbolic factorization of a batch of pose graphs (dnls_graph_analyze: host
+    only, no device): stored factor blocks, algorithmic block products and flops, elimination
+    levels, and the dense supernode (its block columns, and how many problems have one)."""
+    po = np.ascontiguousarray(batch.pose_offsets, dtype=np.int64)
+    eo = np.ascontiguousarray(batch.edge_offsets, dtype=np.int64)
+    ei = np.ascontiguousarray(batch.edge_i, dtype=np.int32)
+    ej = np.ascontiguousarray(batch.edge_j, dtype=np.int32)
+    desc = _d.GraphDesc(int(batch.kind), len(po) - 1, po.ctypes.data, eo.ctypes.data,
+                        ei.ctypes.data, ej.ctypes.data,
+                        _d.ORDER_NATURAL if ordering == "natural" else _d.ORDER_MIN_DEGREE)
+    s = _d.GraphStats()
+    _d.check(_d.lib().dnls_graph_analyze(ctypes.byref(desc), ctypes.byref(s)), "dnls_graph_analyze")
+    return {f: getattr(s, f) for f, _ in s._fields_}
+
+
 class PoseGraphStructure:
     """Structure of a batch of pose graphs (the Objective's variable/cost graph, Sec. 3) with
     its symbolic factorization, owned by a libdnls handle."""
