@@ -22,6 +22,7 @@ Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [-
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import statistics
@@ -48,6 +49,21 @@ METRIC = "batched LM iters/s (fwd + implicit bwd) vs plain FP64 GPU path at 1e-5
 FORWARD_SOURCES = ["dnls_graph.cu", "dnls_blockchol.cuh", "dnls_cost.cuh", "dnls_lie.cuh",
                    "dnls_graph.h", "dnls_symbolic.cpp"]
 CAPTURED_TRAFFIC = {"pgo_se3_b256": ("de7dc412ff9b3917", (4.636928e6 + 1.759488e6) * 256 / 64)}
+
+
+def forward_cluster(st, opts, ctas_per_sm: int, dev) -> int:
+    """CTAs per problem of the GN/LM forward as the library chooses them (the cg_ctas rule of
+    include/dnls.h), for the report."""
+    if opts.cg_ctas > 0:
+        return int(opts.cg_ctas)
+    if st.stats()["n_supernodes"] == 0:
+        return 1
+    import torch
+    slots = torch.cuda.get_device_properties(dev).multi_processor_count * ctas_per_sm
+    cl = 1
+    while cl < 8 and st.batch * cl * 2 <= slots:
+        cl *= 2
+    return cl
 
 
 def forward_sources_sha() -> str:
@@ -91,7 +107,8 @@ def _args():
                          "batch split over the ranks, balanced by per-problem factorization flops")
     ap.add_argument("--shape", default="",
                     help="fixed launch shape instead of autotuning: pose graphs threads,ctas_per_sm,"
-                         "smem_factor; bundle adjustment the reduced CG's CTAs per problem")
+                         "smem_factor[,ctas_per_problem]; bundle adjustment the reduced CG's CTAs "
+                         "per problem")
     return ap.parse_args()
 
 
@@ -509,8 +526,11 @@ def run_pose_graphs(args, rank, world, local, dist, out):
     rng = np.random.default_rng(1234)
     v = t64(rng.normal(size=(st.n_poses, dof)) * 1e-2)  # synthetic outer-loss tangent gradient
     if args.shape:
-        thr, ctas, smem = (int(x) for x in args.shape.split(","))
+        parts = [int(x) for x in args.shape.split(",")]
+        thr, ctas, smem = parts[:3]
         tuned = {"threads": thr, "ctas_per_sm": ctas, "smem_factor": smem, "table": "fixed by --shape"}
+        if len(parts) > 3:
+            opts = dataclasses.replace(opts, cg_ctas=parts[3])
     else:
         big = int(np.diff(batch.pose_offsets).max()) > 1024
         tuned = autotune.tune(st, opts, (theta0, meas, wd, lw), v, use_cache=False, reps=1 if big else 2)
@@ -558,7 +578,8 @@ def run_pose_graphs(args, rank, world, local, dist, out):
         "fwd_ms": fwd_ms, "bwd_ms": bwd_ms,
         "executed_lm_iterations_per_step": executed, "factorizations_per_step": int(nfact.sum()),
         "gpu_launches": 2 * args.steps,
-        "launch_shape": {k: tuned[k] for k in ("threads", "ctas_per_sm", "smem_factor")},
+        "launch_shape": {**{k: tuned[k] for k in ("threads", "ctas_per_sm", "smem_factor")},
+                         "ctas_per_problem": forward_cluster(st, opts, tuned["ctas_per_sm"], dev)},
         "autotune_table": tuned["table"],
         "backward_refine_steps_mean": float(np.mean(info["refine_steps"])),
         "backward_not_converged": int((info["status"] == 1).sum()),
@@ -641,7 +662,6 @@ def run_pose_graphs(args, rank, world, local, dist, out):
                        "grad_tolerance": 1e-8 if precision == "fp64" else 1e-4}
     # the same batched solver in FP64 throughout: what mixed precision adds on top of batching
     if precision != "fp64":
-        import dataclasses
         s64 = layer.PoseGraphSolver(st, dataclasses.replace(opts, precision="fp64"), dev)
         th64 = torch.empty_like(theta0)
 

@@ -108,10 +108,15 @@ typedef struct {
                               iterations (truncated backpropagation); 0 = all (unrolling) */
   int32_t reduced_solver;  /* bundle adjustment: DNLS_REDUCED_AUTO (0), DNLS_REDUCED_TC or
                               DNLS_REDUCED_FP64; pose graphs ignore it */
-  int32_t cg_ctas;         /* bundle adjustment, tensor-core reduced solver: CTAs per problem of the
-                              forward's conjugate-gradient solve (one thread-block cluster): 0 =
-                              library choice (enough to cover the SMs, >= 32 rows each), else
-                              1, 2, 4 or 8; pose graphs ignore it */
+  int32_t cg_ctas;         /* CTAs per problem (one thread-block cluster), 0 = library choice, else
+                              1, 2, 4 or 8.  Bundle adjustment, tensor-core reduced solver: of the
+                              forward's conjugate-gradient solve (library choice: enough to cover
+                              the SMs, >= 32 rows each).  Pose graphs, GN / LM forward: the extra
+                              CTAs share each dense supernode's trailing updates (App. E; see
+                              dnls_graph_stats.supernode_cols_max), the rest of the problem runs
+                              on the first CTA (library choice: 1 unless the batch has a dense
+                              supernode and at most half as many problems as CTA slots, then the
+                              largest power of two <= 8 that keeps one slot per CTA) */
   int32_t reserved;        /* zero */
 } dnls_solver_opts;
 

@@ -27,6 +27,56 @@ __device__ __forceinline__ double fma_t(double a, double b, double c) { return f
 __device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
 
 // ----------------------------------------------------------------------------- helpers
+// Thread-block cluster barrier with release / acquire semantics at cluster scope: every write
+// (shared or global) of every thread of the cluster before it is visible to every thread after it.
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+  asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+
+// One int of CTA `rank`'s shared memory at the offset of `local` (distributed shared memory of
+// the thread-block cluster).
+__device__ __forceinline__ int ld_cluster_shared(const int* local, int rank) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(local);
+  uint32_t ra;
+  int v;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
+  asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(ra) : "memory");
+  return v;
+}
+
+// Who runs a dense supernode's trailing updates.  SoloTeam: the problem's CTA alone.
+// ClusterTeam: the problem's CTA (cluster rank 0) and the nranks - 1 other CTAs of its thread-block
+// cluster, which wait in supernode_helper for commands that rank 0 posts in its shared memory.
+struct SoloTeam {
+  static constexpr int nranks = 1;
+  __device__ bool active() const { return false; }
+  __device__ void post(int, int) const {}
+};
+
+enum { kSnExit = 0, kSnTrailing = 1 };
+struct SnCmd {  // rank 0's command slot (shared memory)
+  int op, b, i;
+};
+
+struct ClusterTeam {
+  int nranks;   // CTAs of the cluster (> 1)
+  int b;        // the problem rank 0 is solving
+  SnCmd* cmd;   // rank 0's command slot
+  bool on;      // the problem's factor is in global memory (helpers cannot see shared memory)
+  __device__ bool active() const { return on; }
+  // Posts a command: every CTA of the cluster passes one cluster barrier, after which the
+  // helpers read the slot.
+  __device__ void post(int op, int i) const {
+    if (threadIdx.x == 0) {
+      cmd->op = op;
+      cmd->b = b;
+      cmd->i = i;
+    }
+    cluster_sync_all();
+  }
+};
+
 __device__ __forceinline__ double block_sum(double v, double* red) {
   const int t = threadIdx.x;
   red[t] = v;
@@ -236,17 +286,55 @@ __device__ __forceinline__ void damp_diagonal(F& p, double* L, double lam, doubl
   }
 }
 
-// The dense supernode (levels dense_lev .. nlev-1: one block column each, every block of its
-// lower triangle stored), factored right-looking once the sparse levels are final: (1) every
+// Trailing update of dense-supernode column i (levels dense_lev .. nlev-1: one block column
+// each, every block of the lower triangle stored): every block (r, s), i < s <= r, minus
+// L(r,i) L(s,i)^T, one block row (D outputs, D^2 FMAs from registers) per item, items spread
+// over the team threads tid = 0 .. nthr-1.
+template <int D, class F>
+__device__ __forceinline__ void supernode_trailing(F& p, double* L, int i, int tid, int nthr) {
+  constexpr int BS = D * D;
+  const int d0 = p.dense_lev, m = p.nlev - d0;
+  const int M = m - 1 - i;  // trailing supernode columns
+  // column i's off-diagonal blocks, rows i+1 .. m-1 of the supernode in order
+  const double* P = L + (int64_t)(p.N + p.colptr[p.lvlcols[p.lvlptr[d0 + i]]]) * BS;
+  // trailing blocks in column-major order: column s' (supernode column i+1+s') holds rows
+  // r' = s' .. M-1 and starts at first(s') = s' M - s' (s' - 1) / 2.  T D fits in int32: the
+  // whole factor of one problem is below 2^31 bytes.
+  const int T = M * (M + 1) / 2;
+  const int twoM1 = 2 * M + 1;
+  for (int it = tid; it < T * D; it += nthr) {
+    const int q = it / D, a = it - q * D;
+    int sc = (int)(0.5f * ((float)twoM1 - sqrtf((float)(twoM1 * twoM1 - 8 * q))));
+    sc = max(0, min(sc, M - 1));
+    while (sc > 0 && sc * M - sc * (sc - 1) / 2 > q) --sc;
+    while (sc + 1 < M && (sc + 1) * M - (sc + 1) * sc / 2 <= q) ++sc;
+    const int rc = sc + q - (sc * M - sc * (sc - 1) / 2);
+    const int ks = p.lvlcols[p.lvlptr[d0 + i + 1 + sc]];
+    double* A = L + (int64_t)(rc == sc ? ks : p.N + p.colptr[ks] + (rc - sc - 1)) * BS + a * D;
+    const double* Lr = P + (int64_t)rc * BS + a * D;
+    const double* Ls = P + (int64_t)sc * BS;
+    double x[D];
+#pragma unroll
+    for (int mm = 0; mm < D; ++mm) x[mm] = Lr[mm];
+#pragma unroll
+    for (int b = 0; b < D; ++b) {
+      double acc = A[b];
+#pragma unroll
+      for (int mm = 0; mm < D; ++mm) acc = fma(-x[mm], Ls[b * D + mm], acc);
+      A[b] = acc;
+    }
+  }
+}
+
+// The dense supernode, factored right-looking once the sparse levels are final: (1) every
 // supernode block minus its products with sparse columns, one gather over all its targets;
 // then for each supernode column i: (2) its diagonal block factored by warp 0, (3) its
-// off-diagonal blocks L(r,i) by substitution, (4) every trailing block (r, s), i < s <= r,
-// minus L(r,i) L(s,i)^T, one block row (D outputs, D^2 FMAs from registers) per thread.  The
-// products are those of the level schedule, summed column by column.  Returns false (uniformly)
-// on a pivot that is not positive and finite, after writing `gen` into *sflag.
-template <int D, class F>
-__device__ bool dense_supernode(F& p, double* L, int* sflag, int gen) {
-  constexpr int BS = D * D;
+// off-diagonal blocks L(r,i) by substitution, (4) the trailing update (supernode_trailing), by
+// this CTA alone or, with an active ClusterTeam, by all CTAs of the cluster.  The products are
+// those of the level schedule, summed column by column.  Returns false (uniformly) on a pivot
+// that is not positive and finite, after writing `gen` into *sflag.
+template <int D, class F, class Team>
+__device__ bool dense_supernode(F& p, double* L, int* sflag, int gen, const Team& team) {
   const int d0 = p.dense_lev, m = p.nlev - d0;
   gather_targets<D>(p, L, p.tgtptr[d0], p.tgtptr[p.nlev], p.glanes[p.nlev], 1, threadIdx.x,
                     blockDim.x);
@@ -257,40 +345,22 @@ __device__ bool dense_supernode(F& p, double* L, int* sflag, int gen) {
     __syncthreads();
     if (*sflag == gen) return false;
     panel_subst<D>(p, L, d0 + i, threadIdx.x, blockDim.x);
-    __syncthreads();
-    const int M = m - 1 - i;  // trailing supernode columns
-    if (M == 0) break;
-    // column i's off-diagonal blocks, rows i+1 .. m-1 of the supernode in order
-    const double* P = L + (int64_t)(p.N + p.colptr[p.lvlcols[c0]]) * BS;
-    // trailing blocks in column-major order: column s' (supernode column i+1+s') holds rows
-    // r' = s' .. M-1 and starts at first(s') = s' M - s' (s' - 1) / 2.  T D fits in int32: the
-    // whole factor of one problem is below 2^31 bytes.
-    const int T = M * (M + 1) / 2;
-    const int twoM1 = 2 * M + 1;
-    for (int it = threadIdx.x; it < T * D; it += blockDim.x) {
-      const int q = it / D, a = it - q * D;
-      int sc = (int)(0.5f * ((float)twoM1 - sqrtf((float)(twoM1 * twoM1 - 8 * q))));
-      sc = max(0, min(sc, M - 1));
-      while (sc > 0 && sc * M - sc * (sc - 1) / 2 > q) --sc;
-      while (sc + 1 < M && (sc + 1) * M - (sc + 1) * sc / 2 <= q) ++sc;
-      const int rc = sc + q - (sc * M - sc * (sc - 1) / 2);
-      const int ks = p.lvlcols[p.lvlptr[d0 + i + 1 + sc]];
-      double* A = L + (int64_t)(rc == sc ? ks : p.N + p.colptr[ks] + (rc - sc - 1)) * BS + a * D;
-      const double* Lr = P + (int64_t)rc * BS + a * D;
-      const double* Ls = P + (int64_t)sc * BS;
-      double x[D];
-#pragma unroll
-      for (int mm = 0; mm < D; ++mm) x[mm] = Lr[mm];
-#pragma unroll
-      for (int b = 0; b < D; ++b) {
-        double acc = A[b];
-#pragma unroll
-        for (int mm = 0; mm < D; ++mm) acc = fma(-x[mm], Ls[b * D + mm], acc);
-        A[b] = acc;
-      }
+    if (m - 1 - i == 0) break;
+    if (team.active()) {
+      // the command's barrier also publishes this CTA's panel to the helpers; the second
+      // barrier publishes their trailing blocks back
+      team.post(kSnTrailing, i);
+      const int nr = team.nranks;
+      supernode_trailing<D>(p, L, i, ((threadIdx.x >> 5) * nr) * 32 + (threadIdx.x & 31),
+                            nr * blockDim.x);
+      cluster_sync_all();
+    } else {
+      __syncthreads();
+      supernode_trailing<D>(p, L, i, threadIdx.x, blockDim.x);
+      __syncthreads();
     }
-    __syncthreads();
   }
+  __syncthreads();
   return true;
 }
 
@@ -300,8 +370,9 @@ __device__ bool dense_supernode(F& p, double* L, int* sflag, int gen) {
 // Returns false (uniformly across the CTA) if a pivot is not positive or not finite.  A failing
 // thread writes the call's generation number `gen` into *sflag; the flag is never reset, so a
 // slow thread can never see a later call's state.
-template <int D, class F>
-__device__ bool block_factor(F& p, double lam, int* sflag, int gen, double shift = 0.0) {
+template <int D, class F, class Team = SoloTeam>
+__device__ bool block_factor(F& p, double lam, int* sflag, int gen, double shift = 0.0,
+                             const Team& team = Team()) {
   constexpr int CPW = 32 / D;  // diagonal blocks per warp in diag_rows_factor
   double* L = p.L;
   const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -336,7 +407,7 @@ __device__ bool block_factor(F& p, double lam, int* sflag, int gen, double shift
     panel_subst<D>(p, L, lv, threadIdx.x, blockDim.x);
     __syncthreads();
   }
-  if (nsparse < p.nlev && !dense_supernode<D>(p, L, sflag, gen)) return false;
+  if (nsparse < p.nlev && !dense_supernode<D>(p, L, sflag, gen, team)) return false;
   for (int cc = warp * CPW; cc < p.N; cc += nwarps * CPW)
     diag_rows_inverse<D>(p, L, cc, min(cc + CPW, p.N), nullptr);
   __syncthreads();
@@ -344,12 +415,6 @@ __device__ bool block_factor(F& p, double lam, int* sflag, int gen, double shift
 }
 
 // ----------------------------------------------------------------------------- cluster factor
-// Thread-block cluster barrier with release / acquire semantics at cluster scope: every write
-// (shared or global) of every thread of the cluster before it is visible to every thread after it.
-__device__ __forceinline__ void cluster_sync_all() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
-  asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
-}
 
 // block_factor by the nranks CTAs of a thread-block cluster (rank = the CTA's rank in it), for a
 // factor too large for one SM's FP64 rate: the same level schedule and the same sums in the same

@@ -65,6 +65,8 @@ struct KArgs {
   int64_t rec_stride;   // bytes per problem record
   int rec_nmax;         // poses per record slot (the batch's largest problem)
   int smem_bytes;       // dynamic shared memory per CTA for staging (0 = none)
+  int cluster;          // GN/LM forward: CTAs per problem (a thread-block cluster; 0 or 1: one),
+                        // the extra CTAs sharing the dense supernode's trailing updates
 };
 
 template <int KIND>
@@ -363,6 +365,11 @@ __device__ __forceinline__ bool factor(Prob<KIND>& p, double lam, int* sflag, in
                                        double shift = 0.0) {
   return block_factor<Group<KIND>::DOF>(p, lam, sflag, gen, shift);
 }
+template <int KIND, class Team>
+__device__ __forceinline__ bool factor_team(Prob<KIND>& p, double lam, int* sflag, int gen,
+                                            const Team& team) {
+  return block_factor<Group<KIND>::DOF>(p, lam, sflag, gen, 0.0, team);
+}
 template <int KIND, bool kTopChain = true>
 __device__ __forceinline__ void chol_solve(Prob<KIND>& p, double* x) {
   block_solve<Group<KIND>::DOF, kTopChain>(p, x);
@@ -421,11 +428,15 @@ __device__ RecView rec_view(const KArgs& a, int b) {
 
 // ----------------------------------------------------------------------------- forward
 template <int KIND, class P>
-__device__ void forward_problem(const KArgs& a, int b, char* smem, double* red, int* sflag) {
+__device__ void forward_problem(const KArgs& a, int b, char* smem, double* red, int* sflag,
+                                SnCmd* cmd) {
   constexpr int D = Group<KIND>::DOF, PW = Group<KIND>::PW;
   Prob<KIND> p;
   p.init(a, b, smem, a.smem_bytes);
   p.stage_in(false);
+  // the cluster's other CTAs take part in the dense supernode's trailing updates when the
+  // factor is in global memory (they cannot see this CTA's shared memory)
+  const ClusterTeam team{a.cluster > 1 ? a.cluster : 1, b, cmd, a.cluster > 1 && p.L == p.Lg};
   p.prepare_weights();
   const int n = p.N * D;
   double S = eval_S<KIND>(p, p.theta, red);
@@ -450,7 +461,7 @@ __device__ void forward_problem(const KArgs& a, int b, char* smem, double* red, 
       }
     }
     ++nfact;
-    const bool ok = factor<KIND>(p, lam, sflag, it);
+    const bool ok = factor_team<KIND>(p, lam, sflag, it, team);
     factor_ok = ok ? 1 : 0;
     lam_fact = lam;
     if (!ok) {
@@ -704,16 +715,51 @@ __device__ __forceinline__ int next_problem(const KArgs& a, int* slot) {
   return q < a.g.B ? a.g.order[q] : -1;
 }
 
+// Cluster ranks > 0 of the GN/LM forward: their share of every dense-supernode trailing update
+// that rank 0 posts (supernode_trailing with the cluster's team indexing), until rank 0 posts
+// the exit.  Each command is one cluster barrier (then the slot is read from rank 0's shared
+// memory) and, for an update, one more after it; the exit's second barrier keeps rank 0 alive
+// until every helper has read the slot.
+template <int KIND>
+__device__ void supernode_helper(const KArgs& a, const SnCmd* cmd, int rank, int nranks) {
+  for (;;) {
+    cluster_sync_all();
+    const int op = ld_cluster_shared(&cmd->op, 0);
+    if (op == kSnExit) {
+      cluster_sync_all();
+      return;
+    }
+    const int b = ld_cluster_shared(&cmd->b, 0), i = ld_cluster_shared(&cmd->i, 0);
+    Prob<KIND> p;
+    p.init(a, b, nullptr, 0);
+    supernode_trailing<Group<KIND>::DOF>(
+        p, p.L, i, ((threadIdx.x >> 5) * nranks + rank) * 32 + (threadIdx.x & 31), nranks * blockDim.x);
+    cluster_sync_all();
+  }
+}
+
 template <int KIND, class P>
 __global__ void __launch_bounds__(256, 2) k_forward(KArgs a) {
   __shared__ double red[256];
   __shared__ int sflag, slot;
+  __shared__ SnCmd cmd;
+  const int nr = a.cluster > 1 ? a.cluster : 1;
+  const int rank = (int)(blockIdx.x % (unsigned)nr);  // a 1-D cluster's CTA rank
+  if (rank > 0) {
+    supernode_helper<KIND>(a, &cmd, rank, nr);
+    return;
+  }
   for (;;) {
     const int b = next_problem(a, &slot);
     if (b < 0) break;
     if (threadIdx.x == 0) sflag = -1;
     __syncthreads();
-    forward_problem<KIND, P>(a, b, a.smem_bytes ? dyn_smem : nullptr, red, &sflag);
+    forward_problem<KIND, P>(a, b, a.smem_bytes ? dyn_smem : nullptr, red, &sflag, &cmd);
+  }
+  if (nr > 1) {
+    const ClusterTeam exit_team{nr, 0, &cmd, true};
+    exit_team.post(kSnExit, 0);
+    cluster_sync_all();
   }
 }
 
@@ -1485,6 +1531,8 @@ dnls_status check_opts(const dnls_solver_opts* o) {
     return DNLS_ERR_ARG;
   if (o->threads != 0 && o->threads != 128 && o->threads != 256) return DNLS_ERR_ARG;
   if (o->ctas_per_sm < 0 || o->ctas_per_sm > 16) return DNLS_ERR_ARG;
+  if (o->cg_ctas != 0 && o->cg_ctas != 1 && o->cg_ctas != 2 && o->cg_ctas != 4 && o->cg_ctas != 8)
+    return DNLS_ERR_ARG;
   if (!(o->lambda0 >= 0.0) || !(o->tau >= 0.0)) return DNLS_ERR_ARG;
   return DNLS_OK;
 }
@@ -1526,9 +1574,21 @@ KArgs base_args(const dnls_graph* g, const dnls_graph_inputs* in, void* ws) {
   return a;
 }
 
+// CTAs per problem of the GN/LM forward: the option (pose graphs: cg_ctas), else, for a batch
+// with a dense supernode and fewer problems than half the CTA slots, the largest power of two
+// (<= 8) that still gives every problem's cluster its own slots; else 1.
+int forward_cluster(const GraphHandle& G, const dnls_solver_opts* o, int ctas) {
+  if (o->cg_ctas > 0) return o->cg_ctas;
+  bool sn = false;
+  for (const ProbMeta& m : G.h.meta) sn = sn || m.dense_lev < m.nlev;
+  int cl = 1;
+  while (sn && cl < 8 && (int64_t)G.h.B * cl * 2 <= (int64_t)G.sm_count * ctas) cl *= 2;
+  return cl;
+}
+
 template <class K>
 dnls_status launch_persistent(K kernel, const dnls_graph* g, const dnls_solver_opts* o, KArgs& a,
-                              cudaStream_t st, bool /*unused*/ = true) {
+                              cudaStream_t st, int cluster = 1) {
   const GraphHandle& G = g->impl;
   const int threads = o->threads ? o->threads : (G.h.dof == 6 ? 256 : 128);
   const int ctas = o->ctas_per_sm ? o->ctas_per_sm : (G.h.dof == 6 ? 1 : 2);
@@ -1539,12 +1599,30 @@ dnls_status launch_persistent(K kernel, const dnls_graph* g, const dnls_solver_o
     smem = std::max(0, std::min(G.h.max_arena_bytes, budget));
   }
   a.smem_bytes = smem;
+  a.cluster = cluster;
   if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
     return DNLS_ERR_CUDA;
-  const int grid = std::max(1, std::min(G.h.B, G.sm_count * ctas));
   if (cudaMemsetAsync(a.counter, 0, sizeof(int), st) != cudaSuccess) return DNLS_ERR_CUDA;
-  kernel<<<grid, threads, smem, st>>>(a);
-  return cuda_status(cudaGetLastError());
+  if (cluster <= 1) {
+    const int grid = std::max(1, std::min(G.h.B, G.sm_count * ctas));
+    kernel<<<grid, threads, smem, st>>>(a);
+    return cuda_status(cudaGetLastError());
+  }
+  // one cluster per problem in flight: rank 0 takes problems from the counter, the others help
+  const int clusters = std::max(1, std::min(G.h.B, G.sm_count * ctas / cluster));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(clusters * cluster));
+  cfg.blockDim = dim3((unsigned)threads);
+  cfg.dynamicSmemBytes = (size_t)smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)cluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cuda_status(cudaLaunchKernelEx(&cfg, kernel, a));
 }
 
 // the forward kernel for the problem kind, precision and algorithm
@@ -1558,11 +1636,13 @@ dnls_status launch_forward(const dnls_graph* g, const dnls_solver_opts* opts, KA
     return mixed ? launch_persistent(k_forward_dogleg<2, float>, g, opts, a, st)
                  : launch_persistent(k_forward_dogleg<2, double>, g, opts, a, st);
   }
+  const int ctas = opts->ctas_per_sm ? opts->ctas_per_sm : (g->impl.h.dof == 6 ? 1 : 2);
+  const int cl = forward_cluster(g->impl, opts, ctas);
   if (se3)
-    return mixed ? launch_persistent(k_forward<3, float>, g, opts, a, st)
-                 : launch_persistent(k_forward<3, double>, g, opts, a, st);
-  return mixed ? launch_persistent(k_forward<2, float>, g, opts, a, st)
-               : launch_persistent(k_forward<2, double>, g, opts, a, st);
+    return mixed ? launch_persistent(k_forward<3, float>, g, opts, a, st, cl)
+                 : launch_persistent(k_forward<3, double>, g, opts, a, st, cl);
+  return mixed ? launch_persistent(k_forward<2, float>, g, opts, a, st, cl)
+               : launch_persistent(k_forward<2, double>, g, opts, a, st, cl);
 }
 
 }  // namespace
@@ -1690,11 +1770,11 @@ dnls_status dnls_graph_backward(const dnls_graph* g, const dnls_solver_opts* opt
     a.rec = (char*)workspace + rec_offset(g);
     a.rec_stride = rec_stride(g, opts->iters);
     a.rec_nmax = g->impl.nmax;
-    if (g->impl.h.kind == DNLS_SE3) return launch_persistent(k_unroll<3>, g, opts, a, st, false);
-    return launch_persistent(k_unroll<2>, g, opts, a, st, false);
+    if (g->impl.h.kind == DNLS_SE3) return launch_persistent(k_unroll<3>, g, opts, a, st);
+    return launch_persistent(k_unroll<2>, g, opts, a, st);
   }
-  if (g->impl.h.kind == DNLS_SE3) return launch_persistent(k_backward<3>, g, opts, a, st, false);
-  return launch_persistent(k_backward<2>, g, opts, a, st, false);
+  if (g->impl.h.kind == DNLS_SE3) return launch_persistent(k_backward<3>, g, opts, a, st);
+  return launch_persistent(k_backward<2>, g, opts, a, st);
 }
 
 dnls_status dnls_graph_linearize(const dnls_graph* g, const dnls_solver_opts* opts,

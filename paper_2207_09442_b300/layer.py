@@ -36,7 +36,8 @@ class Options:
     radius0: float = 1.0             # algo "dogleg": initial trust radius
     trunc_steps: int = 0             # backward_mode "unroll": last k iterations only (0 = all)
     reduced_solver: str = "auto"     # bundle adjustment: "auto" | "tc" | "fp64"
-    cg_ctas: int = 0                 # bundle adjustment: CTAs per problem of the reduced CG (0 = library)
+    cg_ctas: int = 0                 # CTAs per problem (0 = library): BA reduced CG; pose-graph
+                                     # GN/LM forward: the dense supernode's trailing updates
 
     def c(self) -> _d.SolverOpts:
         fp64 = self.precision == "fp64"

@@ -115,3 +115,44 @@ def test_dogleg_and_dlm_with_supernode():
     for k in range(b.batch):
         assert rel(edges_of(b, gm, k), refs[k][0]) < 1e-8, k
         assert rel(edges_of(b, gl, k), refs[k][1]) < 1e-8, k
+
+
+@pytest.mark.parametrize("cl", [2, 4, 8])
+def test_cluster_shares_trailing_updates_bitwise(cl):
+    """CTAs per problem (a thread-block cluster) for the supernode's trailing updates: every
+    trailing block row is still computed by one thread in the same order, so the poses equal the
+    single-CTA forward's bit for bit."""
+    b = synth.pgo_se3(batch=3, n_poses=600, n_lc=150, config_id=167)
+    base = dict(algo="lm", iters=6, precision="mixed_fp32", tau=0.0, threads=256, ctas_per_sm=2,
+                smem_factor=0)
+    sol1, th1, _ = run_forward(b, layer.Options(**base, cg_ctas=1))
+    sol2, th2, _ = run_forward(b, layer.Options(**base, cg_ctas=cl))
+    assert torch.equal(th1, th2)
+    i1, i2 = sol1.info_dict(), sol2.info_dict()
+    assert (i1["S_final"] == i2["S_final"]).all() and (i2["status"] == 0).all()
+
+
+def test_cluster_with_staged_small_problems():
+    """A cluster launch over a batch whose small problems keep their factor in shared memory
+    (no help for them: the other CTAs cannot see it) and whose large one has a supernode in
+    global memory (helped): the same poses as one CTA per problem, and the oracle's."""
+    parts = [synth.pgo_se3(batch=1, n_poses=40, n_lc=10, config_id=168),
+             synth.pgo_se3(batch=1, n_poses=500, n_lc=125, config_id=169),
+             synth.pgo_se3(batch=1, n_poses=24, n_lc=6, config_id=170)]
+    b = synth.concat_pose_graphs(parts)
+    base = dict(algo="lm", iters=8, precision="fp64", tau=0.0, threads=256, ctas_per_sm=1,
+                smem_factor=1)
+    _, th1, _ = run_forward(b, layer.Options(**base, cg_ctas=1))
+    sol2, th2, _ = run_forward(b, layer.Options(**base, cg_ctas=2))
+    assert torch.equal(th1, th2)
+    opts = layer.Options(**base)
+    for k in range(b.batch):
+        _, ref, _ = oracle_solve(b, k, opts)
+        assert rel(poses_of(b, th2, k), ref) < 1e-7, k
+
+
+def test_cluster_size_is_validated():
+    from paper_2207_09442_b300 import dnls
+    b = synth.pgo_se3(batch=1, n_poses=16, n_lc=4, config_id=171)
+    with pytest.raises(dnls.DnlsError):
+        run_forward(b, layer.Options(algo="lm", iters=2, precision="fp64", cg_ctas=3))
