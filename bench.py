@@ -100,6 +100,9 @@ def _args():
     ap.add_argument("--trunc", type=int, default=0,
                     help="with --backward unroll: differentiate only the last k iterations (0 = all)")
     ap.add_argument("--no-extras", action="store_true", help="skip baselines (for profiling)")
+    ap.add_argument("--iters", type=int, default=0,
+                    help="pose graphs: LM/GN iterations instead of the workload's (small profiling "
+                         "cases); 0 = the workload's")
     ap.add_argument("--batch", type=int, default=0,
                     help="first N problems only (profiling captures); default: the full workload")
     ap.add_argument("--scaling", default="weak", choices=["weak", "strong"],
@@ -499,6 +502,7 @@ def run_pose_graphs(args, rank, world, local, dist, out):
     name = args.workload
     algo, iters, precision, lam0 = _setting(name)
     algo = args.algo or algo
+    iters = args.iters or iters
     bmode = args.backward
     dev = torch.device("cuda", local)
     part_info = None
