@@ -525,7 +525,7 @@ __global__ void __launch_bounds__(256) k_ba_reduced_factor(BAArgs a) {
   RedView p;
   p.init(a, b);
   if (rank == 0 && threadIdx.x == 0) s.fact_flag = -1;  // published by the first cluster barrier
-  const bool ok = block_factor_cluster<6>(p, 0.0, rank, kRedCluster, &s.fact_flag, 0);
+  const bool ok = block_factor_cluster<6, false>(p, 0.0, rank, kRedCluster, &s.fact_flag, 0);
   if (rank == 0 && threadIdx.x == 0) {
     s.factor_ok = ok ? 1 : 0;
     if (!ok) s.bad = 1;

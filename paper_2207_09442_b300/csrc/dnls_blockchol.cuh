@@ -34,7 +34,7 @@ __device__ __forceinline__ void cluster_sync_all() {
   asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
 }
 
-// One int of CTA `rank`'s shared memory at the offset of `local` (distributed shared memory of
+// One value of CTA `rank`'s shared memory at the offset of `local` (distributed shared memory of
 // the thread-block cluster).
 __device__ __forceinline__ int ld_cluster_shared(const int* local, int rank) {
   const uint32_t a = (uint32_t)__cvta_generic_to_shared(local);
@@ -44,38 +44,14 @@ __device__ __forceinline__ int ld_cluster_shared(const int* local, int rank) {
   asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(ra) : "memory");
   return v;
 }
-
-// Who runs a dense supernode's trailing updates.  SoloTeam: the problem's CTA alone.
-// ClusterTeam: the problem's CTA (cluster rank 0) and the nranks - 1 other CTAs of its thread-block
-// cluster, which wait in supernode_helper for commands that rank 0 posts in its shared memory.
-struct SoloTeam {
-  static constexpr int nranks = 1;
-  __device__ bool active() const { return false; }
-  __device__ void post(int, int) const {}
-};
-
-enum { kSnExit = 0, kSnTrailing = 1 };
-struct SnCmd {  // rank 0's command slot (shared memory)
-  int op, b, i;
-};
-
-struct ClusterTeam {
-  int nranks;   // CTAs of the cluster (> 1)
-  int b;        // the problem rank 0 is solving
-  SnCmd* cmd;   // rank 0's command slot
-  bool on;      // the problem's factor is in global memory (helpers cannot see shared memory)
-  __device__ bool active() const { return on; }
-  // Posts a command: every CTA of the cluster passes one cluster barrier, after which the
-  // helpers read the slot.
-  __device__ void post(int op, int i) const {
-    if (threadIdx.x == 0) {
-      cmd->op = op;
-      cmd->b = b;
-      cmd->i = i;
-    }
-    cluster_sync_all();
-  }
-};
+__device__ __forceinline__ double ld_cluster_shared(const double* local, int rank) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(local);
+  uint32_t ra;
+  double v;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
+  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(ra) : "memory");
+  return v;
+}
 
 __device__ __forceinline__ double block_sum(double v, double* red) {
   const int t = threadIdx.x;
@@ -329,12 +305,11 @@ __device__ __forceinline__ void supernode_trailing(F& p, double* L, int i, int t
 // The dense supernode, factored right-looking once the sparse levels are final: (1) every
 // supernode block minus its products with sparse columns, one gather over all its targets;
 // then for each supernode column i: (2) its diagonal block factored by warp 0, (3) its
-// off-diagonal blocks L(r,i) by substitution, (4) the trailing update (supernode_trailing), by
-// this CTA alone or, with an active ClusterTeam, by all CTAs of the cluster.  The products are
-// those of the level schedule, summed column by column.  Returns false (uniformly) on a pivot
-// that is not positive and finite, after writing `gen` into *sflag.
-template <int D, class F, class Team>
-__device__ bool dense_supernode(F& p, double* L, int* sflag, int gen, const Team& team) {
+// off-diagonal blocks L(r,i) by substitution, (4) the trailing update (supernode_trailing).
+// The products are those of the level schedule, summed column by column.  Returns false
+// (uniformly) on a pivot that is not positive and finite, after writing `gen` into *sflag.
+template <int D, class F>
+__device__ bool dense_supernode(F& p, double* L, int* sflag, int gen) {
   const int d0 = p.dense_lev, m = p.nlev - d0;
   gather_targets<D>(p, L, p.tgtptr[d0], p.tgtptr[p.nlev], p.glanes[p.nlev], 1, threadIdx.x,
                     blockDim.x);
@@ -345,22 +320,11 @@ __device__ bool dense_supernode(F& p, double* L, int* sflag, int gen, const Team
     __syncthreads();
     if (*sflag == gen) return false;
     panel_subst<D>(p, L, d0 + i, threadIdx.x, blockDim.x);
+    __syncthreads();
     if (m - 1 - i == 0) break;
-    if (team.active()) {
-      // the command's barrier also publishes this CTA's panel to the helpers; the second
-      // barrier publishes their trailing blocks back
-      team.post(kSnTrailing, i);
-      const int nr = team.nranks;
-      supernode_trailing<D>(p, L, i, ((threadIdx.x >> 5) * nr) * 32 + (threadIdx.x & 31),
-                            nr * blockDim.x);
-      cluster_sync_all();
-    } else {
-      __syncthreads();
-      supernode_trailing<D>(p, L, i, threadIdx.x, blockDim.x);
-      __syncthreads();
-    }
+    supernode_trailing<D>(p, L, i, threadIdx.x, blockDim.x);
+    __syncthreads();
   }
-  __syncthreads();
   return true;
 }
 
@@ -370,9 +334,8 @@ __device__ bool dense_supernode(F& p, double* L, int* sflag, int gen, const Team
 // Returns false (uniformly across the CTA) if a pivot is not positive or not finite.  A failing
 // thread writes the call's generation number `gen` into *sflag; the flag is never reset, so a
 // slow thread can never see a later call's state.
-template <int D, class F, class Team = SoloTeam>
-__device__ bool block_factor(F& p, double lam, int* sflag, int gen, double shift = 0.0,
-                             const Team& team = Team()) {
+template <int D, class F>
+__device__ bool block_factor(F& p, double lam, int* sflag, int gen, double shift = 0.0) {
   constexpr int CPW = 32 / D;  // diagonal blocks per warp in diag_rows_factor
   double* L = p.L;
   const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -407,7 +370,7 @@ __device__ bool block_factor(F& p, double lam, int* sflag, int gen, double shift
     panel_subst<D>(p, L, lv, threadIdx.x, blockDim.x);
     __syncthreads();
   }
-  if (nsparse < p.nlev && !dense_supernode<D>(p, L, sflag, gen, team)) return false;
+  if (nsparse < p.nlev && !dense_supernode<D>(p, L, sflag, gen)) return false;
   for (int cc = warp * CPW; cc < p.N; cc += nwarps * CPW)
     diag_rows_inverse<D>(p, L, cc, min(cc + CPW, p.N), nullptr);
   __syncthreads();
@@ -420,13 +383,16 @@ __device__ bool block_factor(F& p, double lam, int* sflag, int gen, double shift
 // factor too large for one SM's FP64 rate: the same level schedule and the same sums in the same
 // order, with the gather, panel and wide-level items spread over all the cluster's threads, the
 // narrow-level diagonal blocks factored by warp 0 of rank 0 while every other warp of the cluster
-// takes the next level's early gather pairs, and cluster barriers between the phases.  The
-// factor lives in global memory; `gflag` (global, one per problem, set to -1 by the caller
-// before the launch) records a failed pivot as for block_factor.  Returns the same value in
-// every thread of the cluster.  The structure must have no dense supernode (dense_lev = nlev:
-// the bundle-adjustment reduced system is analysed without one).
-template <int D, class F>
-__device__ bool block_factor_cluster(F& p, double lam, int rank, int nranks, int* gflag, int gen) {
+// takes the next level's early gather pairs, and cluster barriers between the phases; the dense
+// supernode, if any, column by column as in dense_supernode with its gathers, panels and
+// trailing updates spread the same way.  The factor lives in global memory; `gflag` (global, one
+// per problem, set to -1 before the first call of a launch and published by a cluster barrier)
+// records a failed pivot as for block_factor.  Returns the same value in every thread of the
+// cluster, right after a cluster barrier.  kDense = false compiles the supernode part out (for
+// structures analysed without one).
+template <int D, bool kDense = true, class F>
+__device__ bool block_factor_cluster(F& p, double lam, int rank, int nranks, int* gflag, int gen,
+                                     double shift = 0.0) {
   double* L = p.L;
   // team index: consecutive warps of work go to consecutive CTAs, so that a phase with fewer
   // items than the cluster has threads still spreads over all of the cluster's SMs
@@ -434,21 +400,22 @@ __device__ bool block_factor_cluster(F& p, double lam, int rank, int nranks, int
   const int nthr = nranks * blockDim.x;
   load_factor<D>(p, L, tid, nthr);
   cluster_sync_all();
-  damp_diagonal<D>(p, L, lam, 0.0, tid, nthr);
+  damp_diagonal<D>(p, L, lam, shift, tid, nthr);
   cluster_sync_all();
   constexpr int CPW = 32 / D;  // diagonal blocks per warp in diag_rows_factor
   const int warp = tid >> 5, nwarps = nthr >> 5;
+  const int nsparse = kDense ? p.dense_lev : p.nlev;  // levels of the level schedule
   bool early_done = false;
-  for (int lv = 0; lv < p.nlev; ++lv) {
+  for (int lv = 0; lv < nsparse; ++lv) {
     gather_level<D>(p, L, lv, early_done ? 2 : 0, tid, nthr);
     cluster_sync_all();
     const int c0 = p.lvlptr[lv], c1 = p.lvlptr[lv + 1];
     if (c1 - c0 <= CPW) {
       if (warp == 0)
         diag_rows_factor<D>(p, L, c0, c1, gflag, gen);
-      else if (lv + 1 < p.nlev)
+      else if (lv + 1 < nsparse)
         gather_level<D>(p, L, lv + 1, 1, tid - 32, nthr - 32);
-      early_done = lv + 1 < p.nlev;
+      early_done = lv + 1 < nsparse;
     } else {
       for (int cc = c0 + warp * CPW; cc < c1; cc += nwarps * CPW)
         diag_rows_factor<D>(p, L, cc, min(cc + CPW, c1), gflag, gen);
@@ -458,6 +425,22 @@ __device__ bool block_factor_cluster(F& p, double lam, int rank, int nranks, int
     if (*(volatile int*)gflag == gen) return false;
     panel_subst<D>(p, L, lv, tid, nthr);
     cluster_sync_all();
+  }
+  if (kDense && nsparse < p.nlev) {
+    const int m = p.nlev - nsparse;
+    gather_targets<D>(p, L, p.tgtptr[nsparse], p.tgtptr[p.nlev], p.glanes[p.nlev], 1, tid, nthr);
+    cluster_sync_all();
+    for (int i = 0; i < m; ++i) {
+      const int c0 = p.lvlptr[nsparse + i];
+      if (warp == 0) diag_rows_factor<D>(p, L, c0, c0 + 1, gflag, gen);
+      cluster_sync_all();
+      if (*(volatile int*)gflag == gen) return false;
+      panel_subst<D>(p, L, nsparse + i, tid, nthr);
+      cluster_sync_all();
+      if (m - 1 - i == 0) break;
+      supernode_trailing<D>(p, L, i, tid, nthr);
+      cluster_sync_all();
+    }
   }
   for (int cc = warp * CPW; cc < p.N; cc += nwarps * CPW)
     diag_rows_inverse<D>(p, L, cc, min(cc + CPW, p.N), nullptr);

@@ -365,10 +365,47 @@ __device__ __forceinline__ bool factor(Prob<KIND>& p, double lam, int* sflag, in
                                        double shift = 0.0) {
   return block_factor<Group<KIND>::DOF>(p, lam, sflag, gen, shift);
 }
-template <int KIND, class Team>
-__device__ __forceinline__ bool factor_team(Prob<KIND>& p, double lam, int* sflag, int gen,
-                                            const Team& team) {
-  return block_factor<Group<KIND>::DOF>(p, lam, sflag, gen, 0.0, team);
+// Thread-block cluster per problem (GN/LM forward, KArgs::cluster > 1).  Rank 0 runs the
+// problem; the other CTAs wait in cluster_helper and join each numeric factorization, which
+// then runs as block_factor_cluster over the whole cluster.  Rank 0 posts a command in its
+// shared memory slot; every CTA passes one cluster barrier, after which the helpers read the slot
+// through distributed shared memory.  A factorization command is followed by the cluster
+// factorization (which ends on a cluster barrier, also when a pivot fails) and one more barrier,
+// so that the slot is not rewritten before every helper has read it; the exit command by one more
+// barrier, which keeps rank 0 (and its slot) alive until every helper has read it.
+enum { kClExit = 0, kClFactor = 1 };
+struct ClCmd {
+  double lam;  // damping of the factorization
+  int op, b, gen;
+};
+
+struct ClusterTeam {
+  int nranks;  // CTAs of the cluster (1: none)
+  ClCmd* cmd;  // rank 0's command slot
+  bool on;     // this problem's factor is in global memory (the helpers cannot see shared memory)
+  __device__ void post(int op, int b, int gen, double lam) const {
+    if (threadIdx.x == 0) {
+      cmd->op = op;
+      cmd->b = b;
+      cmd->gen = gen;
+      cmd->lam = lam;
+    }
+    cluster_sync_all();
+  }
+};
+
+// The numeric factorization of the LM iteration `it`: by the whole cluster when the team is on,
+// else by this CTA (sflag: its shared failure flag).  kCluster = false (the kernel instance for
+// one CTA per problem) compiles the cluster path out, so that its register allocation is that of
+// the single-CTA factorization alone.
+template <int KIND, bool kCluster>
+__device__ bool factor_team(Prob<KIND>& p, double lam, int* sflag, int it, const ClusterTeam& team,
+                            int b) {
+  if (!kCluster || !team.on) return factor<KIND>(p, lam, sflag, it);
+  team.post(kClFactor, b, it, lam);
+  const bool ok = block_factor_cluster<Group<KIND>::DOF>(p, lam, 0, team.nranks, &p.st->fact_flag, it);
+  cluster_sync_all();
+  return ok;
 }
 template <int KIND, bool kTopChain = true>
 __device__ __forceinline__ void chol_solve(Prob<KIND>& p, double* x) {
@@ -427,16 +464,17 @@ __device__ RecView rec_view(const KArgs& a, int b) {
 }
 
 // ----------------------------------------------------------------------------- forward
-template <int KIND, class P>
+template <int KIND, class P, bool kCluster>
 __device__ void forward_problem(const KArgs& a, int b, char* smem, double* red, int* sflag,
-                                SnCmd* cmd) {
+                                ClCmd* cmd) {
   constexpr int D = Group<KIND>::DOF, PW = Group<KIND>::PW;
   Prob<KIND> p;
   p.init(a, b, smem, a.smem_bytes);
   p.stage_in(false);
-  // the cluster's other CTAs take part in the dense supernode's trailing updates when the
-  // factor is in global memory (they cannot see this CTA's shared memory)
-  const ClusterTeam team{a.cluster > 1 ? a.cluster : 1, b, cmd, a.cluster > 1 && p.L == p.Lg};
+  // the cluster's other CTAs take part in the factorizations when the factor is in global
+  // memory (they cannot see this CTA's shared memory)
+  const ClusterTeam team{a.cluster > 1 ? a.cluster : 1, cmd, kCluster && a.cluster > 1 && p.L == p.Lg};
+  if (team.on && threadIdx.x == 0) p.st->fact_flag = -1;  // published by the first command
   p.prepare_weights();
   const int n = p.N * D;
   double S = eval_S<KIND>(p, p.theta, red);
@@ -461,7 +499,7 @@ __device__ void forward_problem(const KArgs& a, int b, char* smem, double* red, 
       }
     }
     ++nfact;
-    const bool ok = factor_team<KIND>(p, lam, sflag, it, team);
+    const bool ok = factor_team<KIND, kCluster>(p, lam, sflag, it, team, b);
     factor_ok = ok ? 1 : 0;
     lam_fact = lam;
     if (!ok) {
@@ -715,38 +753,36 @@ __device__ __forceinline__ int next_problem(const KArgs& a, int* slot) {
   return q < a.g.B ? a.g.order[q] : -1;
 }
 
-// Cluster ranks > 0 of the GN/LM forward: their share of every dense-supernode trailing update
-// that rank 0 posts (supernode_trailing with the cluster's team indexing), until rank 0 posts
-// the exit.  Each command is one cluster barrier (then the slot is read from rank 0's shared
-// memory) and, for an update, one more after it; the exit's second barrier keeps rank 0 alive
-// until every helper has read the slot.
+// Cluster ranks > 0 of the GN/LM forward: take part in every factorization rank 0 posts, until
+// it posts the exit (the protocol is described at ClusterTeam).
 template <int KIND>
-__device__ void supernode_helper(const KArgs& a, const SnCmd* cmd, int rank, int nranks) {
+__device__ void cluster_helper(const KArgs& a, const ClCmd* cmd, int rank, int nranks) {
   for (;;) {
     cluster_sync_all();
     const int op = ld_cluster_shared(&cmd->op, 0);
-    if (op == kSnExit) {
+    if (op == kClExit) {
       cluster_sync_all();
       return;
     }
-    const int b = ld_cluster_shared(&cmd->b, 0), i = ld_cluster_shared(&cmd->i, 0);
+    const int b = ld_cluster_shared(&cmd->b, 0), gen = ld_cluster_shared(&cmd->gen, 0);
+    const double lam = ld_cluster_shared(&cmd->lam, 0);
     Prob<KIND> p;
     p.init(a, b, nullptr, 0);
-    supernode_trailing<Group<KIND>::DOF>(
-        p, p.L, i, ((threadIdx.x >> 5) * nranks + rank) * 32 + (threadIdx.x & 31), nranks * blockDim.x);
+    block_factor_cluster<Group<KIND>::DOF>(p, lam, rank, nranks, &p.st->fact_flag, gen);
     cluster_sync_all();
   }
 }
 
-template <int KIND, class P>
+// kCluster: launched as thread-block clusters of KArgs::cluster CTAs per problem.
+template <int KIND, class P, bool kCluster>
 __global__ void __launch_bounds__(256, 2) k_forward(KArgs a) {
   __shared__ double red[256];
   __shared__ int sflag, slot;
-  __shared__ SnCmd cmd;
-  const int nr = a.cluster > 1 ? a.cluster : 1;
+  __shared__ ClCmd cmd;
+  const int nr = kCluster && a.cluster > 1 ? a.cluster : 1;
   const int rank = (int)(blockIdx.x % (unsigned)nr);  // a 1-D cluster's CTA rank
   if (rank > 0) {
-    supernode_helper<KIND>(a, &cmd, rank, nr);
+    cluster_helper<KIND>(a, &cmd, rank, nr);
     return;
   }
   for (;;) {
@@ -754,11 +790,11 @@ __global__ void __launch_bounds__(256, 2) k_forward(KArgs a) {
     if (b < 0) break;
     if (threadIdx.x == 0) sflag = -1;
     __syncthreads();
-    forward_problem<KIND, P>(a, b, a.smem_bytes ? dyn_smem : nullptr, red, &sflag, &cmd);
+    forward_problem<KIND, P, kCluster>(a, b, a.smem_bytes ? dyn_smem : nullptr, red, &sflag, &cmd);
   }
   if (nr > 1) {
-    const ClusterTeam exit_team{nr, 0, &cmd, true};
-    exit_team.post(kSnExit, 0);
+    const ClusterTeam exit_team{nr, &cmd, true};
+    exit_team.post(kClExit, 0, 0, 0.0);
     cluster_sync_all();
   }
 }
@@ -1638,11 +1674,18 @@ dnls_status launch_forward(const dnls_graph* g, const dnls_solver_opts* opts, KA
   }
   const int ctas = opts->ctas_per_sm ? opts->ctas_per_sm : (g->impl.h.dof == 6 ? 1 : 2);
   const int cl = forward_cluster(g->impl, opts, ctas);
+  if (cl > 1) {
+    if (se3)
+      return mixed ? launch_persistent(k_forward<3, float, true>, g, opts, a, st, cl)
+                   : launch_persistent(k_forward<3, double, true>, g, opts, a, st, cl);
+    return mixed ? launch_persistent(k_forward<2, float, true>, g, opts, a, st, cl)
+                 : launch_persistent(k_forward<2, double, true>, g, opts, a, st, cl);
+  }
   if (se3)
-    return mixed ? launch_persistent(k_forward<3, float>, g, opts, a, st, cl)
-                 : launch_persistent(k_forward<3, double>, g, opts, a, st, cl);
-  return mixed ? launch_persistent(k_forward<2, float>, g, opts, a, st, cl)
-               : launch_persistent(k_forward<2, double>, g, opts, a, st, cl);
+    return mixed ? launch_persistent(k_forward<3, float, false>, g, opts, a, st)
+                 : launch_persistent(k_forward<3, double, false>, g, opts, a, st);
+  return mixed ? launch_persistent(k_forward<2, float, false>, g, opts, a, st)
+               : launch_persistent(k_forward<2, double, false>, g, opts, a, st);
 }
 
 }  // namespace

@@ -60,7 +60,8 @@ struct ProbState {
   double lambda_fact;  // damping of the cached factorization
   double S;            // objective at the returned poses
   int32_t factor_ok;   // cached factorization valid
-  int32_t pad[3];
+  int32_t fact_flag;   // failed-pivot flag of a cluster factorization (the LM iteration's number)
+  int32_t pad[2];
 };
 
 struct GraphHost {

@@ -156,3 +156,28 @@ def test_cluster_size_is_validated():
     b = synth.pgo_se3(batch=1, n_poses=16, n_lc=4, config_id=171)
     with pytest.raises(dnls.DnlsError):
         run_forward(b, layer.Options(algo="lm", iters=2, precision="fp64", cg_ctas=3))
+
+
+def test_cluster_failed_pivot_then_next_problem():
+    """Gauss-Newton on a batch whose first problem has no costs (H = 0: the first pivot fails)
+    and whose second has a supernode, on 2-CTA clusters: the cluster factorization reports the
+    failure to every CTA at the same barrier (status 2 for that problem), and the cluster goes on
+    to the next problem, which matches the oracle."""
+    one = synth.pgo_se3(batch=1, n_poses=6, n_lc=1, config_id=172)
+    big = synth.pgo_se3(batch=1, n_poses=500, n_lc=125, config_id=173)
+    b = synth.concat_pose_graphs([one, big])
+    b.pose_offsets = np.array([0, 2, 2 + 500], np.int64)
+    b.edge_offsets = np.array([0, 0, len(big.edge_i)], np.int64)
+    b.edge_i, b.edge_j = big.edge_i.copy(), big.edge_j.copy()
+    b.meas, b.wdiag, b.logw = big.meas.copy(), big.wdiag.copy(), big.logw.copy()
+    b.theta_init = np.concatenate([one.theta_init[:2], big.theta_init])
+    b.theta_gt = np.concatenate([one.theta_gt[:2], big.theta_gt])
+    opts = layer.Options(algo="gn", iters=6, precision="fp64", tau=0.0, threads=256,
+                         ctas_per_sm=2, smem_factor=0, cg_ctas=2)
+    sol, theta, _ = run_forward(b, opts)
+    info = sol.info_dict()
+    assert info["status"][0] == 2 and info["status"][1] == 0
+    _, ref, _ = oracle_solve(b, 1, opts)
+    assert rel(poses_of(b, theta, 1), ref) < 1e-7
+    sol1, theta1, _ = run_forward(b, layer.Options(**{**opts.__dict__, "cg_ctas": 1}))
+    assert torch.equal(theta, theta1)
