@@ -112,11 +112,13 @@ typedef struct {
                               1, 2, 4 or 8.  Bundle adjustment, tensor-core reduced solver: of the
                               forward's conjugate-gradient solve (library choice: enough to cover
                               the SMs, >= 32 rows each).  Pose graphs, GN / LM forward: the extra
-                              CTAs share each dense supernode's trailing updates (App. E; see
-                              dnls_graph_stats.supernode_cols_max), the rest of the problem runs
-                              on the first CTA (library choice: 1 unless the batch has a dense
-                              supernode and at most half as many problems as CTA slots, then the
-                              largest power of two <= 8 that keeps one slot per CTA) */
+                              CTAs share every numeric factorization (level schedule and dense
+                              supernode, App. E; see dnls_graph_stats.supernode_cols_max), the
+                              rest of the LM iteration runs on the first CTA; a problem whose
+                              factor fits in shared memory is factored by its first CTA alone
+                              (library choice: 1 unless the batch has a dense supernode and at
+                              most half as many problems as CTA slots, then the largest power of
+                              two <= 8 that keeps one slot per CTA) */
   int32_t reserved;        /* zero */
 } dnls_solver_opts;
 

@@ -66,7 +66,7 @@ struct KArgs {
   int rec_nmax;         // poses per record slot (the batch's largest problem)
   int smem_bytes;       // dynamic shared memory per CTA for staging (0 = none)
   int cluster;          // GN/LM forward: CTAs per problem (a thread-block cluster; 0 or 1: one),
-                        // the extra CTAs sharing the dense supernode's trailing updates
+                        // the extra CTAs sharing the numeric factorizations
 };
 
 template <int KIND>

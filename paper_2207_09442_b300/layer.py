@@ -37,7 +37,7 @@ class Options:
     trunc_steps: int = 0             # backward_mode "unroll": last k iterations only (0 = all)
     reduced_solver: str = "auto"     # bundle adjustment: "auto" | "tc" | "fp64"
     cg_ctas: int = 0                 # CTAs per problem (0 = library): BA reduced CG; pose-graph
-                                     # GN/LM forward: the dense supernode's trailing updates
+                                     # GN/LM forward: the numeric factorizations
 
     def c(self) -> _d.SolverOpts:
         fp64 = self.precision == "fp64"

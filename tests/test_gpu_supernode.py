@@ -119,9 +119,10 @@ def test_dogleg_and_dlm_with_supernode():
 
 @pytest.mark.parametrize("cl", [2, 4, 8])
 def test_cluster_shares_trailing_updates_bitwise(cl):
-    """CTAs per problem (a thread-block cluster) for the supernode's trailing updates: every
-    trailing block row is still computed by one thread in the same order, so the poses equal the
-    single-CTA forward's bit for bit."""
+    """CTAs per problem (a thread-block cluster) sharing the numeric factorizations: every
+    output (element sum, diagonal block, panel row, trailing block row) is still computed by one
+    thread or lane group in the same order, so the poses equal the single-CTA forward's bit for
+    bit."""
     b = synth.pgo_se3(batch=3, n_poses=600, n_lc=150, config_id=167)
     base = dict(algo="lm", iters=6, precision="mixed_fp32", tau=0.0, threads=256, ctas_per_sm=2,
                 smem_factor=0)
