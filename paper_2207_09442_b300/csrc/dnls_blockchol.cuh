@@ -151,6 +151,41 @@ __device__ __forceinline__ void diag_rows_inverse(F& p, const double* L, int c0,
   }
 }
 
+// L(k,k)^-1 in FP32 from the FP32 factor copy Lf, into Linvf, for k = c0 .. c1-1, by the 32 lanes
+// of one warp (lane r of group g: column r of block c0 + g, as diag_rows_inverse).  All 32 lanes
+// must call it.
+template <int D>
+__device__ __forceinline__ void diag_rows_inverse_f32(const float* Lf, float* Linvf, int c0, int c1) {
+  constexpr int BS = D * D;
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int grp = lane / D, r = lane - grp * D, base = grp * D;
+  const bool act = grp < c1 - c0;
+  const int k = act ? c0 + grp : 0;
+  const float* Lk = Lf + (int64_t)k * BS;
+  float A[D], I[D];
+#pragma unroll
+  for (int m = 0; m < D; ++m) A[m] = act ? Lk[r * D + m] : (m == r ? 1.0f : 0.0f);
+#pragma unroll
+  for (int i = 0; i < D; ++i) I[i] = 0.0f;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    const float lii = __shfl_sync(full, A[i], base + i);  // L(i, i) from lane i
+    float s = 0.0f;
+#pragma unroll
+    for (int m = 0; m < i; ++m) {
+      const float lim = __shfl_sync(full, A[m], base + i);  // L(i, m) from lane i
+      if (m >= r) s += lim * I[m];
+    }
+    if (i == r) I[i] = 1.0f / lii;
+    if (i > r) I[i] = -s / lii;
+  }
+  if (act) {
+#pragma unroll
+    for (int m = 0; m < D; ++m) Linvf[(int64_t)k * BS + m * D + r] = I[m];
+  }
+}
+
 // Off-diagonal blocks of level lv's columns by forward substitution with L(k,k) and its
 // reciprocal pivots (the diagonal of L(k,k)^-1, stored by diag_rows_factor):
 // L(r,k) <- A(r,k) L(k,k)^-T, one row per thread of the team.
@@ -334,8 +369,12 @@ __device__ bool dense_supernode(F& p, double* L, int* sflag, int gen) {
 // Returns false (uniformly across the CTA) if a pivot is not positive or not finite.  A failing
 // thread writes the call's generation number `gen` into *sflag; the flag is never reset, so a
 // slow thread can never see a later call's state.
+// inverse = false leaves out the final pass (L(k,k)^-1 then holds only its diagonal, the
+// reciprocal pivots): for a caller that forms the inverses another way or later
+// (diag_inverses).
 template <int D, class F>
-__device__ bool block_factor(F& p, double lam, int* sflag, int gen, double shift = 0.0) {
+__device__ bool block_factor(F& p, double lam, int* sflag, int gen, double shift = 0.0,
+                             bool inverse = true) {
   constexpr int CPW = 32 / D;  // diagonal blocks per warp in diag_rows_factor
   double* L = p.L;
   const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -371,10 +410,23 @@ __device__ bool block_factor(F& p, double lam, int* sflag, int gen, double shift
     __syncthreads();
   }
   if (nsparse < p.nlev && !dense_supernode<D>(p, L, sflag, gen)) return false;
-  for (int cc = warp * CPW; cc < p.N; cc += nwarps * CPW)
-    diag_rows_inverse<D>(p, L, cc, min(cc + CPW, p.N), nullptr);
-  __syncthreads();
+  if (inverse) {
+    for (int cc = warp * CPW; cc < p.N; cc += nwarps * CPW)
+      diag_rows_inverse<D>(p, L, cc, min(cc + CPW, p.N), nullptr);
+    __syncthreads();
+  }
   return true;
+}
+
+// The inverse pass of block_factor on its own (after a factorization with inverse = false), by
+// this CTA's warps.
+template <int D, class F>
+__device__ void diag_inverses(F& p) {
+  constexpr int CPW = 32 / D;
+  const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  for (int cc = warp * CPW; cc < p.N; cc += nwarps * CPW)
+    diag_rows_inverse<D>(p, p.L, cc, min(cc + CPW, p.N), nullptr);
+  __syncthreads();
 }
 
 // ----------------------------------------------------------------------------- cluster factor
@@ -392,7 +444,7 @@ __device__ bool block_factor(F& p, double lam, int* sflag, int gen, double shift
 // structures analysed without one).
 template <int D, bool kDense = true, class F>
 __device__ bool block_factor_cluster(F& p, double lam, int rank, int nranks, int* gflag, int gen,
-                                     double shift = 0.0) {
+                                     double shift = 0.0, bool inverse = true) {
   double* L = p.L;
   // team index: consecutive warps of work go to consecutive CTAs, so that a phase with fewer
   // items than the cluster has threads still spreads over all of the cluster's SMs
@@ -442,9 +494,11 @@ __device__ bool block_factor_cluster(F& p, double lam, int rank, int nranks, int
       cluster_sync_all();
     }
   }
-  for (int cc = warp * CPW; cc < p.N; cc += nwarps * CPW)
-    diag_rows_inverse<D>(p, L, cc, min(cc + CPW, p.N), nullptr);
-  cluster_sync_all();
+  if (inverse) {
+    for (int cc = warp * CPW; cc < p.N; cc += nwarps * CPW)
+      diag_rows_inverse<D>(p, L, cc, min(cc + CPW, p.N), nullptr);
+    cluster_sync_all();
+  }
   return true;
 }
 

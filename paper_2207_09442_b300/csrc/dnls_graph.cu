@@ -362,8 +362,8 @@ __device__ void assemble(Prob<KIND>& p) {
 // ----------------------------------------------------------------------------- factor / solve
 template <int KIND>
 __device__ __forceinline__ bool factor(Prob<KIND>& p, double lam, int* sflag, int gen,
-                                       double shift = 0.0) {
-  return block_factor<Group<KIND>::DOF>(p, lam, sflag, gen, shift);
+                                       double shift = 0.0, bool inverse = true) {
+  return block_factor<Group<KIND>::DOF>(p, lam, sflag, gen, shift, inverse);
 }
 // Thread-block cluster per problem (GN/LM forward, KArgs::cluster > 1).  Rank 0 runs the
 // problem; the other CTAs wait in cluster_helper and join each numeric factorization, which
@@ -377,18 +377,20 @@ enum { kClExit = 0, kClFactor = 1 };
 struct ClCmd {
   double lam;  // damping of the factorization
   int op, b, gen;
+  int inverse;  // form the inverses of the diagonal blocks (block_factor's final pass)
 };
 
 struct ClusterTeam {
   int nranks;  // CTAs of the cluster (1: none)
   ClCmd* cmd;  // rank 0's command slot
   bool on;     // this problem's factor is in global memory (the helpers cannot see shared memory)
-  __device__ void post(int op, int b, int gen, double lam) const {
+  __device__ void post(int op, int b, int gen, double lam, bool inverse) const {
     if (threadIdx.x == 0) {
       cmd->op = op;
       cmd->b = b;
       cmd->gen = gen;
       cmd->lam = lam;
+      cmd->inverse = inverse ? 1 : 0;
     }
     cluster_sync_all();
   }
@@ -400,10 +402,11 @@ struct ClusterTeam {
 // the single-CTA factorization alone.
 template <int KIND, bool kCluster>
 __device__ bool factor_team(Prob<KIND>& p, double lam, int* sflag, int it, const ClusterTeam& team,
-                            int b) {
-  if (!kCluster || !team.on) return factor<KIND>(p, lam, sflag, it);
-  team.post(kClFactor, b, it, lam);
-  const bool ok = block_factor_cluster<Group<KIND>::DOF>(p, lam, 0, team.nranks, &p.st->fact_flag, it);
+                            int b, bool inverse) {
+  if (!kCluster || !team.on) return factor<KIND>(p, lam, sflag, it, 0.0, inverse);
+  team.post(kClFactor, b, it, lam, inverse);
+  const bool ok = block_factor_cluster<Group<KIND>::DOF>(p, lam, 0, team.nranks, &p.st->fact_flag,
+                                                         it, 0.0, inverse);
   cluster_sync_all();
   return ok;
 }
@@ -484,6 +487,7 @@ __device__ void forward_problem(const KArgs& a, int b, char* smem, double* red, 
   assemble<KIND, P>(p);
   __syncthreads();
   const bool lm = a.algo == DNLS_LM;
+  const bool f32_solve = std::is_same<P, float>::value && !a.rec;  // mixed path, no records
   double lam = lm ? a.lam0 : 0.0, lam_fact = lam;
   int done = 0, accepted = 0, status = DNLS_PROBLEM_OK, factor_ok = 0, nfact = 0;
   RecView rv;
@@ -499,7 +503,7 @@ __device__ void forward_problem(const KArgs& a, int b, char* smem, double* red, 
       }
     }
     ++nfact;
-    const bool ok = factor_team<KIND, kCluster>(p, lam, sflag, it, team, b);
+    const bool ok = factor_team<KIND, kCluster>(p, lam, sflag, it, team, b, !f32_solve);
     factor_ok = ok ? 1 : 0;
     lam_fact = lam;
     if (!ok) {
@@ -510,14 +514,22 @@ __device__ void forward_problem(const KArgs& a, int b, char* smem, double* red, 
       lam = fmin(lam * 10.0, kLamMax);
       continue;
     }
-    if (std::is_same<P, float>::value && !a.rec) {
+    if (f32_solve) {
       // mixed path: the LM step solved with an FP32 copy of the FP64 factor (H itself was
       // assembled in FP32, so the step keeps its accuracy class; the fixed point, g = 0 in FP64
-      // sums, is unchanged); FP32 instructions keep the level chains short.  A forward that
-      // records its steps for the unrolled backward solves in FP64, as that backward assumes.
+      // sums, is unchanged); FP32 instructions keep the level chains short.  The inverses of the
+      // diagonal blocks are formed in FP32 from the copy (the FP64 ones only once, for the
+      // cached factor, after the last iteration).  A forward that records its steps for the
+      // unrolled backward solves in FP64, as that backward assumes.
       const int nb = (p.N + p.nnzL) * D * D;
       for (int k = threadIdx.x; k < nb; k += blockDim.x) p.Lf[k] = (float)p.L[k];
-      for (int k = threadIdx.x; k < p.N * D * D; k += blockDim.x) p.Linvf[k] = (float)p.Linv[k];
+      __syncthreads();
+      {
+        constexpr int CPW = 32 / D;
+        const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+        for (int cc = warp * CPW; cc < p.N; cc += nwarps * CPW)
+          diag_rows_inverse_f32<D>(p.Lf, p.Linvf, cc, min(cc + CPW, p.N));
+      }
       float* xf = (float*)p.bx;  // the backward's vector, free during the forward: x, then tmp
       for (int k = threadIdx.x; k < n; k += blockDim.x) xf[k] = (float)(-p.g[k]);
       __syncthreads();
@@ -566,6 +578,7 @@ __device__ void forward_problem(const KArgs& a, int b, char* smem, double* red, 
     }
     if (frozen) break;
   }
+  if (factor_ok && f32_solve) diag_inverses<D>(p);  // the cached factor's FP64 inverses
   if (factor_ok) p.stage_out_factor();  // keep the factor for the backward
   if (threadIdx.x == 0) {
     if (a.rec) *rv.done = done;
@@ -765,10 +778,11 @@ __device__ void cluster_helper(const KArgs& a, const ClCmd* cmd, int rank, int n
       return;
     }
     const int b = ld_cluster_shared(&cmd->b, 0), gen = ld_cluster_shared(&cmd->gen, 0);
+    const bool inverse = ld_cluster_shared(&cmd->inverse, 0) != 0;
     const double lam = ld_cluster_shared(&cmd->lam, 0);
     Prob<KIND> p;
     p.init(a, b, nullptr, 0);
-    block_factor_cluster<Group<KIND>::DOF>(p, lam, rank, nranks, &p.st->fact_flag, gen);
+    block_factor_cluster<Group<KIND>::DOF>(p, lam, rank, nranks, &p.st->fact_flag, gen, 0.0, inverse);
     cluster_sync_all();
   }
 }
@@ -794,7 +808,7 @@ __global__ void __launch_bounds__(256, 2) k_forward(KArgs a) {
   }
   if (nr > 1) {
     const ClusterTeam exit_team{nr, &cmd, true};
-    exit_team.post(kClExit, 0, 0, 0.0);
+    exit_team.post(kClExit, 0, 0, 0.0, false);
     cluster_sync_all();
   }
 }
