@@ -17,6 +17,7 @@ models; their exact generators are not given, so the recipes below are this proj
   ba_b32        32 bundle-adjustment problems, 64 cameras on a 10 m ring, 4096 points
   pgo_se3_p2048_b256 / pgo_se3_p4096_b64   256 x 2048-pose / 64 x 4096-pose SE(3) graphs,
                 loop closures 25 % of the poses, 10 LM iterations (mixed)
+  pgo_se3_p2048_b16   the first 16 problems of pgo_se3_p2048_b256 (a small batch of large graphs)
 
 Seeds: ``numpy.random.Generator(PCG64(SeedSequence([config_id, b])))`` per problem ``b``.
 
@@ -357,6 +358,8 @@ def workload(name: str, batch: Optional[int] = None, **kw):
         return pgo_se3(batch=batch or 256, n_poses=2048, n_lc=512, config_id=7, **kw)
     if name == "pgo_se3_p4096_b64":
         return pgo_se3(batch=batch or 64, n_poses=4096, n_lc=1024, config_id=8, **kw)
+    if name == "pgo_se3_p2048_b16":
+        return pgo_se3(batch=batch or 16, n_poses=2048, n_lc=512, config_id=7, **kw)
     raise KeyError(name)
 
 
@@ -371,5 +374,6 @@ WORKLOADS = {
     # large graphs (the scale of the paper's scalability study, App. F: 10 inner iterations)
     "pgo_se3_p2048_b256": ("lm", 10, "mixed_fp32", 1e-3),
     "pgo_se3_p4096_b64": ("lm", 10, "mixed_fp32", 1e-3),
+    "pgo_se3_p2048_b16": ("lm", 10, "mixed_fp32", 1e-3),
 }
 
