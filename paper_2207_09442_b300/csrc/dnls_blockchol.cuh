@@ -337,6 +337,16 @@ __device__ __forceinline__ void supernode_trailing(F& p, double* L, int i, int t
   }
 }
 
+// supernode_trailing as a call with a register allocation of its own, for the cluster
+// factorization: inlined into the cluster instance of the forward kernel, spill placement alone
+// made its large-graph factorizations 2.2x slower (the single-CTA factorization keeps the inline
+// form, whose allocation measured best there and which a call boundary would change for every
+// problem size).
+template <int D, class F>
+__device__ __noinline__ void supernode_trailing_call(F& p, double* L, int i, int tid, int nthr) {
+  supernode_trailing<D>(p, L, i, tid, nthr);
+}
+
 // The dense supernode, factored right-looking once the sparse levels are final: (1) every
 // supernode block minus its products with sparse columns, one gather over all its targets;
 // then for each supernode column i: (2) its diagonal block factored by warp 0, (3) its
@@ -490,7 +500,7 @@ __device__ bool block_factor_cluster(F& p, double lam, int rank, int nranks, int
       panel_subst<D>(p, L, nsparse + i, tid, nthr);
       cluster_sync_all();
       if (m - 1 - i == 0) break;
-      supernode_trailing<D>(p, L, i, tid, nthr);
+      supernode_trailing_call<D>(p, L, i, tid, nthr);
       cluster_sync_all();
     }
   }
