@@ -565,7 +565,8 @@ def run_pose_graphs(args, rank, world, local, dist, out):
     out.update({
         "value": sum_over_ranks(executed, dist, dev) / (ms_per_step * 1e-3), "ms_per_step": ms_per_step,
         "dtype": ("f64" if precision == "fp64" else
-                  "mixed: f32 linearize/assemble, f64 factor/solve/accept/backward"),
+                  "mixed: f32 linearize/assemble and LM-step solves (f32 copy of the f64 "
+                  "factor), f64 factor/accept/backward"),
         "data": f"synthetic (seeded generator, random-walk SE({batch.kind}) graphs)",
         "config": {"workload": name, "problems": B,
                    "poses": (int(sizes[0]) if sizes.min() == sizes.max()
@@ -805,7 +806,9 @@ def run_ba(args, rank, world, local, dist, out):
     C, Pn = int(np.diff(b.cam_offsets)[0]), int(np.diff(b.pt_offsets)[0])
     out.update({
         "value": sum_over_ranks(executed, dist, dev) / (ms_per_step * 1e-3), "ms_per_step": ms_per_step,
-        "dtype": "mixed: f32 reprojection linearize, f64 Schur/factor/solve/accept/backward",
+        "dtype": "mixed: f32 reprojection linearize; f64 Schur; reduced system factored on the "
+                 "tensor cores (bf16 3-term split, f32 accumulate) with f64 CG refinement; f64 "
+                 "accept/backward",
         "data": "synthetic (seeded generator: ring of cameras, uniform points, 1 px noise)",
         "config": {"workload": name, "problems": b.batch, "cameras": C, "points": Pn,
                    "observations": int(b.obs_offsets[-1]), "iterations": iters,

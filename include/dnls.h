@@ -92,7 +92,11 @@ typedef struct {
   int32_t iters;           /* number of iterations K (>= 0) */
   int32_t precision;       /* DNLS_FP64, or DNLS_MIXED_FP32 (residuals, Jacobians and H in FP32,
                               each cost's term of g in FP32; relative poses, the sum of g, the
-                              Schur complement, the factorization and the acceptance in FP64) */
+                              Schur complement, the factorization and the acceptance in FP64;
+                              pose graphs: the GN/LM step's triangular solves with an FP32 copy
+                              of the FP64 factor, FP32 inverses of its diagonal blocks; bundle
+                              adjustment: the reduced camera system factored on the tensor cores
+                              at FP32 level and refined by FP64 conjugate gradients) */
   int32_t backward_mode;   /* DNLS_IMPLICIT_EXACT (true Hessian of S), DNLS_IMPLICIT_GN,
                               DNLS_BACKWARD_DLM or DNLS_BACKWARD_UNROLL */
   int32_t refine_max;      /* max (preconditioned CG) steps of the adjoint solve (>= 1) */
