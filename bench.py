@@ -48,7 +48,7 @@ METRIC = "batched LM iters/s (fwd + implicit bwd) vs plain FP64 GPU path at 1e-5
 # while the sources still hash to the captured build; null otherwise.
 FORWARD_SOURCES = ["dnls_graph.cu", "dnls_blockchol.cuh", "dnls_cost.cuh", "dnls_lie.cuh",
                    "dnls_graph.h", "dnls_symbolic.cpp"]
-CAPTURED_TRAFFIC = {"pgo_se3_b256": ("1663ae9e05324f15", (4.693760e6 + 1.670912e6) * 256 / 64)}
+CAPTURED_TRAFFIC = {"pgo_se3_b256": ("dfbbadaa0f0b9239", (6.829568e6 + 1.579008e6) * 256 / 64)}
 
 
 def forward_cluster(st, opts, ctas_per_sm: int, dev) -> int:
