@@ -3,7 +3,8 @@ reduced solve.
 
 The numeric work does not depend on the launch shape; only speed does.  The tuner times the
 forward (and backward) of the caller's own batch for each candidate (threads per CTA, resident
-CTAs per SM, shared-memory staging of the factor) and keeps the fastest, caching it in a JSON file
+CTAs per SM, shared-memory staging of the factor; for a batch with a dense supernode then also
+the CTAs per problem at the winning shape) and keeps the fastest, caching it in a JSON file
 keyed by group, precision, a bucket of the largest pose count and the batch size, and the GPU.
 Launch shapes the GPU cannot run (too many registers or too much shared memory for the requested
 residency) fail at launch and are skipped.
@@ -24,6 +25,7 @@ from . import layer
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned_launch.json")
 CANDIDATES = [(256, 1, 1), (256, 1, 0), (128, 2, 0), (128, 2, 1), (128, 1, 1), (256, 2, 0),
               (128, 3, 0), (128, 4, 0)]
+CLUSTER_CANDIDATES = [1, 2, 4, 8]  # CTAs per problem, batches with a dense supernode
 
 
 def _key(st: layer.PoseGraphStructure, opts: layer.Options) -> str:
@@ -83,8 +85,20 @@ def tune(st: layer.PoseGraphStructure, opts: layer.Options, inputs, v: Optional[
     if not ok:
         raise RuntimeError(f"no launch shape ran: {table}")
     win = min(ok, key=lambda r: r["ms"])
+    # batches with a dense supernode: the CTAs per problem (a thread-block cluster sharing the
+    # factorizations) at the winning shape; 0 keeps the library's choice
+    cg = 0
+    if opts.cg_ctas == 0 and opts.algo in ("gn", "lm") and st.stats()["n_supernodes"] > 0:
+        for kc in CLUSTER_CANDIDATES:
+            shape = {k: win[k] for k in ("threads", "ctas_per_sm", "smem_factor")}
+            ms = _time_shape(st, layer.Options(**{**opts.__dict__, **shape, "cg_ctas": kc}), inputs,
+                             v, reps)
+            table.append({**shape, "cg_ctas": kc, "ms": ms})
+            if ms is not None and ms < win["ms"]:
+                win = {**shape, "ms": ms}
+                cg = kc
     out = {"threads": win["threads"], "ctas_per_sm": win["ctas_per_sm"],
-           "smem_factor": win["smem_factor"], "ms": win["ms"], "table": table,
+           "smem_factor": win["smem_factor"], "cg_ctas": cg, "ms": win["ms"], "table": table,
            "tuned_at": time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime())}
     cache[key] = out
     try:
@@ -95,9 +109,38 @@ def tune(st: layer.PoseGraphStructure, opts: layer.Options, inputs, v: Optional[
     return out
 
 
+def _time_shape(st, o: layer.Options, inputs, v, reps: int):
+    """Best-of-``reps`` ms of forward (+ backward with ``v``) at the options' launch shape, or
+    None if the shape cannot launch."""
+    theta0, meas, wd, lw = inputs
+    stream = torch.cuda.current_stream()
+    try:
+        sol = layer.PoseGraphSolver(st, o, theta0.device)
+        th = sol.forward(theta0, meas, wd, lw)
+        if v is not None:
+            sol.backward(th, v, meas, wd, lw)
+        torch.cuda.synchronize()
+        best = float("inf")
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            th = sol.forward(theta0, meas, wd, lw)
+            if v is not None:
+                sol.backward(th, v, meas, wd, lw)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        return best
+    except _d.DnlsError:
+        torch.cuda.synchronize()
+        return None
+
+
 def apply(opts: layer.Options, tuned: dict) -> layer.Options:
     return layer.Options(**{**opts.__dict__, "threads": tuned["threads"],
-                            "ctas_per_sm": tuned["ctas_per_sm"], "smem_factor": tuned["smem_factor"]})
+                            "ctas_per_sm": tuned["ctas_per_sm"], "smem_factor": tuned["smem_factor"],
+                            "cg_ctas": tuned.get("cg_ctas", opts.cg_ctas)})
 
 
 # ----------------------------------------------------------------------------- bundle adjustment

@@ -182,3 +182,26 @@ def test_cluster_failed_pivot_then_next_problem():
     assert rel(poses_of(b, theta, 1), ref) < 1e-7
     sol1, theta1, _ = run_forward(b, layer.Options(**{**opts.__dict__, "cg_ctas": 1}))
     assert torch.equal(theta, theta1)
+
+
+def test_autotuner_tunes_ctas_per_problem_for_supernodes():
+    """For a batch with a dense supernode the tuner also times the CTAs per problem at its best
+    shape; the tuned options run and give the poses of the untuned solver bit for bit (the
+    cluster split does not change any sum)."""
+    from paper_2207_09442_b300 import autotune
+    from gpu_util import t32, t64
+    b = synth.pgo_se3(batch=2, n_poses=500, n_lc=125, config_id=174)
+    st = layer.PoseGraphStructure.from_batch(b)
+    opts = layer.Options(algo="lm", iters=4, precision="mixed_fp32", smem_factor=0)
+    inputs = (t64(b.theta_init), t64(b.meas), t64(b.wdiag), t32(b.logw))
+    tuned = autotune.tune(st, opts, inputs, use_cache=False, reps=1,
+                          candidates=[(256, 2, 0), (256, 1, 0)])
+    assert tuned["cg_ctas"] in (0, 1, 2, 4, 8)
+    assert {r.get("cg_ctas") for r in tuned["table"]} >= {1, 2, 4, 8}
+    tuned_opts = autotune.apply(opts, tuned)
+    th = layer.PoseGraphSolver(st, tuned_opts).forward(*inputs)
+    ref = layer.PoseGraphSolver(st, layer.Options(**{**opts.__dict__, "threads": tuned["threads"],
+                                                     "ctas_per_sm": tuned["ctas_per_sm"],
+                                                     "cg_ctas": 1})).forward(*inputs)
+    torch.cuda.synchronize()
+    assert torch.equal(th, ref)
