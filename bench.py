@@ -606,7 +606,9 @@ def run_pose_graphs(args, rank, world, local, dist, out):
     out["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                        "frac": achieved / peak,
                        "traffic": captured_traffic(name, B) if algo != "dogleg" else None,
-                       "kernel": f"{kname}<{batch.kind},{'double' if precision == 'fp64' else 'float'}>"
+                       "kernel": f"{kname}<{batch.kind},{'double' if precision == 'fp64' else 'float'}"
+                                 + ("" if algo == "dogleg" else
+                                    f",{int(out['launch_shape']['ctas_per_problem'] > 1)}") + ">"
                                  " (algorithmic FP64 block Cholesky flops of the factorizations run)",
                        "peak_source": "FP64 FMA probe on this GPU (dnls_probe_fp64_peak), of measured"}
     # the backward kernel: per adjoint CG step two triangular solves with the cached factor
