@@ -205,3 +205,21 @@ def test_autotuner_tunes_ctas_per_problem_for_supernodes():
                                                      "cg_ctas": 1})).forward(*inputs)
     torch.cuda.synchronize()
     assert torch.equal(th, ref)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed_fp32"])
+def test_cluster_se2_bitwise_and_oracle(precision):
+    """SE(2) graphs dense enough for a supernode, on 4-CTA clusters: the same poses as one CTA
+    per problem bit for bit, and the oracle's (FP64: 1e-9; mixed: 1e-5)."""
+    b = synth.pgo_se2(batch=3, n_poses=48, n_lc=900, config_id=175)
+    assert layer.analyze(b)["n_supernodes"] == 3
+    base = dict(algo="lm", iters=8, precision=precision, tau=0.0, threads=128, ctas_per_sm=2,
+                smem_factor=0)
+    _, th1, _ = run_forward(b, layer.Options(**base, cg_ctas=1))
+    sol4, th4, _ = run_forward(b, layer.Options(**base, cg_ctas=4))
+    assert torch.equal(th1, th4)
+    assert (sol4.info_dict()["status"] == 0).all()
+    tol = 1e-9 if precision == "fp64" else 1e-5
+    for k in range(b.batch):
+        _, ref, _ = oracle_solve(b, k, layer.Options(**base))
+        assert rel(poses_of(b, th4, k), ref) < tol, k
