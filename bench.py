@@ -40,7 +40,8 @@ WORKLOAD = "pgo_se3_b256"
 # from the workload table of the synthetic-data module)
 PER_GPU = {"pgo_se2_b16": 16, "pgo_se3_b256": 256, "pgo_se3_implicit_b256": 256,
            "pgo_se3_uneven_b1024": 1024, "pgo_se3_robust_b256": 256, "ba_b32": 32,
-           "pgo_se3_p2048_b256": 256, "pgo_se3_p4096_b64": 64, "pgo_se3_p2048_b16": 16}
+           "pgo_se3_p2048_b256": 256, "pgo_se3_p4096_b64": 64, "pgo_se3_p2048_b16": 16,
+           "pgo_se3_p8192_b16": 16}
 METRIC = "batched LM iters/s (fwd + implicit bwd) vs plain FP64 GPU path at 1e-5"
 # DRAM bytes (read + write) per launch of the dominant kernel, from a full ncu capture of the
 # forward kernel built from the sources that hash to the recorded value (a 64-problem case,

@@ -18,6 +18,8 @@ models; their exact generators are not given, so the recipes below are this proj
   pgo_se3_p2048_b256 / pgo_se3_p4096_b64   256 x 2048-pose / 64 x 4096-pose SE(3) graphs,
                 loop closures 25 % of the poses, 10 LM iterations (mixed)
   pgo_se3_p2048_b16   the first 16 problems of pgo_se3_p2048_b256 (a small batch of large graphs)
+  pgo_se3_p8192_b16   16 SE(3) graphs of 8192 poses (the largest pose count of the paper's
+                scalability study), loop closures 25 % of the poses, 10 LM iterations (mixed)
 
 Seeds: ``numpy.random.Generator(PCG64(SeedSequence([config_id, b])))`` per problem ``b``.
 
@@ -360,6 +362,8 @@ def workload(name: str, batch: Optional[int] = None, **kw):
         return pgo_se3(batch=batch or 64, n_poses=4096, n_lc=1024, config_id=8, **kw)
     if name == "pgo_se3_p2048_b16":
         return pgo_se3(batch=batch or 16, n_poses=2048, n_lc=512, config_id=7, **kw)
+    if name == "pgo_se3_p8192_b16":
+        return pgo_se3(batch=batch or 16, n_poses=8192, n_lc=2048, config_id=9, **kw)
     raise KeyError(name)
 
 
@@ -375,5 +379,6 @@ WORKLOADS = {
     "pgo_se3_p2048_b256": ("lm", 10, "mixed_fp32", 1e-3),
     "pgo_se3_p4096_b64": ("lm", 10, "mixed_fp32", 1e-3),
     "pgo_se3_p2048_b16": ("lm", 10, "mixed_fp32", 1e-3),
+    "pgo_se3_p8192_b16": ("lm", 10, "mixed_fp32", 1e-3),
 }
 
