@@ -719,6 +719,35 @@ def run_pose_graphs(args, rank, world, local, dist, out):
                                                f"median per problem, mean x{B}",
                                      "max_relative_spread": max(spread)}
     out["speedup_vs_plain_fp64"] = plain_ms / ms_per_step
+    # context only (not this library's path): the paper's dense solver analogue, a batched FP64
+    # torch.linalg.cholesky + cholesky_solve of dense n x n SPD matrices of the workload's size,
+    # timed per LM iteration (factor and solve only: no linearization, retraction or backward)
+    nmax = int(sizes.max()) * dof
+    dense_bytes = B * nmax * nmax * 8
+    if dense_bytes <= 8e9:
+        g_ = torch.Generator(device=dev).manual_seed(7)
+        Hd = torch.randn(B, nmax, nmax, dtype=torch.float64, device=dev, generator=g_) / nmax ** 0.5
+        Hd = Hd @ Hd.transpose(1, 2) + torch.eye(nmax, dtype=torch.float64, device=dev)
+        rhs = torch.randn(B, nmax, 1, dtype=torch.float64, device=dev, generator=g_)
+        for _ in range(2):
+            torch.cholesky_solve(rhs, torch.linalg.cholesky(Hd))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        dreps = 5
+        e0.record(stream)
+        for _ in range(dreps):
+            torch.cholesky_solve(rhs, torch.linalg.cholesky(Hd))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_d = e0.elapsed_time(e1) / dreps
+        out["dense_cholesky_context"] = {
+            "ms_per_iteration": ms_d, "n": nmax, "batch": B,
+            "factor_solve_lm_iters_per_s": B / (ms_d * 1e-3),
+            "what": "torch.linalg.cholesky + cholesky_solve, FP64, batched dense n x n (the paper's "
+                    "dense solver analogue); factor and solve only, context, not this library's path"}
+        del Hd, rhs
+    else:
+        out["dense_cholesky_context"] = {"skipped": f"the dense batch would hold {dense_bytes / 1e9:.0f} GB"}
     # end to end through the public API with host (pinned) buffers
     h_in = [torch.as_tensor(np.ascontiguousarray(a)).pin_memory() for a in
             (batch.theta_init, batch.meas, batch.wdiag, batch.logw)] + [v.cpu().pin_memory()]
