@@ -96,3 +96,12 @@ def test_unroll_needs_the_record_and_rejects_dogleg():
     big = layer.PoseGraphSolver(st, layer.Options(algo="lm", iters=3, precision="fp64",
                                                   backward_mode="unroll"))
     assert big.workspace.numel() > small.workspace.numel()  # room for the iteration records
+
+
+def test_unrolled_through_supernode_factorizations():
+    """Unrolling on graphs whose factor has a dense supernode (48 SE(3) poses, 400 loop closures):
+    every recorded iteration is refactored with the supernode path, and the gradients match
+    autograd through the oracle's loop."""
+    b = synth.pgo_se3(batch=2, n_poses=48, n_lc=400, config_id=176, log_weights=True)
+    assert layer.analyze(b)["n_supernodes"] == 2
+    _check(b, 3, "lm", 4, 0)
