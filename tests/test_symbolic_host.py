@@ -1,7 +1,10 @@
 """The symbolic analysis on the host (no GPU): a small C++ driver compiled with g++ runs
 build_graph_host on seeded graphs of the benchmark shapes and checks the invariants the CUDA
 factorization and solves rely on (level schedule, top chain and its row partition, lane counts,
-gather lists with their early/late split and ordering, assembly maps)."""
+gather lists with their early/late split and ordering, the dense supernode's storage and source
+lists, assembly maps).  It then runs the device factorization's steps as plain host loops on a
+seeded SPD matrix with the graph's pattern, through the same structure and the same block-row
+mapping of the supernode's trailing updates, and checks L L^T against the matrix."""
 import os
 import shutil
 import subprocess
@@ -44,6 +47,8 @@ def _run(checker, batch):
     lambda: synth.pgo_se3(batch=6, n_poses_range=(16, 256), config_id=4),  # uneven sizes
     lambda: synth.pgo_se3(batch=2, n_poses=24, n_lc=0, config_id=153),     # pure chains
     lambda: synth.pgo_se3(batch=3, n_poses=8, n_lc=6, config_id=154),      # dense small graphs
+    lambda: synth.pgo_se3(batch=2, n_poses=48, n_lc=400, config_id=160),   # supernode: most of L
+    lambda: synth.pgo_se3(batch=1, n_poses=600, n_lc=150, config_id=162),  # supernode on sparse levels
 ])
 def test_symbolic_invariants(checker, make):
     b = make()
@@ -51,14 +56,23 @@ def test_symbolic_invariants(checker, make):
     assert len(out) == b.batch
     for line in out:
         assert line.startswith("ok"), line
+        assert float(line.split()[5]) < 1e-12  # emulated factorization: L L^T = A
+
+
+def test_supernode_is_emulated(checker):
+    """The 600-pose graph gets a dense supernode (its first level below the number of levels),
+    and the emulation goes through it."""
+    b = synth.pgo_se3(batch=1, n_poses=600, n_lc=150, config_id=162)
+    _, nlev, chain_lev, _, dense_lev, resid = _run(checker, b)[0].split()
+    assert int(dense_lev) == int(chain_lev) < int(nlev) and float(resid) < 1e-12
 
 
 def test_pure_chain_is_all_top_chain(checker):
     """An odometry chain eliminates as a path: one column per level, the top chain starts at
     level 0."""
     b = synth.pgo_se3(batch=1, n_poses=24, n_lc=0, config_id=153)
-    _, nlev, chain_lev, _ = _run(checker, b)[0].split()
-    assert int(nlev) == 24 and int(chain_lev) == 0
+    _, nlev, chain_lev, _, dense_lev, _ = _run(checker, b)[0].split()
+    assert int(nlev) == 24 and int(chain_lev) == 0 and int(dense_lev) == 24  # sparse: no supernode
 
 
 def test_flop_count_matches_block_structure(checker):
